@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Throughput of the matrix-free P1 operator apply y = A x on GB300.
+
+One step = one apply on the 2D workload "square32jit_L11": the unit square as
+4x4 cells x 2 triangles = 32 jittered macro-triangles, refined to level 11
+(67,125,249 distinct DoFs, 67,207,200 slots), float64 vectors, x ~ U[-1,1].
+The metric is distinct DoF updates per second (GDoF/s) — the paper's
+throughput unit (Sec. 4.2 reports GFLOP/s of the same kernel at 13 flop per
+update).  Inputs (0.54 GB x + 0.54 GB y) are larger than the 129 MB L2, so
+the L2 is not flushed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (the apply has no data-path collective at this size);
+`value` sums all ranks' DoF updates over the slowest rank's time.
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GDoF-updates/s of A*x (P1 stiffness apply, distinct DoFs)"
+UNIT = "GDoF/s"
+WORKLOAD = "square32jit_L11"
+CPU_SAMPLE_LEVEL = 9
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-variants", action="store_true", help="skip the fp32 / 3D / native-fp64 lines")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(name):
+    from inputs import WORKLOADS
+    w = WORKLOADS[name]
+    return w
+
+
+def describe(name, n_global, n_slots):
+    from inputs import WORKLOADS
+    w = WORKLOADS[name]
+    if w["dim"] == 2:
+        shape = f"unit square, {w['k']}x{w['k']} cells x 2 triangles = {2 * w['k'] ** 2} macro-triangles"
+    else:
+        shape = f"unit cube, {w['k']}^3 cells x 6 Kuhn tets = {6 * w['k'] ** 3} macro-tets"
+    jit = f", interior coarse vertices jittered U[-{w['jitter']}h, {w['jitter']}h] (seed {w['mesh_seed']})" \
+        if w["jitter"] else ""
+    return (f"{name}: {w['dim']}D P1 Laplacian apply, {shape}{jit}, level {w['level']}, "
+            f"{n_global} DoFs ({n_slots} slots), x ~ U[-1,1] seed {w['x_seed']}, Dirichlet rows identity")
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons, with timestamps."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        return rows
+
+    @staticmethod
+    def summarise(rows, t0, t1):
+        import datetime as dt
+        sel, allr = [], []
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                ts = dt.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            allr.append((ts, r))
+            if t0 - 0.05 <= ts <= t1 + 0.05:
+                sel.append(r)
+        note = None
+        if not sel and allr:  # timed window shorter than the sampling period
+            mid = 0.5 * (t0 + t1)
+            sel = [min(allr, key=lambda a: abs(a[0] - mid))[1]]
+            note = "timed region shorter than the 50 ms sampling period; nearest sample"
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in sel if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in sel if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in sel for i in range(4) if r[5 + i].strip() == "Active"})
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": reasons, "samples": len(sel)}
+        if note:
+            out["note"] = note
+        return out
+
+
+# ---------------------------------------------------------------- setup
+def setup(name, device, dtype_code):
+    import torch
+    import paper_2305_15116_gb300 as H
+    from inputs import workload, random_vector
+    coarse, L, seed = workload(name)
+    M = H.Mesh(coarse.coords, coarse.cells).refine(L)
+    ns, ng = M.num_slots(L)
+    smap = M.dof_map(L)
+    x = random_vector(ng, seed)
+    tdt = torch.float32 if dtype_code == H.F32 else torch.float64
+    xs = torch.from_numpy(x[smap]).to(device=device, dtype=tdt)
+    ys = torch.empty_like(xs)
+    n = 1 << L
+    interior = coarse.n_cells * ((n - 1) * (n - 2) // 2 if coarse.dim == 2 else (n - 1) * (n - 2) * (n - 3) // 6)
+    return dict(M=M, L=L, ns=ns, ng=ng, xs=xs, ys=ys, smap=smap, x_global=x, coarse=coarse,
+                interior=interior, elem=4 if dtype_code == H.F32 else 8, code=dtype_code)
+
+
+def timed_applies(w, steps, warmup, stream, barrier=None):
+    """Warm-up, then exactly `steps` applies timed with CUDA events on the
+    launching stream; per-kernel durations from events recorded by the
+    library between its two launches."""
+    import torch
+    M, L, code = w["M"], w["L"], w["code"]
+    xp, yp, sp = w["xs"].data_ptr(), w["ys"].data_ptr(), stream.cuda_stream
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for row in ev:  # create the events (torch creates them lazily)
+            for e in row:
+                e.record(stream)
+        for _ in range(warmup):
+            M.apply_raw(L, code, xp, yp, sp)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    start.record(stream)
+    for k in range(steps):
+        M.apply_timed(L, code, xp, yp, sp, ev[k][0].cuda_event, ev[k][1].cuda_event, ev[k][2].cuda_event)
+    end.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if barrier:
+        barrier()
+    total_ms = start.elapsed_time(end)
+    interior_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(steps)]
+    iface_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(steps)]
+    return dict(total_ms=total_ms, interior_ms=float(np.mean(interior_ms)), iface_ms=float(np.mean(iface_ms)),
+                t0=t0, t1=t1)
+
+
+def interior_bytes(w):
+    """Algorithmic bytes of one macro-interior launch: every slot of every
+    macro is read once (interior points and the macro-boundary halo) and
+    every interior point is written once."""
+    return w["elem"] * (w["ns"] + w["interior"])
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes from the committed ncu summary, only while the
+    kernel source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        entry = data[kernel_key]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, entry["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h2 = hashlib.sha256(open(os.path.join(ROOT, "paper_2305_15116_gb300", "csrc", "arith.cuh"), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if entry.get("source_sha") != h or entry.get("arith_sha") != h2:
+        return None
+    return entry["dram_bytes_per_launch"]
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_run(steps, warmup):
+    """The oracle's CSR SpMV on a bounded sample of the workload: the same
+    32-macro mesh at level 9, matrix assembled outside the timed region."""
+    import oracle
+    from inputs import workload, random_vector
+    coarse, L, seed = workload(WORKLOAD, level=CPU_SAMPLE_LEVEL)
+    rm = oracle.RefinedMesh(coarse.coords, coarse.cells, L)
+    A = oracle.operator_matrix(rm)
+    x = random_vector(rm.n_global, seed)
+    for _ in range(warmup):
+        oracle.spmv(A, x)
+    ts = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        oracle.spmv(A, x)
+        ts.append(time.perf_counter() - t)
+    sample = (f"{WORKLOAD} mesh at level {CPU_SAMPLE_LEVEL} ({rm.n_global} DoFs), scipy CSR SpMV of the "
+              f"oracle's assembled FP64 matrix, single thread, {steps} timed runs")
+    return rm.n_global, ts, sample
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    steps, warmup = args.steps, max(args.warmup, 1)
+    ng, ts, sample = cpu_oracle_run(steps, warmup)
+    total = sum(ts)
+    value = ng * steps / total / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": steps, "warmup": warmup,
+        "ms_per_step": 1e3 * total / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + f" (oracle sample at level {CPU_SAMPLE_LEVEL})", "parallelism": "none"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    barrier = (lambda: dist.barrier(device_ids=[local])) if world > 1 else None
+    import paper_2305_15116_gb300 as H
+
+    stream = torch.cuda.Stream(device=device)
+    w = setup(WORKLOAD, device, H.F64)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    time.sleep(0.2)
+    r = timed_applies(w, args.steps, args.warmup, stream, barrier)
+    clocks = ClockSampler.summarise(sampler.stop(), r["t0"], r["t1"]) if sampler else None
+
+    total_ms = r["total_ms"]
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = w["ng"] * args.steps * world / (total_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (copies inside the call)
+    xh = w["xs"].cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    w["M"].apply_host(w["L"], xh, yh, stream=stream)
+    if barrier:
+        barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        w["M"].apply_host(w["L"], xh, yh, stream=stream)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": w["ng"] * world / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+           "d2h_bytes_per_step": int(yh.numel() * yh.element_size())}
+    del xh, yh
+
+    peak, peak_kind = measured_peaks()
+    ib = interior_bytes(w)
+    achieved = ib / (r["interior_ms"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_interior2d<ArF64FF>", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                "traffic": ncu_traffic("interior2d_f64ff_square32jit_L11"),
+                "algorithmic_bytes_per_launch": ib,
+                "interior_ms": r["interior_ms"], "interface_ms": r["iface_ms"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 data, float-float (2 x f32) arithmetic", "data": "synthetic",
+        "config": {"workload": describe(WORKLOAD, w["ng"], w["ns"]), "dofs": w["ng"], "slots": w["ns"],
+                   "l2": "inputs larger than L2 (x+y = %.2f GB per apply), no flush" % (2 * w["ns"] * 8 / 1e9),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "impl": "ours",
+    }
+    del w
+    torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1 and not args.no_variants:
+        variants = []
+        for name, code, label in ((WORKLOAD, H.F32, "f32"), (WORKLOAD, H.F64_IEEE, "f64 native fma"),
+                                  ("cube384jit_L6", H.F64, "f64 data, float-float arithmetic"),
+                                  ("cube384jit_L6", H.F32, "f32"),
+                                  ("cube384jit_L6", H.F64_IEEE, "f64 native fma")):
+            v = setup(name, device, code)
+            steps = min(args.steps, 100)
+            rv = timed_applies(v, steps, args.warmup, stream)
+            vb = interior_bytes(v)
+            variants.append({
+                "workload": name, "dtype": label, "value": v["ng"] * steps / (rv["total_ms"] * 1e-3) / 1e9,
+                "unit": UNIT, "ms_per_step": rv["total_ms"] / steps,
+                "interior_GBps": vb / (rv["interior_ms"] * 1e-3) / 1e9,
+                "interior_frac": vb / (rv["interior_ms"] * 1e-3) / 1e9 / peak,
+                "interior_ms": rv["interior_ms"], "interface_ms": rv["iface_ms"]})
+            del v
+            torch.cuda.empty_cache()
+        line["variants"] = variants
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ng, ts, sample = cpu_oracle_run(5, 1)
+        line["cpu_baseline"] = {"value": ng / min(ts) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample + " (best of 5)"}
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,158 @@
+/*
+ * hyteg.h — C ABI of the GB300 matrix-free P1 operator library (libhyteg.so).
+ *
+ * The method (Thönnes & Rüde, "Model-Based Performance Analysis of the HyTeG
+ * Finite Element Framework", PASC '23):  an unstructured coarse mesh of
+ * triangles (2D) or tetrahedra (3D) — the "macro-primitives" — is refined
+ * uniformly L times, which gives a structured grid inside every macro
+ * (Sec. 1.2).  Inside a macro every row of the P1 stiffness matrix is the same
+ * constant stencil, so the matrix-vector product ("apply", Sec. 4.1) needs no
+ * stored matrix (Sec. 1.2, Sec. 2): 7 points in 2D (the vertex-to-vertex
+ * stencil of Sec. 4.2), 15 points in 3D.  The DoFs on macro vertices, edges
+ * and (3D) faces are completed by the interface step (Sec. 4.1).
+ *
+ * Conventions shared by every call
+ *  - All functions return HYTEG_OK (0) or a negative HYTEG_E* code and never
+ *    throw.  hyteg_last_error() returns a description of the most recent
+ *    failure on the calling thread.
+ *  - "Device" pointers are CUDA global-memory pointers on the device that was
+ *    current when the mesh was refined; "host" pointers are ordinary memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Kernels are enqueued on it and the call returns without synchronising,
+ *    unless stated otherwise.
+ *  - Vectors live in the library's "slot layout": macros in cell order, each
+ *    macro a contiguous array of S(L) slots, S(L) = (n+1)(n+2)/2 in 2D and
+ *    (n+1)(n+2)(n+3)/6 in 3D, n = 2^L.  Inside a 2D macro with vertices
+ *    (v0, v1, v2) the refined vertex v0 + (i/n)(v1-v0) + (j/n)(v2-v0) sits at
+ *    slot i + j(n+1) - j(j-1)/2 (row j, i inner — the index arithmetic of the
+ *    generated kernel of Sec. 3).  A 3D macro stacks such triangles slice by
+ *    slice along v3 (slice k has side n+1-k).  Every DoF on a macro
+ *    vertex/edge/face has one copy per incident macro; inputs must hold equal
+ *    values in all copies and outputs are written to all copies.
+ *  - Global vertex numbering (hyteg_dof_map): coarse vertices; then the
+ *    interior points of each coarse edge (edges sorted by (low id, high id),
+ *    points from the low to the high vertex); in 3D the interior points of
+ *    each coarse face (faces sorted by sorted vertex triple (f0<f1<f2), point
+ *    (a, b) at f0 + (a/n)(f1-f0) + (b/n)(f2-f0), b outer, a inner); then the
+ *    interior points of every cell in cell order and slot order.
+ */
+#ifndef HYTEG_H
+#define HYTEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HYTEG_OK         0
+#define HYTEG_EINVAL    -1   /* bad argument (null pointer, size, level, dtype) */
+#define HYTEG_ENOMEM    -2   /* host or device allocation failed */
+#define HYTEG_ECUDA     -3   /* a CUDA runtime call or kernel launch failed */
+#define HYTEG_EMESH     -4   /* coarse mesh is invalid (degenerate cell, non-conforming) */
+#define HYTEG_ESTATE    -5   /* call out of order (e.g. apply before refine) */
+
+/* ---- arithmetic / storage types of the apply --------------------------- */
+#define HYTEG_F64       1    /* float64 vectors; float-float (2 x fp32) arithmetic
+                                with integer-only conversions, relative error
+                                below 1e-13 of sum_j |a_ij x_j| for finite inputs
+                                with 2^-80 <= |x| < 2^126 (smaller values lose
+                                their low part, zero stays zero) */
+#define HYTEG_F32       2    /* float32 vectors, fp32 FMA arithmetic */
+#define HYTEG_F64_IEEE  3    /* float64 vectors, native fp64 FMA arithmetic */
+
+/* ---- boundary handling for hyteg_mesh_create ---------------------------- */
+#define HYTEG_BC_NONE       0  /* no Dirichlet rows: the plain stiffness matrix */
+#define HYTEG_BC_DIRICHLET  1  /* rows of DoFs on the domain boundary are identity
+                                  rows (y_b = x_b); a coarse edge (2D) or face (3D)
+                                  with one incident cell is on the boundary */
+
+typedef struct hyteg_mesh hyteg_mesh;   /* opaque, owned by the library */
+
+/* Creates a mesh from a conforming coarse simplex mesh (Sec. 1.2: the
+ * unstructured grid of triangles or tetrahedra that is refined uniformly).
+ *   dim       2 or 3
+ *   n_verts   number of coarse vertices (>= dim+1)
+ *   coords    host, float64 [n_verts * dim], vertex v at coords[v*dim + c]
+ *   n_cells   number of coarse cells (>= 1)
+ *   cells     host, int64 [n_cells * (dim+1)], the vertex ids of each cell; the
+ *             order inside a cell fixes that macro's local axes (v0 origin) and
+ *             is kept as given (either orientation is accepted)
+ *   bc        HYTEG_BC_NONE or HYTEG_BC_DIRICHLET
+ *   out       receives the new mesh
+ * The host arrays are copied; nothing is allocated on the GPU yet.
+ * Errors: HYTEG_EINVAL (bad sizes/ids/pointers), HYTEG_EMESH (zero-volume
+ * cell, an edge/face shared by an invalid number of cells), HYTEG_ENOMEM. */
+int hyteg_mesh_create(int dim, int64_t n_verts, const double* coords, int64_t n_cells,
+                      const int64_t* cells, int bc, hyteg_mesh** out);
+
+/* Refines every macro uniformly to levels 0..max_level (Sec. 1.2) and builds,
+ * on the current CUDA device, the per-macro constant stencils (7 weights in
+ * 2D, 15 in 3D, from the affine P1 element matrices; Sec. 1.2, Sec. 2), the
+ * interface tables and the kernels' work lists.  Allocates a few small device
+ * tables with cudaMalloc (size O(cells * levels + interface primitives)),
+ * owned by the mesh.  Synchronous.  May be called again with a larger level.
+ * Errors: HYTEG_EINVAL (max_level < 0 or > 15), HYTEG_ECUDA, HYTEG_ENOMEM. */
+int hyteg_mesh_refine(hyteg_mesh* mesh, int max_level);
+
+/* Frees the mesh and its device tables (synchronises the device first). */
+void hyteg_mesh_destroy(hyteg_mesh* mesh);
+
+/* Number of slots of one level (n_cells * S(L)) into *n_slots, and the number
+ * of distinct refined vertices into *n_global (either pointer may be NULL).
+ * Host-only: works for any level 0..15 without hyteg_mesh_refine.
+ * Errors: HYTEG_EINVAL (null mesh, level outside 0..15). */
+int hyteg_num_slots(const hyteg_mesh* mesh, int level, int64_t* n_slots, int64_t* n_global);
+
+/* Writes the global vertex id of every slot of `level` into the host array
+ * global_id[n_slots] (numbering: see the header comment).  Host-only, any
+ * level 0..15, no refine needed.  Errors: HYTEG_EINVAL. */
+int hyteg_dof_map(const hyteg_mesh* mesh, int level, int64_t* global_id);
+
+/* y = A x on refinement level `level` (Sec. 4.1 "apply"): A is the P1
+ * stiffness matrix of the refined mesh with Dirichlet identity rows when the
+ * mesh was created with HYTEG_BC_DIRICHLET.  Launches the macro-interior
+ * stencil kernel (Sec. 4.2 for the 2D 7-point case; 15 points in 3D) and the
+ * interface kernel, which completes the DoFs on macro vertices, edges and
+ * faces by summing the contributions of every incident macro in ascending
+ * macro order and writing the sum into every copy.
+ *   dtype   HYTEG_F64, HYTEG_F32 or HYTEG_F64_IEEE (element type of x and y)
+ *   x       device, [n_slots] in slot layout, copies consistent; read only
+ *   y       device, [n_slots]; every slot is written; must not overlap x
+ *   stream  cudaStream_t as void*
+ * Asynchronous.  No allocation.  Deterministic: the same inputs give bitwise
+ * the same outputs.  Errors: HYTEG_EINVAL (null, x == y, dtype),
+ * HYTEG_ESTATE (level not refined), HYTEG_ECUDA (launch failure). */
+int hyteg_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y,
+                void* stream);
+
+/* hyteg_apply with CUDA events (cudaEvent_t as void*, each may be NULL)
+ * recorded on `stream` before the macro-interior kernel (ev_begin), between
+ * it and the interface kernel (ev_mid) and after the interface kernel
+ * (ev_end), so a caller can time each kernel on the launching stream.  The
+ * events must have been created by the caller on the mesh's device.
+ * Errors as hyteg_apply. */
+int hyteg_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y,
+                      void* stream, void* ev_begin, void* ev_mid, void* ev_end);
+
+/* The same product with HOST vectors: copies x_host to device staging
+ * buffers owned by the mesh (allocated on first use, grown as needed, freed by
+ * hyteg_mesh_destroy), applies, copies the result into y_host and
+ * synchronises `stream`.  x_host, y_host: [n_slots] elements of dtype; pinned
+ * memory gives full copy bandwidth.  Errors as hyteg_apply, plus HYTEG_ENOMEM. */
+int hyteg_apply_host(hyteg_mesh* mesh, int level, int dtype, const void* x_host, void* y_host,
+                     void* stream);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char* hyteg_last_error(void);
+
+/* Library version string. */
+const char* hyteg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYTEG_H */

@@ -1,0 +1,222 @@
+// The C ABI of libhyteg.so (declared in include/hyteg.h): argument checks,
+// error codes and the launch sequence of one operator apply.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/hyteg.h"
+#include "hyteg_internal.h"
+
+struct hyteg_mesh {
+  hyteg::Mesh m;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(HYTEG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t elem_size(int dtype) { return dtype == HYTEG_F32 ? 4 : 8; }
+
+bool valid_dtype(int dtype) { return dtype == HYTEG_F64 || dtype == HYTEG_F32 || dtype == HYTEG_F64_IEEE; }
+
+int check_level(const hyteg_mesh* mesh, int level) {
+  if (!mesh) return fail(HYTEG_EINVAL, "mesh is NULL");
+  if (level < 0) return fail(HYTEG_EINVAL, "level < 0");
+  if (level > mesh->m.max_level)
+    return fail(HYTEG_ESTATE, "level " + std::to_string(level) + " not refined (max " +
+                                  std::to_string(mesh->m.max_level) + ")");
+  return HYTEG_OK;
+}
+
+// Host-only queries need no refined device tables.
+int check_host_level(const hyteg_mesh* mesh, int level) {
+  if (!mesh) return fail(HYTEG_EINVAL, "mesh is NULL");
+  if (level < 0 || level > 15) return fail(HYTEG_EINVAL, "level must be in 0..15");
+  return HYTEG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hyteg_mesh_create(int dim, int64_t n_verts, const double* coords, int64_t n_cells, const int64_t* cells,
+                      int bc, hyteg_mesh** out) {
+  if (!out) return fail(HYTEG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fail(HYTEG_EINVAL, "dim must be 2 or 3");
+  if (n_verts < dim + 1 || n_cells < 1) return fail(HYTEG_EINVAL, "too few vertices or cells");
+  if (n_cells > (int64_t(1) << 30) || n_verts > (int64_t(1) << 30)) return fail(HYTEG_EINVAL, "mesh too large");
+  if (!coords || !cells) return fail(HYTEG_EINVAL, "coords or cells is NULL");
+  if (bc != HYTEG_BC_NONE && bc != HYTEG_BC_DIRICHLET) return fail(HYTEG_EINVAL, "unknown bc");
+  hyteg_mesh* h = new (std::nothrow) hyteg_mesh();
+  if (!h) return fail(HYTEG_ENOMEM, "host allocation failed");
+  try {
+    h->m.dim = dim;
+    h->m.bc = bc;
+    h->m.n_verts = n_verts;
+    h->m.n_cells = n_cells;
+    h->m.coords.assign(coords, coords + n_verts * dim);
+    h->m.cells.assign(cells, cells + n_cells * (dim + 1));
+    const std::string err = hyteg::build_topology(h->m);
+    if (!err.empty()) {
+      delete h;
+      return fail(HYTEG_EMESH, err);
+    }
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return fail(HYTEG_ENOMEM, "host allocation failed");
+  }
+  *out = h;
+  return HYTEG_OK;
+}
+
+int hyteg_mesh_refine(hyteg_mesh* mesh, int max_level) {
+  if (!mesh) return fail(HYTEG_EINVAL, "mesh is NULL");
+  if (max_level < 0 || max_level > 15) return fail(HYTEG_EINVAL, "max_level must be in 0..15");
+  hyteg::Mesh& m = mesh->m;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (m.device >= 0 && m.device != dev) return fail(HYTEG_ESTATE, "refine called on a different device");
+  try {
+    if (!m.d_prims) {
+      e = cudaMalloc((void**)&m.d_prims, m.prims.size() * sizeof(hyteg::Prim));
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      e = cudaMemcpy(m.d_prims, m.prims.data(), m.prims.size() * sizeof(hyteg::Prim), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+      e = cudaMalloc((void**)&m.d_incs, m.incs.size() * sizeof(hyteg::Inc));
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      e = cudaMemcpy(m.d_incs, m.incs.data(), m.incs.size() * sizeof(hyteg::Inc), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+      m.device = dev;
+    }
+    for (int l = m.max_level + 1; l <= max_level; ++l) {
+      hyteg::LevelDev L;
+      const std::string err = hyteg::build_level(m, l, L);
+      if (!err.empty()) {
+        hyteg::free_level(L);
+        return fail(HYTEG_ECUDA, err);
+      }
+      m.levels.push_back(L);
+      m.max_level = l;
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(HYTEG_ENOMEM, "host allocation failed");
+  }
+  return HYTEG_OK;
+}
+
+void hyteg_mesh_destroy(hyteg_mesh* mesh) {
+  if (!mesh) return;
+  hyteg::Mesh& m = mesh->m;
+  if (m.device >= 0) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(m.device);
+    cudaDeviceSynchronize();
+    for (auto& L : m.levels) hyteg::free_level(L);
+    cudaFree(m.d_prims);
+    cudaFree(m.d_incs);
+    cudaFree(m.stage_x);
+    cudaFree(m.stage_y);
+    cudaSetDevice(cur);
+  }
+  delete mesh;
+}
+
+int hyteg_num_slots(const hyteg_mesh* mesh, int level, int64_t* n_slots, int64_t* n_global) {
+  if (int r = check_host_level(mesh, level)) return r;
+  if (n_slots) *n_slots = mesh->m.n_cells * hyteg::slots_per_macro(mesh->m.dim, level);
+  if (n_global) *n_global = hyteg::n_global_dofs(mesh->m, level);
+  return HYTEG_OK;
+}
+
+int hyteg_dof_map(const hyteg_mesh* mesh, int level, int64_t* global_id) {
+  if (int r = check_host_level(mesh, level)) return r;
+  if (!global_id) return fail(HYTEG_EINVAL, "global_id is NULL");
+  try {
+    hyteg::compute_dof_map(mesh->m, level, global_id);
+  } catch (const std::exception& ex) {
+    return fail(HYTEG_EINVAL, ex.what());
+  }
+  return HYTEG_OK;
+}
+
+int hyteg_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream,
+                      void* ev_begin, void* ev_mid, void* ev_end) {
+  if (int r = check_level(mesh, level)) return r;
+  if (!valid_dtype(dtype)) return fail(HYTEG_EINVAL, "unknown dtype");
+  if (!x || !y) return fail(HYTEG_EINVAL, "x or y is NULL");
+  const hyteg::Mesh& m = mesh->m;
+  const size_t bytes = size_t(m.n_cells) * size_t(hyteg::slots_per_macro(m.dim, level)) * elem_size(dtype);
+  const char* xb = static_cast<const char*>(x);
+  const char* yb = static_cast<const char*>(y);
+  if (xb < yb + bytes && yb < xb + bytes) return fail(HYTEG_EINVAL, "x and y overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const hyteg::LevelDev& L = m.levels[level];
+  cudaError_t e;
+  if (ev_begin && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), s)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventRecord");
+  e = m.dim == 2 ? hyteg::launch_interior2d(dtype, L, m.n_cells, x, y, s)
+                 : hyteg::launch_interior3d(dtype, L, m.n_cells, x, y, s);
+  if (e != cudaSuccess) return cuda_fail(e, "interior kernel launch");
+  if (ev_mid && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_mid), s)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventRecord");
+  e = hyteg::launch_interface(dtype, m.dim, m, L, x, y, s);
+  if (e != cudaSuccess) return cuda_fail(e, "interface kernel launch");
+  if (ev_end && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_end), s)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventRecord");
+  return HYTEG_OK;
+}
+
+int hyteg_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream) {
+  return hyteg_apply_timed(mesh, level, dtype, x, y, stream, nullptr, nullptr, nullptr);
+}
+
+int hyteg_apply_host(hyteg_mesh* mesh, int level, int dtype, const void* x_host, void* y_host, void* stream) {
+  if (int r = check_level(mesh, level)) return r;
+  if (!valid_dtype(dtype)) return fail(HYTEG_EINVAL, "unknown dtype");
+  if (!x_host || !y_host) return fail(HYTEG_EINVAL, "x_host or y_host is NULL");
+  hyteg::Mesh& m = mesh->m;
+  const size_t bytes = size_t(m.n_cells) * size_t(hyteg::slots_per_macro(m.dim, level)) * elem_size(dtype);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (m.stage_bytes < bytes) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    cudaFree(m.stage_x);
+    cudaFree(m.stage_y);
+    m.stage_x = m.stage_y = nullptr;
+    m.stage_bytes = 0;
+    if (cudaMalloc(&m.stage_x, bytes) != cudaSuccess || cudaMalloc(&m.stage_y, bytes) != cudaSuccess) {
+      cudaFree(m.stage_x);
+      m.stage_x = nullptr;
+      cudaGetLastError();
+      return fail(HYTEG_ENOMEM, "device staging allocation failed");
+    }
+    m.stage_bytes = bytes;
+  }
+  e = cudaMemcpyAsync(m.stage_x, x_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+  if (int r = hyteg_apply(mesh, level, dtype, m.stage_x, m.stage_y, stream)) return r;
+  e = cudaMemcpyAsync(y_host, m.stage_y, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  return HYTEG_OK;
+}
+
+const char* hyteg_last_error(void) { return g_last_error.c_str(); }
+
+const char* hyteg_version(void) { return "hyteg-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

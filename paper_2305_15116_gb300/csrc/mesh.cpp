@@ -1,0 +1,487 @@
+// Host mesh module: coarse topology, uniform refinement bookkeeping, the
+// per-macro constant stencils and the kernels' work lists.
+//
+// Sec. 1.2 of the paper: the coarse mesh is unstructured, every macro is
+// refined uniformly, and inside a macro all rows of the matrix are the same
+// stencil because the refinement is affine.  The stencil of a macro is the sum
+// of the P1 element matrices of the micro-elements around a point; this file
+// computes it once per macro and level, together with the partial stencils of
+// points on the macro's own edges/faces/vertices (only the micro-elements of
+// this macro), which the interface kernel sums over all incident macros.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <numeric>
+
+#include "hyteg_internal.h"
+
+namespace hyteg {
+
+namespace {
+
+const int OFF2[NW2][2] = {{0, -1}, {1, -1}, {-1, 0}, {0, 0}, {1, 0}, {-1, 1}, {0, 1}};
+const int OFF3[NW3][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                          {1, -1, 0}, {-1, 1, 0},  {0, 0, 1},  {-1, 0, 1},  {0, -1, 1},
+                          {1, -1, 1}, {0, 0, -1},  {1, 0, -1}, {0, 1, -1},  {-1, 1, -1}};
+
+int find_off2(int dx, int dy) {
+  for (int k = 0; k < NW2; ++k)
+    if (OFF2[k][0] == dx && OFF2[k][1] == dy) return k;
+  return -1;
+}
+int find_off3(int dx, int dy, int dz) {
+  for (int k = 0; k < NW3; ++k)
+    if (OFF3[k][0] == dx && OFF3[k][1] == dy && OFF3[k][2] == dz) return k;
+  return -1;
+}
+
+// Micro-element types as vertex offsets in the macro's index space.
+// 2D: the "up" and "down" triangles of the regular refinement.
+const int ELEM2[2][3][2] = {{{0, 0}, {1, 0}, {0, 1}}, {{1, 0}, {0, 1}, {1, 1}}};
+
+// 3D: the Kuhn simplices.  In the coordinates u = (x+y+z, y+z, z) the unit
+// cube splits into six simplices a, a+e_p, a+e_p+e_q, a+(1,1,1), one per axis
+// permutation (p,q,r).  Mapped back (x = u1-u2, y = u2-u3, z = u3) they tile a
+// refined macro-tet with n^3 elements.
+void kuhn_types(int out[6][4][3]) {
+  int perm[3] = {0, 1, 2};
+  int t = 0;
+  do {
+    int u[4][3] = {{0, 0, 0}};
+    for (int s = 1; s < 4; ++s) {
+      for (int c = 0; c < 3; ++c) u[s][c] = u[s - 1][c];
+      u[s][perm[s - 1]] += 1;
+    }
+    for (int s = 0; s < 4; ++s) {
+      out[t][s][0] = u[s][0] - u[s][1];
+      out[t][s][1] = u[s][1] - u[s][2];
+      out[t][s][2] = u[s][2];
+    }
+    ++t;
+  } while (std::next_permutation(perm, perm + 3));
+}
+
+// P1 Laplace element matrix of a triangle by the cotangent formula: the
+// coupling of vertices i and j is -cot(angle at the third vertex k) / 2 and
+// every row sums to zero.
+void tri_stiffness(const double P[3][2], double K[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) K[i][j] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const int i = (k + 1) % 3, j = (k + 2) % 3;
+    const double ax = P[i][0] - P[k][0], ay = P[i][1] - P[k][1];
+    const double bx = P[j][0] - P[k][0], by = P[j][1] - P[k][1];
+    const double cot = (ax * bx + ay * by) / std::fabs(ax * by - ay * bx);
+    K[i][j] = K[j][i] = -0.5 * cot;
+  }
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j)
+      if (j != i) s += K[i][j];
+    K[i][i] = -s;
+  }
+}
+
+// P1 Laplace element matrix of a tetrahedron: K_ab = |T| grad(l_a).grad(l_b),
+// barycentric gradients from the inverse of the edge matrix (adjugate / det).
+void tet_stiffness(const double P[4][3], double K[4][4]) {
+  double J[3][3];  // columns: P1-P0, P2-P0, P3-P0
+  for (int c = 0; c < 3; ++c)
+    for (int r = 0; r < 3; ++r) J[r][c] = P[c + 1][r] - P[0][r];
+  const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  // rows of J^{-1} are the gradients of l_1, l_2, l_3
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  double g[4][3];
+  for (int c = 0; c < 3; ++c) {
+    g[1][c] = inv[0][c];
+    g[2][c] = inv[1][c];
+    g[3][c] = inv[2][c];
+    g[0][c] = -(inv[0][c] + inv[1][c] + inv[2][c]);
+  }
+  const double vol = std::fabs(det) / 6.0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) K[a][b] = vol * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
+}
+
+// Does an offset d from a point of boundary class `cls` stay inside the macro?
+// 2D class bits: 0 x=0, 1 y=0, 2 x+y=n.  3D: 0 x=0, 1 y=0, 2 z=0, 3 x+y+z=n.
+bool inside2(int cls, int dx, int dy) {
+  if ((cls & 1) && dx < 0) return false;
+  if ((cls & 2) && dy < 0) return false;
+  if ((cls & 4) && dx + dy > 0) return false;
+  return true;
+}
+bool inside3(int cls, int dx, int dy, int dz) {
+  if ((cls & 1) && dx < 0) return false;
+  if ((cls & 2) && dy < 0) return false;
+  if ((cls & 4) && dz < 0) return false;
+  if ((cls & 8) && dx + dy + dz > 0) return false;
+  return true;
+}
+
+template <class T>
+std::string upload(T** dptr, const std::vector<T>& h) {
+  if (h.empty()) {
+    *dptr = nullptr;
+    return "";
+  }
+  cudaError_t e = cudaMalloc((void**)dptr, h.size() * sizeof(T));
+  if (e != cudaSuccess) return std::string("cudaMalloc: ") + cudaGetErrorString(e);
+  e = cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return std::string("cudaMemcpy: ") + cudaGetErrorString(e);
+  return "";
+}
+
+}  // namespace
+
+int64_t slots_per_macro(int dim, int level) {
+  const int64_t n = int64_t(1) << level;
+  return dim == 2 ? (n + 1) * (n + 2) / 2 : (n + 1) * (n + 2) * (n + 3) / 6;
+}
+
+int64_t n_global_dofs(const Mesh& m, int level) {
+  const int64_t n = int64_t(1) << level;
+  const int64_t ne = std::max<int64_t>(n - 1, 0);
+  const int64_t nf = std::max<int64_t>((n - 1) * (n - 2) / 2, 0);
+  const int64_t nc = m.dim == 2 ? nf : std::max<int64_t>((n - 1) * (n - 2) * (n - 3) / 6, 0);
+  return m.n_verts + m.n_edges * ne + (m.dim == 3 ? m.n_faces * nf : 0) + m.n_cells * nc;
+}
+
+std::string build_topology(Mesh& m) {
+  const int d = m.dim;
+  const int nv = d + 1;
+  // geometry check: no degenerate cell
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    const int64_t* cv = &m.cells[c * nv];
+    for (int i = 0; i < nv; ++i) {
+      if (cv[i] < 0 || cv[i] >= m.n_verts) return "cell vertex id out of range";
+      for (int j = 0; j < i; ++j)
+        if (cv[i] == cv[j]) return "cell with repeated vertex";
+    }
+    double vol;
+    if (d == 2) {
+      const double* p0 = &m.coords[cv[0] * 2];
+      const double* p1 = &m.coords[cv[1] * 2];
+      const double* p2 = &m.coords[cv[2] * 2];
+      vol = (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p1[1] - p0[1]) * (p2[0] - p0[0]);
+    } else {
+      double J[3][3];
+      for (int c2 = 0; c2 < 3; ++c2)
+        for (int r = 0; r < 3; ++r) J[r][c2] = m.coords[cv[c2 + 1] * 3 + r] - m.coords[cv[0] * 3 + r];
+      vol = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    }
+    if (!(std::fabs(vol) > 0.0) || !std::isfinite(vol)) return "degenerate (zero-volume) cell";
+  }
+  // unique edges and faces
+  std::map<std::pair<int64_t, int64_t>, int64_t> emap;
+  std::map<std::array<int64_t, 3>, int64_t> fmap;
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    const int64_t* cv = &m.cells[c * nv];
+    for (int i = 0; i < nv; ++i)
+      for (int j = i + 1; j < nv; ++j) emap[{std::min(cv[i], cv[j]), std::max(cv[i], cv[j])}] = 0;
+    if (d == 3)
+      for (int i = 0; i < 4; ++i)
+        for (int j = i + 1; j < 4; ++j)
+          for (int k = j + 1; k < 4; ++k) {
+            std::array<int64_t, 3> t = {cv[i], cv[j], cv[k]};
+            std::sort(t.begin(), t.end());
+            fmap[t] = 0;
+          }
+  }
+  m.edges.clear();
+  int64_t idx = 0;
+  for (auto& kv : emap) {
+    kv.second = idx++;
+    m.edges.push_back(kv.first.first);
+    m.edges.push_back(kv.first.second);
+  }
+  m.n_edges = idx;
+  m.faces.clear();
+  idx = 0;
+  for (auto& kv : fmap) {
+    kv.second = idx++;
+    for (int i = 0; i < 3; ++i) m.faces.push_back(kv.first[i]);
+  }
+  m.n_faces = idx;
+
+  // incidences, ascending cell id
+  std::vector<std::vector<Inc>> vinc(m.n_verts), einc(m.n_edges), finc(m.n_faces);
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    const int64_t* cv = &m.cells[c * nv];
+    auto corner_of = [&](int64_t v) {
+      for (int i = 0; i < nv; ++i)
+        if (cv[i] == v) return i;
+      return -1;
+    };
+    for (int i = 0; i < nv; ++i) vinc[cv[i]].push_back(Inc{int(c), {i, -1, -1}});
+    for (int i = 0; i < nv; ++i)
+      for (int j = i + 1; j < nv; ++j) {
+        const int64_t lo = std::min(cv[i], cv[j]), hi = std::max(cv[i], cv[j]);
+        einc[emap[{lo, hi}]].push_back(Inc{int(c), {corner_of(lo), corner_of(hi), -1}});
+      }
+    if (d == 3)
+      for (int i = 0; i < 4; ++i)
+        for (int j = i + 1; j < 4; ++j)
+          for (int k = j + 1; k < 4; ++k) {
+            std::array<int64_t, 3> t = {cv[i], cv[j], cv[k]};
+            std::sort(t.begin(), t.end());
+            finc[fmap[t]].push_back(Inc{int(c), {corner_of(t[0]), corner_of(t[1]), corner_of(t[2])}});
+          }
+  }
+  // conformity and the domain boundary: a facet (edge in 2D, face in 3D)
+  // belongs to one cell (boundary) or two (interior)
+  m.vertex_bnd.assign(m.n_verts, 0);
+  m.edge_bnd.assign(m.n_edges, 0);
+  m.face_bnd.assign(m.n_faces, 0);
+  if (d == 2) {
+    for (int64_t e = 0; e < m.n_edges; ++e) {
+      const size_t k = einc[e].size();
+      if (k < 1 || k > 2) return "non-conforming mesh: an edge is shared by more than two triangles";
+      if (k == 1 && m.bc == 1) {
+        m.edge_bnd[e] = 1;
+        m.vertex_bnd[m.edges[2 * e]] = 1;
+        m.vertex_bnd[m.edges[2 * e + 1]] = 1;
+      }
+    }
+  } else {
+    std::map<std::pair<int64_t, int64_t>, int64_t>& em = emap;
+    for (int64_t f = 0; f < m.n_faces; ++f) {
+      const size_t k = finc[f].size();
+      if (k < 1 || k > 2) return "non-conforming mesh: a face is shared by more than two tetrahedra";
+      if (k == 1 && m.bc == 1) {
+        m.face_bnd[f] = 1;
+        const int64_t* fv = &m.faces[3 * f];
+        for (int i = 0; i < 3; ++i) m.vertex_bnd[fv[i]] = 1;
+        for (int i = 0; i < 3; ++i)
+          for (int j = i + 1; j < 3; ++j) m.edge_bnd[em[{fv[i], fv[j]}]] = 1;
+      }
+    }
+  }
+  // interface primitives
+  m.prims.clear();
+  m.incs.clear();
+  auto add = [&](int type, int bnd, const std::vector<Inc>& inc) {
+    Prim p{type, bnd, int(m.incs.size()), int(inc.size())};
+    m.prims.push_back(p);
+    m.incs.insert(m.incs.end(), inc.begin(), inc.end());
+  };
+  for (int64_t v = 0; v < m.n_verts; ++v) {
+    if (vinc[v].empty()) return "coarse vertex not used by any cell";
+    add(0, m.vertex_bnd[v], vinc[v]);
+  }
+  for (int64_t e = 0; e < m.n_edges; ++e) add(1, m.edge_bnd[e], einc[e]);
+  for (int64_t f = 0; f < m.n_faces; ++f) add(2, m.face_bnd[f], finc[f]);
+  return "";
+}
+
+void free_level(LevelDev& L) {
+  cudaFree(L.st64);
+  cudaFree(L.st32);
+  cudaFree(L.st_hi);
+  cudaFree(L.st_lo);
+  cudaFree(L.tiles);
+  cudaFree(L.items);
+  L = LevelDev{};
+}
+
+std::string build_level(Mesh& m, int level, LevelDev& L) {
+  const int d = m.dim;
+  const int nv = d + 1;
+  const int n = 1 << level;
+  L.level = level;
+  L.n = n;
+  L.slots_per_macro = slots_per_macro(d, level);
+  const int ncls = d == 2 ? NCLS2 : NCLS3;
+  const int nw = d == 2 ? NW2 : NW3;
+
+  // ---- class stencils [cell][class][weight] ------------------------------
+  std::vector<double> st(size_t(m.n_cells) * ncls * nw, 0.0);
+  int kt[6][4][3];
+  kuhn_types(kt);
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    const int64_t* cv = &m.cells[c * nv];
+    double* W = &st[size_t(c) * ncls * nw];
+    if (d == 2) {
+      // micro-element geometry: P(q) = (q_x (v1-v0) + q_y (v2-v0)) / n
+      double M[2][2];
+      for (int r = 0; r < 2; ++r) {
+        M[r][0] = (m.coords[cv[1] * 2 + r] - m.coords[cv[0] * 2 + r]) / n;
+        M[r][1] = (m.coords[cv[2] * 2 + r] - m.coords[cv[0] * 2 + r]) / n;
+      }
+      double K[2][3][3];
+      for (int t = 0; t < 2; ++t) {
+        double P[3][2];
+        for (int s = 0; s < 3; ++s)
+          for (int r = 0; r < 2; ++r) P[s][r] = M[r][0] * ELEM2[t][s][0] + M[r][1] * ELEM2[t][s][1];
+        tri_stiffness(P, K[t]);
+      }
+      for (int cls = 0; cls < ncls; ++cls)
+        for (int t = 0; t < 2; ++t)
+          for (int r = 0; r < 3; ++r) {  // the point is vertex r of the element
+            bool ok = true;
+            for (int s = 0; s < 3; ++s)
+              ok = ok && inside2(cls, ELEM2[t][s][0] - ELEM2[t][r][0], ELEM2[t][s][1] - ELEM2[t][r][1]);
+            if (!ok) continue;
+            for (int s = 0; s < 3; ++s) {
+              const int k = find_off2(ELEM2[t][s][0] - ELEM2[t][r][0], ELEM2[t][s][1] - ELEM2[t][r][1]);
+              W[cls * nw + k] += K[t][r][s];
+            }
+          }
+    } else {
+      double M[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int j = 0; j < 3; ++j) M[r][j] = (m.coords[cv[j + 1] * 3 + r] - m.coords[cv[0] * 3 + r]) / n;
+      double K[6][4][4];
+      for (int t = 0; t < 6; ++t) {
+        double P[4][3];
+        for (int s = 0; s < 4; ++s)
+          for (int r = 0; r < 3; ++r)
+            P[s][r] = M[r][0] * kt[t][s][0] + M[r][1] * kt[t][s][1] + M[r][2] * kt[t][s][2];
+        tet_stiffness(P, K[t]);
+      }
+      for (int cls = 0; cls < ncls; ++cls)
+        for (int t = 0; t < 6; ++t)
+          for (int r = 0; r < 4; ++r) {
+            bool ok = true;
+            for (int s = 0; s < 4; ++s)
+              ok = ok && inside3(cls, kt[t][s][0] - kt[t][r][0], kt[t][s][1] - kt[t][r][1], kt[t][s][2] - kt[t][r][2]);
+            if (!ok) continue;
+            for (int s = 0; s < 4; ++s) {
+              const int k = find_off3(kt[t][s][0] - kt[t][r][0], kt[t][s][1] - kt[t][r][1], kt[t][s][2] - kt[t][r][2]);
+              if (k < 0) return "internal: Kuhn edge outside the 15-point stencil";
+              W[cls * nw + k] += K[t][r][s];
+            }
+          }
+    }
+  }
+  std::vector<float> st32(st.size()), sth(st.size()), stl(st.size());
+  for (size_t i = 0; i < st.size(); ++i) {
+    st32[i] = float(st[i]);
+    sth[i] = float(st[i]);
+    stl[i] = float(st[i] - double(sth[i]));
+  }
+
+  // ---- macro-interior work list: strips of 30 columns x chunks of rows ----
+  // A warp loads 32 consecutive columns and writes the 30 inner ones.
+  constexpr int TW = 30, TH = 64;
+  std::vector<int4> tiles;
+  if (d == 2) {
+    for (int x0 = 1; x0 <= n - 2; x0 += TW) {
+      const int ymax = n - 1 - x0;
+      for (int y0 = 1; y0 <= ymax; y0 += TH) tiles.push_back(make_int4(x0, y0, std::min(y0 + TH, ymax + 1), 0));
+    }
+  } else {
+    for (int z = 1; z <= n - 3; ++z)
+      for (int x0 = 1; x0 <= n - 2 - z; x0 += TW) {
+        const int ymax = n - 1 - z - x0;
+        for (int y0 = 1; y0 <= ymax; y0 += TH) tiles.push_back(make_int4(x0, y0, std::min(y0 + TH, ymax + 1), z));
+      }
+  }
+  // rows of neighbouring strips run side by side, so halo rows hit in L2
+  std::stable_sort(tiles.begin(), tiles.end(), [](const int4& a, const int4& b) {
+    if (a.w != b.w) return a.w < b.w;
+    if (a.y != b.y) return a.y < b.y;
+    return a.x < b.x;
+  });
+  L.n_tiles = int(tiles.size());
+
+  // ---- interface work list: (prim, b, a0, a1), at most 128 points each ----
+  constexpr int IB = 128;
+  std::vector<int4> items;
+  for (size_t p = 0; p < m.prims.size(); ++p) {
+    const Prim& pr = m.prims[p];
+    if (pr.type == 0) {
+      items.push_back(make_int4(int(p), 0, 0, 1));
+    } else if (pr.type == 1) {
+      for (int a0 = 1; a0 <= n - 1; a0 += IB) items.push_back(make_int4(int(p), 0, a0, std::min(a0 + IB, n)));
+    } else {
+      for (int b = 1; b <= n - 2; ++b)
+        for (int a0 = 1; a0 <= n - 1 - b; a0 += IB)
+          items.push_back(make_int4(int(p), b, a0, std::min(a0 + IB, n - b)));
+    }
+  }
+  L.n_items = int(items.size());
+
+  std::string err;
+  if (!(err = upload(&L.st64, st)).empty()) return err;
+  if (!(err = upload(&L.st32, st32)).empty()) return err;
+  if (!(err = upload(&L.st_hi, sth)).empty()) return err;
+  if (!(err = upload(&L.st_lo, stl)).empty()) return err;
+  if (!(err = upload(&L.tiles, tiles)).empty()) return err;
+  if (!(err = upload(&L.items, items)).empty()) return err;
+  return "";
+}
+
+void compute_dof_map(const Mesh& m, int level, int64_t* gid) {
+  const int d = m.dim;
+  const int nv = d + 1;
+  const int64_t n = int64_t(1) << level;
+  const int64_t ne = std::max<int64_t>(n - 1, 0);
+  const int64_t nf = std::max<int64_t>((n - 1) * (n - 2) / 2, 0);
+  const int64_t nc = d == 2 ? nf : std::max<int64_t>((n - 1) * (n - 2) * (n - 3) / 6, 0);
+  const int64_t base_e = m.n_verts;
+  const int64_t base_f = base_e + m.n_edges * ne;
+  const int64_t base_c = base_f + (d == 3 ? m.n_faces * nf : 0);
+  const int64_t S = slots_per_macro(d, level);
+
+  std::map<std::pair<int64_t, int64_t>, int64_t> emap;
+  for (int64_t e = 0; e < m.n_edges; ++e) emap[{m.edges[2 * e], m.edges[2 * e + 1]}] = e;
+  std::map<std::array<int64_t, 3>, int64_t> fmap;
+  for (int64_t f = 0; f < m.n_faces; ++f) fmap[{m.faces[3 * f], m.faces[3 * f + 1], m.faces[3 * f + 2]}] = f;
+
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    const int64_t* cv = &m.cells[c * nv];
+    int64_t* out = gid + c * S;
+    int64_t slot = 0, rank = 0;
+    auto classify = [&](const int64_t w[4]) -> int64_t {
+      int idx[4], k = 0;
+      for (int i = 0; i < nv; ++i)
+        if (w[i] > 0) idx[k++] = i;
+      if (k == 1) return cv[idx[0]];
+      if (k == 2) {
+        const int64_t a = cv[idx[0]], b = cv[idx[1]];
+        const int64_t lo = std::min(a, b), hi = std::max(a, b);
+        const int64_t khi = (a == hi) ? w[idx[0]] : w[idx[1]];
+        return base_e + emap.at({lo, hi}) * ne + khi - 1;
+      }
+      if (k == 3 && d == 3) {
+        std::array<std::pair<int64_t, int64_t>, 3> g = {{{cv[idx[0]], w[idx[0]]}, {cv[idx[1]], w[idx[1]]},
+                                                        {cv[idx[2]], w[idx[2]]}}};
+        std::sort(g.begin(), g.end());
+        const int64_t f = fmap.at({g[0].first, g[1].first, g[2].first});
+        const int64_t a = g[1].second, b = g[2].second;
+        return base_f + f * nf + (b - 1) * (n - 1) - ((b - 1) * b) / 2 + (a - 1);
+      }
+      return base_c + c * nc + (rank++);
+    };
+    if (d == 2) {
+      for (int64_t y = 0; y <= n; ++y)
+        for (int64_t x = 0; x <= n - y; ++x) {
+          const int64_t w[4] = {n - x - y, x, y, 0};
+          out[slot++] = classify(w);
+        }
+    } else {
+      for (int64_t z = 0; z <= n; ++z)
+        for (int64_t y = 0; y <= n - z; ++y)
+          for (int64_t x = 0; x <= n - z - y; ++x) {
+            const int64_t w[4] = {n - x - y - z, x, y, z};
+            out[slot++] = classify(w);
+          }
+    }
+  }
+}
+
+}  // namespace hyteg

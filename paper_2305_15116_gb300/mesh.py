@@ -1,0 +1,129 @@
+"""Python view of a refined mesh and its operator apply (marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi as C
+from ._capi import F64, F32, F64_IEEE, BC_NONE, BC_DIRICHLET, HytegError
+
+_ELEM = {F64: 8, F32: 4, F64_IEEE: 8}
+
+
+def version() -> str:
+    return C.lib.hyteg_version().decode()
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Mesh:
+    """A coarse simplex mesh (2D triangles / 3D tetrahedra) refined uniformly.
+
+    coords: float64 [n_verts, dim]; cells: int64 [n_cells, dim+1] (vertex
+    order inside a cell fixes the macro's local axes); bc: BC_DIRICHLET
+    (identity rows on the domain boundary) or BC_NONE.
+    """
+
+    def __init__(self, coords, cells, bc: int = BC_DIRICHLET):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        if coords.ndim != 2 or cells.ndim != 2:
+            raise ValueError("coords and cells must be 2-D arrays")
+        self.dim = int(coords.shape[1])
+        self.n_cells = int(cells.shape[0])
+        h = ctypes.c_void_p()
+        C.check(C.lib.hyteg_mesh_create(self.dim, coords.shape[0], coords.ctypes.data_as(C.c_dblp),
+                                        cells.shape[0], cells.ctypes.data_as(C.c_i64p), bc, ctypes.byref(h)),
+                "hyteg_mesh_create")
+        self._h = h
+        self.max_level = -1
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            C.lib.hyteg_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def refine(self, max_level: int) -> "Mesh":
+        C.check(C.lib.hyteg_mesh_refine(self._h, max_level), "hyteg_mesh_refine")
+        self.max_level = max(self.max_level, max_level)
+        return self
+
+    def num_slots(self, level: int):
+        """(slots in the library layout, distinct refined vertices)."""
+        ns, ng = ctypes.c_int64(), ctypes.c_int64()
+        C.check(C.lib.hyteg_num_slots(self._h, level, ctypes.byref(ns), ctypes.byref(ng)), "hyteg_num_slots")
+        return ns.value, ng.value
+
+    def dof_map(self, level: int) -> np.ndarray:
+        """Global vertex id of every slot (int64 [n_slots])."""
+        ns, _ = self.num_slots(level)
+        out = np.empty(ns, dtype=np.int64)
+        C.check(C.lib.hyteg_dof_map(self._h, level, out.ctypes.data_as(C.c_i64p)), "hyteg_dof_map")
+        return out
+
+    @staticmethod
+    def _dtype_code(t, ieee: bool) -> int:
+        import torch
+        if t.dtype == torch.float32:
+            return F32
+        if t.dtype == torch.float64:
+            return F64_IEEE if ieee else F64
+        raise TypeError(f"unsupported dtype {t.dtype}")
+
+    def apply(self, level: int, x, y, ieee: bool = False, stream=None):
+        """y = A x for device tensors x, y (float64 or float32) in slot layout.
+
+        Enqueued on `stream` (default: torch's current stream); returns y."""
+        if not (x.is_cuda and y.is_cuda):
+            raise ValueError("x and y must be CUDA tensors; use apply_host for host buffers")
+        if x.dtype != y.dtype or not x.is_contiguous() or not y.is_contiguous():
+            raise ValueError("x and y must be contiguous and of the same dtype")
+        ns, _ = self.num_slots(level)
+        if x.numel() != ns or y.numel() != ns:
+            raise ValueError(f"x and y must have {ns} elements")
+        code = self._dtype_code(x, ieee)
+        C.check(C.lib.hyteg_apply(self._h, level, code, ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+                "hyteg_apply")
+        return y
+
+    def apply_raw(self, level: int, dtype: int, x_ptr: int, y_ptr: int, stream_ptr: int) -> None:
+        """y = A x for raw device pointers (no checks beyond the library's)."""
+        C.check(C.lib.hyteg_apply(self._h, level, dtype, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
+                                  ctypes.c_void_p(stream_ptr)), "hyteg_apply")
+
+    def apply_timed(self, level: int, dtype: int, x_ptr: int, y_ptr: int, stream_ptr: int,
+                    ev_begin: int, ev_mid: int, ev_end: int) -> None:
+        """apply_raw that also records three CUDA events (raw cudaEvent_t
+        handles) around the macro-interior and the interface kernel."""
+        C.check(C.lib.hyteg_apply_timed(self._h, level, dtype, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
+                                        ctypes.c_void_p(stream_ptr), ctypes.c_void_p(ev_begin),
+                                        ctypes.c_void_p(ev_mid), ctypes.c_void_p(ev_end)), "hyteg_apply_timed")
+
+    def apply_host(self, level: int, x_host, y_host, ieee: bool = False, stream=None):
+        """y_host = A x_host for host tensors (pinned for full copy speed);
+        copies, applies and synchronises inside the library."""
+        if x_host.is_cuda or y_host.is_cuda:
+            raise ValueError("apply_host takes host tensors")
+        ns, _ = self.num_slots(level)
+        if x_host.numel() != ns or y_host.numel() != ns or x_host.dtype != y_host.dtype:
+            raise ValueError(f"x_host and y_host must have {ns} elements of one dtype")
+        code = self._dtype_code(x_host, ieee)
+        C.check(C.lib.hyteg_apply_host(self._h, level, code, ctypes.c_void_p(x_host.data_ptr()),
+                                       ctypes.c_void_p(y_host.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+                "hyteg_apply_host")
+        return y_host

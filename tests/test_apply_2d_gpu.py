@@ -1,0 +1,167 @@
+"""2D apply on the GPU against the oracle, element by element (needs a GPU)."""
+import numpy as np
+import pytest
+
+from inputs import unit_square_mesh, random_vector, workload
+import oracle
+from parity import oracle_reference, check_close, gpu_apply, TOL
+
+pytestmark = pytest.mark.gpu
+
+KINDS = ["f64", "f32", "f64_ieee"]
+
+
+def _lib():
+    import paper_2305_15116_gb300 as H
+    return H
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_two_right_triangles_level7(cuda, kind):
+    """Unit square as two macro-triangles at level 7, Dirichlet rows identity."""
+    coarse, L, seed = workload("square2_L7")
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    rm, x, y, absrow = oracle_reference(coarse, L, x_seed=seed, kind=kind)
+    smap = M.dof_map(L)
+    yg = gpu_apply(M, L, x[smap], kind)
+    check_close(yg, y[smap], absrow[smap], kind, "square2_L7")
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("L", [0, 1, 2, 3, 5, 6, 7])
+def test_jittered_32_macros(cuda, kind, L):
+    """32 jittered macros; levels span no interior (L<=1), one partial strip
+    (L=5: 30 interior columns), ragged strips and row chunks (L=6, 7)."""
+    coarse = unit_square_mesh(4, 0.15, 0)
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    rm, x, y, absrow = oracle_reference(coarse, L, x_seed=1, kind=kind)
+    smap = M.dof_map(L)
+    yg = gpu_apply(M, L, x[smap], kind)
+    check_close(yg, y[smap], absrow[smap], kind, f"jit32 L{L}")
+
+
+@pytest.mark.parametrize("kind", ["f64", "f32"])
+def test_no_dirichlet_any_vertex_order(cuda, kind):
+    """Plain stiffness (no boundary rows) on cells with permuted vertex order."""
+    coarse = unit_square_mesh(3, 0.12, 9)
+    rng = np.random.default_rng(5)
+    cells = np.array([c[rng.permutation(3)] for c in coarse.cells])
+    L = 6
+    M = _lib().Mesh(coarse.coords, cells, bc=0).refine(L)
+
+    class C:  # same coarse mesh with the permuted cells
+        coords = coarse.coords
+    C.cells = cells
+    rm, x, y, absrow = oracle_reference(C, L, bc=False, x_seed=3, kind=kind)
+    smap = M.dof_map(L)
+    yg = gpu_apply(M, L, x[smap], kind)
+    check_close(yg, y[smap], absrow[smap], kind, "permuted, no bc")
+
+
+def test_deterministic_and_stream(cuda):
+    import torch
+    coarse = unit_square_mesh(4, 0.15, 0)
+    L = 7
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    ns, ng = M.num_slots(L)
+    x = torch.from_numpy(random_vector(ng, 2)[M.dof_map(L)]).cuda()
+    y1 = torch.empty_like(x)
+    y2 = torch.empty_like(x)
+    M.apply(L, x, y1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        M.apply(L, x, y2, stream=s)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+
+
+def test_errors(cuda):
+    import torch
+    H = _lib()
+    coarse = unit_square_mesh(2, 0.1, 0)
+    M = H.Mesh(coarse.coords, coarse.cells).refine(3)
+    ns, _ = M.num_slots(3)
+    x = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    with pytest.raises(H.HytegError) as e:
+        M.apply(3, x, x)
+    assert e.value.code == -1  # x and y overlap
+    with pytest.raises(H.HytegError) as e:
+        M.apply_raw(4, H.F64, x.data_ptr(), x.data_ptr() + 8 * ns, 0)
+    assert e.value.code == -5  # level not refined
+    with pytest.raises(H.HytegError) as e:
+        M.apply_raw(3, 7, x.data_ptr(), x.data_ptr(), 0)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("kind", ["f64", "f32"])
+def test_apply_host(cuda, kind):
+    import torch
+    coarse = unit_square_mesh(4, 0.15, 0)
+    L = 6
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    rm, x, y, absrow = oracle_reference(coarse, L, x_seed=4, kind=kind)
+    smap = M.dof_map(L)
+    dt = torch.float32 if kind == "f32" else torch.float64
+    xh = torch.from_numpy(x[smap]).to(dt).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    M.apply_host(L, xh, yh)
+    check_close(yh.double().numpy(), y[smap], absrow[smap], kind, "apply_host")
+
+
+def _interface_slots(n, n_cells):
+    """Slots on macro edges of every macro (rows y=0, column x=0, hypotenuse)."""
+    S = (n + 1) * (n + 2) // 2
+    ys = np.arange(n + 1)
+    starts = ys * (n + 2) - ys * (ys + 1) // 2
+    local = np.unique(np.concatenate([np.arange(n + 1), starts, starts + (n - ys)]))
+    return (np.arange(n_cells)[:, None] * S + local[None, :]).ravel()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_full_size_sampled(cuda, kind):
+    """32 jittered macros at level 11 (67M DoFs), the benchmark's launch: every
+    slot written, copies equal, and sampled rows (interior and interface)
+    against the oracle's row-by-row evaluation."""
+    import torch
+    coarse, L, seed = workload("square32jit_L11")
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    ns, ng = M.num_slots(L)
+    smap = M.dof_map(L)
+    x = random_vector(ng, seed)
+    if kind == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    yg = gpu_apply(M, L, x[smap], kind)
+    assert np.all(np.isfinite(yg))
+    # copies of a DoF hold one value
+    order = np.argsort(smap, kind="stable")
+    sm, yo = smap[order], yg[order]
+    same = sm[1:] == sm[:-1]
+    assert np.array_equal(yo[1:][same], yo[:-1][same])
+    rm = oracle.RefinedMesh(coarse.coords, coarse.cells, L)
+    rng = np.random.default_rng(17)
+    iface = _interface_slots(rm.n, coarse.n_cells)
+    slots = np.concatenate([rng.integers(0, ns, 300), rng.choice(iface, 200, replace=False)])
+    gids = smap[slots]
+    yref = oracle.row_apply(rm, gids, x)
+    absrow = np.array([_absrow(rm, g, x) for g in gids])
+    check_close(yg[slots], yref, absrow, kind, "L11 sampled")
+
+
+def _absrow(rm, g, x):
+    """sum_j |a_gj x_j| from the oracle's micro-elements around g."""
+    from oracle.assemble import _incidences, _macro_element_matrices
+    from oracle.refine import element_offsets, in_region
+    if rm.boundary[g]:
+        return abs(x[g])
+    row = {}
+    for m, p in _incidences(rm, g):
+        for off in element_offsets(rm.dim):
+            for r in range(rm.dim + 1):
+                verts = (p - off[r])[None, :] + off
+                if not np.all(in_region(verts, rm.n)):
+                    continue
+                K = _macro_element_matrices(rm, m, verts[None])[0]
+                gv = rm.local_to_global(m, verts)
+                for j, v in zip(gv, K[r]):
+                    row[j] = row.get(j, 0.0) + v
+    return sum(abs(v * x[j]) for j, v in row.items())

@@ -1,0 +1,73 @@
+"""3D apply (15-point stencil on Kuhn-refined macro-tets) on the GPU against
+the oracle, element by element (needs a GPU)."""
+import numpy as np
+import pytest
+
+from inputs import unit_cube_kuhn_mesh, random_vector, workload
+import oracle
+from parity import oracle_reference, check_close, gpu_apply
+from test_apply_2d_gpu import _absrow
+
+pytestmark = pytest.mark.gpu
+
+KINDS = ["f64", "f32", "f64_ieee"]
+
+
+def _lib():
+    import paper_2305_15116_gb300 as H
+    return H
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("k,L", [(1, 0), (1, 1), (1, 2), (2, 2), (2, 3), (1, 4), (1, 5)])
+def test_jittered_cubes(cuda, kind, k, L):
+    """Levels 0-1 have no macro interior, 2 has one interior point per macro,
+    4-5 have ragged strips (n-2-z not a multiple of 30)."""
+    coarse = unit_cube_kuhn_mesh(k, 0.1, 0)
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    rm, x, y, absrow = oracle_reference(coarse, L, x_seed=1, kind=kind)
+    smap = M.dof_map(L)
+    yg = gpu_apply(M, L, x[smap], kind)
+    check_close(yg, y[smap], absrow[smap], kind, f"cube k{k} L{L}")
+
+
+@pytest.mark.parametrize("kind", ["f64", "f32"])
+def test_permuted_vertex_order_no_bc(cuda, kind):
+    coarse = unit_cube_kuhn_mesh(1, 0.0, 0)
+    rng = np.random.default_rng(8)
+    cells = np.array([c[rng.permutation(4)] for c in coarse.cells])
+
+    class C:
+        coords = coarse.coords
+    C.cells = cells
+    L = 4
+    M = _lib().Mesh(C.coords, cells, bc=0).refine(L)
+    rm, x, y, absrow = oracle_reference(C, L, bc=False, x_seed=2, kind=kind)
+    smap = M.dof_map(L)
+    yg = gpu_apply(M, L, x[smap], kind)
+    check_close(yg, y[smap], absrow[smap], kind, "3d permuted")
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_full_size_sampled(cuda, kind):
+    """384 jittered macro-tets at level 6 (17M DoFs), the benchmark's launch."""
+    coarse, L, seed = workload("cube384jit_L6")
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    ns, ng = M.num_slots(L)
+    smap = M.dof_map(L)
+    x = random_vector(ng, seed)
+    if kind == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    yg = gpu_apply(M, L, x[smap], kind)
+    assert np.all(np.isfinite(yg))
+    order = np.argsort(smap, kind="stable")
+    sm, yo = smap[order], yg[order]
+    same = sm[1:] == sm[:-1]
+    assert np.array_equal(yo[1:][same], yo[:-1][same])
+    rm = oracle.RefinedMesh(coarse.coords, coarse.cells, L)
+    rng = np.random.default_rng(23)
+    slots = rng.integers(0, ns, 400)
+    gids = smap[slots]
+    yref = oracle.row_apply(rm, gids, x)
+    absrow = np.array([_absrow(rm, g, x) for g in gids])
+    check_close(yg[slots], yref, absrow, kind, "L6 3D sampled")
