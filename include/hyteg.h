@@ -145,6 +145,33 @@ int hyteg_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* 
 int hyteg_apply_host(hyteg_mesh* mesh, int level, int dtype, const void* x_host, void* y_host,
                      void* stream);
 
+/* Staging limit of hyteg_apply_host_static: bytes per vector (16 MiB, i.e.
+ * 2,097,152 float64 or 4,194,304 float32 slots). */
+#define HYTEG_STATIC_STAGE_BYTES (16u << 20)
+
+/* hyteg_apply_host without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let the
+ * library call cudaMalloc — code running while its stream is captured into a
+ * CUDA graph, real-time loops that forbid allocation after start-up, and
+ * processes whose device memory is fully reserved by another allocator.
+ * x and y are staged in one fixed file-scope device array of
+ * 2 * HYTEG_STATIC_STAGE_BYTES that every GPU loading the library holds until
+ * the process exits.  Arguments and result as hyteg_apply_host; synchronises
+ * `stream` before returning.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.  The current device must be the mesh's device.
+ *  - Every call on a device shares the array and leaves its contents behind;
+ *    no part of it needs clearing, since each call overwrites all of x it
+ *    reads and all of y it returns.  Calls that overlap on the GPU (from
+ *    several host threads or streams at once) race on the array and must be
+ *    serialised by the caller.
+ *  - Vectors larger than HYTEG_STATIC_STAGE_BYTES are rejected with
+ *    HYTEG_EINVAL and a message naming the limit.
+ * Errors: as hyteg_apply_host, HYTEG_ENOMEM never. */
+int hyteg_apply_host_static(const hyteg_mesh* mesh, int level, int dtype, const void* x_host,
+                            void* y_host, void* stream);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char* hyteg_last_error(void);
 

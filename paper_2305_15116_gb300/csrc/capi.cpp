@@ -7,10 +7,6 @@
 #include "../../include/hyteg.h"
 #include "hyteg_internal.h"
 
-struct hyteg_mesh {
-  hyteg::Mesh m;
-};
-
 namespace {
 
 thread_local std::string g_last_error;
@@ -45,6 +41,8 @@ int check_host_level(const hyteg_mesh* mesh, int level) {
 }
 
 }  // namespace
+
+void hyteg::set_last_error(const std::string& msg) { g_last_error = msg; }
 
 extern "C" {
 

@@ -85,6 +85,9 @@ struct Mesh {
   size_t stage_bytes = 0;
 };
 
+// Records the message returned by hyteg_last_error() on this thread.
+void set_last_error(const std::string& msg);
+
 // ---- host mesh module (mesh.cpp) ----------------------------------------
 // Returns an error message, empty on success.
 std::string build_topology(Mesh& m);
@@ -104,3 +107,8 @@ cudaError_t launch_interface(int dtype, int dim, const Mesh& m, const LevelDev& 
                              void* y, cudaStream_t s);
 
 }  // namespace hyteg
+
+// The opaque handle of the C ABI.
+struct hyteg_mesh {
+  hyteg::Mesh m;
+};
