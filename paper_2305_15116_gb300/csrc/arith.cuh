@@ -6,15 +6,56 @@
 // The HYTEG_F64 path therefore keeps float64 vectors in memory but computes in
 // float-float arithmetic: every float64 value v is split with integer
 // instructions only into v = h + l + r, h = v truncated to 24 significant bits,
-// l = the next 23 bits (|r| <= 2^-46 |v|), products use the exact fp32 FMA
+// l = the next 23 bits (|r| <= 2^-46 |v|), products keep the exact fp32 FMA
 // product error, the high parts are summed with Knuth's TwoSum, and the result
 // h + l is rebuilt as a float64 with integer instructions and one fp64 add.
+//
+// The kernels evaluate two independent points per thread (two row streams).
+// The float-float policy packs the two points into the two halves of 64-bit
+// registers and uses Blackwell's packed f32x2 add/sub/mul/fma, which do two
+// fp32 operations per issued instruction.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <cstdint>
 
 namespace hyteg {
+
+// ---- packed fp32 pairs (sm_100+ f32x2 instructions) ------------------------
+
+typedef unsigned long long f2_t;  // low half: stream A, high half: stream B
+
+__device__ __forceinline__ f2_t f2_pack(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// Note: a packed multiply whose result feeds a packed add may be fused with it
+// by the code generator even with .rn; error-free transformations must form
+// their rounded products with scalar mul.rn.f32 (see ArF64FF).
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 
 // ---- float-float helpers ---------------------------------------------------
 
@@ -23,12 +64,13 @@ struct FF {
 };
 
 // Split a float64 into (h, l) with integer instructions only.
-// Valid for finite |v| in [2^-126, 2^127); |v| < 2^-126 gives (±0, 0);
-// the low part is dropped below 2^-80.
+// Finite |v| < 2^127: h = v truncated to 24 bits, l = the next 23 bits
+// (|v - h - l| <= 2^-46 |v|); l is dropped for |v| < 2^-80 and both parts for
+// |v| < 2^-126 (signed zero).
 __device__ __forceinline__ FF ff_split(double v) {
   const unsigned hi = (unsigned)__double2hiint(v);
   const unsigned lo = (unsigned)__double2loint(v);
-  const int e8 = (int)((hi >> 20) & 0x7FFu) - 896;  // float exponent field of v
+  const unsigned mag = hi & 0x7FFFFFFFu;
   // sign | (e - 896) << 23 | top 23 mantissa bits  (truncation)
   unsigned hb = __funnelshift_l(lo, hi - (896u << 20), 3);
   hb = (hb & 0x7FFFFFFFu) | (hi & 0x80000000u);
@@ -37,23 +79,18 @@ __device__ __forceinline__ FF ff_split(double v) {
   // their weight: 2^(exponent of v - 46), with the sign of v
   const unsigned sb = (hb & 0xFF800000u) - (46u << 23);
   FF r;
-  const bool ok = (unsigned)(e8 - 1) < 254u;
-  r.h = ok ? __uint_as_float(hb) : __uint_as_float(hi & 0x80000000u);
-  r.l = (ok && e8 >= 47) ? __fmul_rn(t, __uint_as_float(sb)) : 0.0f;
+  r.h = mag >= (897u << 20) ? __uint_as_float(hb) : __uint_as_float(hi & 0x80000000u);
+  r.l = mag >= (943u << 20) ? __fmul_rn(t, __uint_as_float(sb)) : 0.0f;
   return r;
 }
 
 // Exact float32 -> float64 with integer instructions (no conversion unit).
+// Zero maps to zero; fp32 subnormals (|f| < 2^-126) are flushed to zero.
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned a = u & 0x7FFFFFFFu;
-  unsigned hi = ((a >> 3) + (896u << 20)) | (u & 0x80000000u);
-  unsigned lo = a << 29;
-  if (a < 0x00800000u) {  // zero or subnormal -> signed zero
-    hi = u & 0x80000000u;
-    lo = 0u;
-  }
-  if (a >= 0x7F800000u) hi |= 0x7FF00000u;  // inf / nan
+  const unsigned hi = a >= 0x00800000u ? (((a >> 3) + (896u << 20)) | (u & 0x80000000u)) : (u & 0x80000000u);
+  const unsigned lo = a >= 0x00800000u ? (u << 29) : 0u;
   return __hiloint2double((int)hi, (int)lo);
 }
 
@@ -72,50 +109,94 @@ struct StencilPtr {
 };
 
 // ---- policies -------------------------------------------------------------------
-// Each policy defines the element type T in memory, the register value V of a
-// loaded point, the weight type Wt, the accumulator Acc and the operations
-// used by the kernels.  `first` starts a sum, `add` adds one weighted term.
+// A policy defines the element type T in memory, the register value V of one
+// loaded point, a pair type P2 holding the same term of the two points a
+// thread evaluates, the weight type W, the pair accumulator Acc and:
+//   load(p)            one element -> V
+//   up(v) / down(v)    the value of the lane below / above (x-1 / x+1)
+//   pair(a, b)         two V -> P2
+//   weight(st, i)      weight i of the stencil table
+//   first(acc, w, p)   acc = w * p     add(acc, w, p)   acc += w * p
+//   finish(acc, a, b)  the two results in T
 
 struct ArF32 {
   using T = float;
   using V = float;
-  using Wt = float;
-  using Acc = float;
+  using P2 = float2;
+  using W = float;
+  using Acc = float2;
   static __device__ __forceinline__ V load(const T* p) { return __ldg(p); }
+  static __device__ __forceinline__ V conv(T v) { return v; }
   static __device__ __forceinline__ V zero() { return 0.0f; }
   static __device__ __forceinline__ V up(V v) { return __shfl_up_sync(0xFFFFFFFFu, v, 1); }
   static __device__ __forceinline__ V down(V v) { return __shfl_down_sync(0xFFFFFFFFu, v, 1); }
-  static __device__ __forceinline__ Wt weight(const StencilPtr& s, int64_t i) { return __ldg(s.f + i); }
-  static __device__ __forceinline__ void first(Acc& a, Wt w, V v) { a = __fmul_rn(w, v); }
-  static __device__ __forceinline__ void add(Acc& a, Wt w, V v) { a = __fmaf_rn(w, v, a); }
-  static __device__ __forceinline__ T finish(const Acc& a) { return a; }
+  static __device__ __forceinline__ P2 pair(V a, V b) { return make_float2(a, b); }
+  static __device__ __forceinline__ W weight(const StencilPtr& s, int64_t i) { return __ldg(s.f + i); }
+  static __device__ __forceinline__ void first(Acc& a, W w, P2 v) {
+    a.x = __fmul_rn(w, v.x);
+    a.y = __fmul_rn(w, v.y);
+  }
+  static __device__ __forceinline__ void add(Acc& a, W w, P2 v) {
+    a.x = __fmaf_rn(w, v.x, a.x);
+    a.y = __fmaf_rn(w, v.y, a.y);
+  }
+  static __device__ __forceinline__ void finish(const Acc& a, T& ra, T& rb) {
+    ra = a.x;
+    rb = a.y;
+  }
+  // single-point forms (3D kernel)
+  static __device__ __forceinline__ void first1(float& a, W w, V v) { a = __fmul_rn(w, v); }
+  static __device__ __forceinline__ void add1(float& a, W w, V v) { a = __fmaf_rn(w, v, a); }
+  static __device__ __forceinline__ T finish1(float a) { return a; }
+  using Acc1 = float;
 };
 
 struct ArF64Native {
   using T = double;
   using V = double;
-  using Wt = double;
-  using Acc = double;
+  using P2 = double2;
+  using W = double;
+  using Acc = double2;
   static __device__ __forceinline__ V load(const T* p) { return __ldg(p); }
+  static __device__ __forceinline__ V conv(T v) { return v; }
   static __device__ __forceinline__ V zero() { return 0.0; }
   static __device__ __forceinline__ V up(V v) { return __shfl_up_sync(0xFFFFFFFFu, v, 1); }
   static __device__ __forceinline__ V down(V v) { return __shfl_down_sync(0xFFFFFFFFu, v, 1); }
-  static __device__ __forceinline__ Wt weight(const StencilPtr& s, int64_t i) { return __ldg(s.d + i); }
-  static __device__ __forceinline__ void first(Acc& a, Wt w, V v) { a = __dmul_rn(w, v); }
-  static __device__ __forceinline__ void add(Acc& a, Wt w, V v) { a = __fma_rn(w, v, a); }
-  static __device__ __forceinline__ T finish(const Acc& a) { return a; }
+  static __device__ __forceinline__ P2 pair(V a, V b) { return make_double2(a, b); }
+  static __device__ __forceinline__ W weight(const StencilPtr& s, int64_t i) { return __ldg(s.d + i); }
+  static __device__ __forceinline__ void first(Acc& a, W w, P2 v) {
+    a.x = __dmul_rn(w, v.x);
+    a.y = __dmul_rn(w, v.y);
+  }
+  static __device__ __forceinline__ void add(Acc& a, W w, P2 v) {
+    a.x = __fma_rn(w, v.x, a.x);
+    a.y = __fma_rn(w, v.y, a.y);
+  }
+  static __device__ __forceinline__ void finish(const Acc& a, T& ra, T& rb) {
+    ra = a.x;
+    rb = a.y;
+  }
+  static __device__ __forceinline__ void first1(double& a, W w, V v) { a = __dmul_rn(w, v); }
+  static __device__ __forceinline__ void add1(double& a, W w, V v) { a = __fma_rn(w, v, a); }
+  static __device__ __forceinline__ T finish1(double a) { return a; }
+  using Acc1 = double;
 };
 
 struct ArF64FF {
   using T = double;
   using V = FF;
-  struct Wt {
-    float h, l;
+  struct P2 {
+    f2_t h, l;  // high parts of the two points, low parts of the two points
+  };
+  struct W {
+    f2_t h, l;     // (wh, wh), (wl, wl)
+    float h1, l1;  // scalar forms
   };
   struct Acc {
-    float s, e;
+    f2_t s, e;  // running sums of high parts and of error terms, both points
   };
   static __device__ __forceinline__ V load(const T* p) { return ff_split(__ldg(p)); }
+  static __device__ __forceinline__ V conv(T v) { return ff_split(v); }
   static __device__ __forceinline__ V zero() { return FF{0.0f, 0.0f}; }
   static __device__ __forceinline__ V up(V v) {
     return FF{__shfl_up_sync(0xFFFFFFFFu, v.h, 1), __shfl_up_sync(0xFFFFFFFFu, v.l, 1)};
@@ -123,33 +204,74 @@ struct ArF64FF {
   static __device__ __forceinline__ V down(V v) {
     return FF{__shfl_down_sync(0xFFFFFFFFu, v.h, 1), __shfl_down_sync(0xFFFFFFFFu, v.l, 1)};
   }
-  static __device__ __forceinline__ Wt weight(const StencilPtr& s, int64_t i) {
-    return Wt{__ldg(s.hi + i), __ldg(s.lo + i)};
+  static __device__ __forceinline__ P2 pair(V a, V b) { return P2{f2_pack(a.h, b.h), f2_pack(a.l, b.l)}; }
+  static __device__ __forceinline__ W weight(const StencilPtr& s, int64_t i) {
+    const float h = __ldg(s.hi + i), l = __ldg(s.lo + i);
+    return W{f2_pack(h, h), f2_pack(l, l), h, l};
   }
   // w*v = wh*vh + (wh*vl + wl*vh) + O(2^-46): the product wh*vh is kept
   // exactly as p + fma(wh, vh, -p); the small terms go to the error sum.
-  static __device__ __forceinline__ void first(Acc& a, Wt w, V v) {
-    const float p = __fmul_rn(w.h, v.h);
-    float e = __fmaf_rn(w.h, v.h, -p);
-    e = __fmaf_rn(w.h, v.l, e);
-    e = __fmaf_rn(w.l, v.h, e);
-    a.s = p;
-    a.e = e;
+  // The rounded products p are formed with scalar mul.rn.f32: a packed
+  // multiply feeding a packed add may be contracted into one fused operation
+  // by the code generator, which would break TwoSum's exactness.
+  static __device__ __forceinline__ f2_t neg_products(const W& w, const P2& v) {
+    float va, vb;
+    f2_unpack(v.h, va, vb);
+    const float nh = -w.h1;
+    return f2_pack(__fmul_rn(nh, va), __fmul_rn(nh, vb));  // -p, rounded
   }
-  static __device__ __forceinline__ void add(Acc& a, Wt w, V v) {
-    const float p = __fmul_rn(w.h, v.h);
-    const float pe = __fmaf_rn(w.h, v.h, -p);
-    // TwoSum(a.s, p): sn + err == a.s + p exactly
+  static __device__ __forceinline__ void first(Acc& a, const W& w, const P2& v) {
+    const f2_t pm = neg_products(w, v);         // -p
+    a.s = f2_sub(f2_pack(0.0f, 0.0f), pm);      // p
+    f2_t e = f2_fma(w.h, v.h, pm);              // wh*vh - p, exact
+    e = f2_fma(w.h, v.l, e);
+    a.e = f2_fma(w.l, v.h, e);
+  }
+  static __device__ __forceinline__ void add(Acc& a, const W& w, const P2& v) {
+    const f2_t pm = neg_products(w, v);         // -p
+    const f2_t pe = f2_fma(w.h, v.h, pm);       // wh*vh - p, exact
+    // TwoSum(s, p): sn + err == s + p exactly
+    const f2_t sn = f2_sub(a.s, pm);
+    const f2_t bp = f2_sub(sn, a.s);
+    const f2_t t2 = f2_sub(a.s, f2_sub(sn, bp));
+    const f2_t err = f2_sub(t2, f2_add(pm, bp));  // t2 + (p - bp)
+    a.s = sn;
+    f2_t e = f2_add(a.e, err);
+    e = f2_add(e, pe);
+    e = f2_fma(w.h, v.l, e);
+    a.e = f2_fma(w.l, v.h, e);
+  }
+  static __device__ __forceinline__ void finish(const Acc& a, T& ra, T& rb) {
+    float sa, sb, ea, eb;
+    f2_unpack(a.s, sa, sb);
+    f2_unpack(a.e, ea, eb);
+    ra = ff_join(sa, ea);
+    rb = ff_join(sb, eb);
+  }
+  // single-point forms (3D kernel)
+  struct Acc1 {
+    float s, e;
+  };
+  static __device__ __forceinline__ void first1(Acc1& a, const W& w, V v) {
+    const float p = __fmul_rn(w.h1, v.h);
+    float e = __fmaf_rn(w.h1, v.h, -p);
+    e = __fmaf_rn(w.h1, v.l, e);
+    a.e = __fmaf_rn(w.l1, v.h, e);
+    a.s = p;
+  }
+  static __device__ __forceinline__ void add1(Acc1& a, const W& w, V v) {
+    const float p = __fmul_rn(w.h1, v.h);
+    const float pe = __fmaf_rn(w.h1, v.h, -p);
     const float sn = __fadd_rn(a.s, p);
     const float bp = __fsub_rn(sn, a.s);
     const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(sn, bp)), __fsub_rn(p, bp));
     a.s = sn;
     float e = __fadd_rn(a.e, err);
     e = __fadd_rn(e, pe);
-    e = __fmaf_rn(w.h, v.l, e);
-    a.e = __fmaf_rn(w.l, v.h, e);
+    e = __fmaf_rn(w.h1, v.l, e);
+    a.e = __fmaf_rn(w.l1, v.h, e);
   }
-  static __device__ __forceinline__ T finish(const Acc& a) { return ff_join(a.s, a.e); }
+  static __device__ __forceinline__ T finish1(const Acc1& a) { return ff_join(a.s, a.e); }
 };
 
 }  // namespace hyteg

@@ -160,17 +160,12 @@ int hyteg_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* 
   const char* yb = static_cast<const char*>(y);
   if (xb < yb + bytes && yb < xb + bytes) return fail(HYTEG_EINVAL, "x and y overlap");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const hyteg::LevelDev& L = m.levels[level];
   cudaError_t e;
   if (ev_begin && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), s)) != cudaSuccess)
     return cuda_fail(e, "cudaEventRecord");
-  e = m.dim == 2 ? hyteg::launch_interior2d(dtype, L, m.n_cells, x, y, s)
-                 : hyteg::launch_interior3d(dtype, L, m.n_cells, x, y, s);
-  if (e != cudaSuccess) return cuda_fail(e, "interior kernel launch");
-  if (ev_mid && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_mid), s)) != cudaSuccess)
-    return cuda_fail(e, "cudaEventRecord");
-  e = hyteg::launch_interface(dtype, m.dim, m, L, x, y, s);
-  if (e != cudaSuccess) return cuda_fail(e, "interface kernel launch");
+  const char* what = "";
+  e = hyteg::launch_apply(m, level, dtype, x, y, s, static_cast<cudaEvent_t>(ev_mid), &what);
+  if (e != cudaSuccess) return cuda_fail(e, what);
   if (ev_end && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_end), s)) != cudaSuccess)
     return cuda_fail(e, "cudaEventRecord");
   return HYTEG_OK;

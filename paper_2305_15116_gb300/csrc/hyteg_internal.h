@@ -43,6 +43,9 @@ struct LevelDev {
   // interface work list: int4 (prim, b, a0, a1)
   int4* items = nullptr;
   int n_items = 0;
+  // 3D slab work list (levels with n <= 64): int4 (macro, z0, z1, 0)
+  int4* slabs = nullptr;
+  int n_slabs = 0;
 };
 
 // Interface primitive (coarse vertex, edge or face) and its incident cells.
@@ -105,6 +108,14 @@ cudaError_t launch_interior3d(int dtype, const LevelDev& L, int64_t n_cells, con
                               cudaStream_t s);
 cudaError_t launch_interface(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,
                              void* y, cudaStream_t s);
+cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, cudaStream_t s);
+cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,
+                                    void* y, cudaStream_t s);
+
+// The launch sequence of one apply y = A x (two kernels); `ev_mid`, when not
+// null, is recorded between them.  Returns the failing step in *what.
+cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
+                         cudaEvent_t ev_mid, const char** what);
 
 }  // namespace hyteg
 

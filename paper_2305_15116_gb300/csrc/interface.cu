@@ -131,6 +131,51 @@ __global__ void __launch_bounds__(128) k_interface(const T* __restrict__ x, T* _
   }
 }
 
+// Reduce variant: the copies already hold their macro's partial row (written
+// by the 3D slab kernel); sum them in ascending macro order and write the sum
+// into every copy.  A point with a single copy is already complete.
+template <class T, int DIM>
+__global__ void __launch_bounds__(128) k_interface_reduce(const T* __restrict__ x, T* __restrict__ y,
+                                                          const int4* __restrict__ items,
+                                                          const Prim* __restrict__ prims,
+                                                          const Inc* __restrict__ incs, int n, int64_t S) {
+  const int4 it = items[blockIdx.x];
+  const int a = it.z + threadIdx.x;
+  if (a >= it.w) return;
+  const Prim p = prims[it.x];
+  if (!p.boundary && p.inc_count == 1) return;
+  const int b = it.y;
+  int wv[3] = {0, 0, 0};
+  if (p.type == 0) {
+    wv[0] = n;
+  } else if (p.type == 1) {
+    wv[0] = n - a;
+    wv[1] = a;
+  } else {
+    wv[0] = n - a - b;
+    wv[1] = a;
+    wv[2] = b;
+  }
+  const int nverts = p.type + 1;
+  // slot of this point in the i-th incident cell
+  auto slot_of = [&](int i) -> int64_t {
+    const Inc inc = incs[p.inc_begin + i];
+    int q[3] = {0, 0, 0};
+    for (int j = 0; j < nverts; ++j) {
+      const int c = inc.corner[j];
+      if (c >= 1) q[c - 1] += wv[j];
+    }
+    return (int64_t)inc.cell * S + (DIM == 2 ? tri_slot(n, q[0], q[1]) : tet_slot(n, q[0], q[1], q[2]));
+  };
+  T acc = T(0);
+  if (p.boundary) {
+    acc = __ldg(x + slot_of(0));
+  } else {
+    for (int i = 0; i < p.inc_count; ++i) acc += y[slot_of(i)];
+  }
+  for (int i = 0; i < p.inc_count; ++i) y[slot_of(i)] = acc;
+}
+
 template <class T>
 cudaError_t launch_t(int dim, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
   if (L.n_items == 0) return cudaSuccess;
@@ -144,7 +189,48 @@ cudaError_t launch_t(int dim, const Mesh& m, const LevelDev& L, const void* x, v
   return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_reduce_t(int dim, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
+  if (L.n_items == 0) return cudaSuccess;
+  if (dim == 2)
+    k_interface_reduce<T, 2><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, m.d_incs, L.n,
+                                                        L.slots_per_macro);
+  else
+    k_interface_reduce<T, 3><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, m.d_incs, L.n,
+                                                        L.slots_per_macro);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x, void* y,
+                                    cudaStream_t s) {
+  switch (dtype) {
+    case 1:
+    case 3: return launch_reduce_t<double>(dim, m, L, x, y, s);
+    case 2: return launch_reduce_t<float>(dim, m, L, x, y, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
+                         cudaEvent_t ev_mid, const char** what) {
+  const LevelDev& L = m.levels[level];
+  cudaError_t e;
+  const bool slab = m.dim == 3 && L.n_slabs > 0;
+  *what = slab ? "3D slab kernel" : "interior kernel";
+  e = slab ? launch_slab3d(dtype, L, x, y, s)
+           : (m.dim == 2 ? launch_interior2d(dtype, L, m.n_cells, x, y, s)
+                         : launch_interior3d(dtype, L, m.n_cells, x, y, s));
+  if (e != cudaSuccess) return e;
+  if (ev_mid) {
+    *what = "cudaEventRecord";
+    e = cudaEventRecord(ev_mid, s);
+    if (e != cudaSuccess) return e;
+  }
+  *what = slab ? "interface reduce kernel" : "interface kernel";
+  return slab ? launch_interface_reduce(dtype, m.dim, m, L, x, y, s) : launch_interface(dtype, m.dim, m, L, x, y, s);
+}
 
 cudaError_t launch_interface(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x, void* y,
                              cudaStream_t s) {

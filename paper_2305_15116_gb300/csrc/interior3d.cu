@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) k_interior3d(const typename P::T* __restr
   typename P::T* __restrict__ ym = y + m * S;
 
   const int64_t wb = m * (int64_t)(NCLS3 * NW3);
-  typename P::Wt w[NW3];
+  typename P::W w[NW3];
 #pragma unroll
   for (int k = 0; k < NW3; ++k) w[k] = P::weight(st, wb + k);
 
@@ -69,25 +69,25 @@ __global__ void __launch_bounds__(256) k_interior3d(const typename P::T* __restr
     const Row<P> nxt = load_row<P>(xm, n, z, z0, r + 1, col);
     const Row<P> ucur = load_row<P>(xm, n, z + 1, zu, r, col);
     const Row<P> dnxt = load_row<P>(xm, n, z - 1, zd, r + 1, col);
-    typename P::Acc a;
-    P::first(a, w[0], cur.v);
-    P::add(a, w[1], cur.e);     // ( 1, 0, 0)
-    P::add(a, w[2], cur.w);     // (-1, 0, 0)
-    P::add(a, w[3], nxt.v);     // ( 0, 1, 0)
-    P::add(a, w[4], prev.v);    // ( 0,-1, 0)
-    P::add(a, w[5], prev.e);    // ( 1,-1, 0)
-    P::add(a, w[6], nxt.w);     // (-1, 1, 0)
-    P::add(a, w[7], ucur.v);    // ( 0, 0, 1)
-    P::add(a, w[8], ucur.w);    // (-1, 0, 1)
-    P::add(a, w[9], uprev.v);   // ( 0,-1, 1)
-    P::add(a, w[10], uprev.e);  // ( 1,-1, 1)
-    P::add(a, w[11], dcur.v);   // ( 0, 0,-1)
-    P::add(a, w[12], dcur.e);   // ( 1, 0,-1)
-    P::add(a, w[13], dnxt.v);   // ( 0, 1,-1)
-    P::add(a, w[14], dnxt.w);   // (-1, 1,-1)
+    typename P::Acc1 a;
+    P::first1(a, w[0], cur.v);
+    P::add1(a, w[1], cur.e);     // ( 1, 0, 0)
+    P::add1(a, w[2], cur.w);     // (-1, 0, 0)
+    P::add1(a, w[3], nxt.v);     // ( 0, 1, 0)
+    P::add1(a, w[4], prev.v);    // ( 0,-1, 0)
+    P::add1(a, w[5], prev.e);    // ( 1,-1, 0)
+    P::add1(a, w[6], nxt.w);     // (-1, 1, 0)
+    P::add1(a, w[7], ucur.v);    // ( 0, 0, 1)
+    P::add1(a, w[8], ucur.w);    // (-1, 0, 1)
+    P::add1(a, w[9], uprev.v);   // ( 0,-1, 1)
+    P::add1(a, w[10], uprev.e);  // ( 1,-1, 1)
+    P::add1(a, w[11], dcur.v);   // ( 0, 0,-1)
+    P::add1(a, w[12], dcur.e);   // ( 1, 0,-1)
+    P::add1(a, w[13], dnxt.v);   // ( 0, 1,-1)
+    P::add1(a, w[14], dnxt.w);   // (-1, 1,-1)
     if (writer && col <= n - 1 - z - r) {
       const int64_t start = z0 + (int64_t)r * side - ((int64_t)r * (r - 1)) / 2;
-      ym[start + col] = P::finish(a);
+      ym[start + col] = P::finish1(a);
     }
     prev = cur;
     cur = nxt;

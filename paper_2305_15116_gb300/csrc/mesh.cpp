@@ -294,6 +294,7 @@ void free_level(LevelDev& L) {
   cudaFree(L.st_lo);
   cudaFree(L.tiles);
   cudaFree(L.items);
+  cudaFree(L.slabs);
   L = LevelDev{};
 }
 
@@ -415,6 +416,26 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   }
   L.n_items = int(items.size());
 
+  // ---- 3D slab work list: every macro cut into z-ranges of about equal
+  // point counts (n <= 64, where three slices fit in shared memory) ----------
+  std::vector<int4> slabs;
+  if (d == 3 && n <= 64) {
+    constexpr int CHUNKS = 2;
+    const int64_t S = L.slots_per_macro;
+    std::vector<int> cuts = {0};
+    int64_t acc = 0;
+    for (int z = 0; z <= n; ++z) {
+      const int64_t M = n + 1 - z;
+      acc += M * (M + 1) / 2;
+      if (int(cuts.size()) < CHUNKS && acc * CHUNKS >= S * int64_t(cuts.size()) && z < n) cuts.push_back(z + 1);
+    }
+    cuts.push_back(n + 1);
+    for (size_t c = 0; c + 1 < cuts.size(); ++c)
+      for (int64_t mm = 0; mm < m.n_cells; ++mm)
+        if (cuts[c] < cuts[c + 1]) slabs.push_back(make_int4(int(mm), cuts[c], cuts[c + 1], 0));
+  }
+  L.n_slabs = int(slabs.size());
+
   std::string err;
   if (!(err = upload(&L.st64, st)).empty()) return err;
   if (!(err = upload(&L.st32, st32)).empty()) return err;
@@ -422,6 +443,7 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   if (!(err = upload(&L.st_lo, stl)).empty()) return err;
   if (!(err = upload(&L.tiles, tiles)).empty()) return err;
   if (!(err = upload(&L.items, items)).empty()) return err;
+  if (!(err = upload(&L.slabs, slabs)).empty()) return err;
   return "";
 }
 

@@ -77,14 +77,11 @@ extern "C" int hyteg_apply_host_static(const hyteg_mesh* mesh, int level, int dt
   void* xd = base;
   void* yd = base + kStageBytes;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const hyteg::LevelDev& L = m.levels[level];
   e = cudaMemcpyAsync(xd, x_host, bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string("cudaMemcpyAsync H2D: ") + cudaGetErrorString(e));
-  e = m.dim == 2 ? hyteg::launch_interior2d(dtype, L, m.n_cells, xd, yd, s)
-                 : hyteg::launch_interior3d(dtype, L, m.n_cells, xd, yd, s);
-  if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string("interior kernel launch: ") + cudaGetErrorString(e));
-  e = hyteg::launch_interface(dtype, m.dim, m, L, xd, yd, s);
-  if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string("interface kernel launch: ") + cudaGetErrorString(e));
+  const char* what = "";
+  e = hyteg::launch_apply(m, level, dtype, xd, yd, s, nullptr, &what);
+  if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
   e = cudaMemcpyAsync(y_host, yd, bytes, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string("cudaMemcpyAsync D2H: ") + cudaGetErrorString(e));
   e = cudaStreamSynchronize(s);

@@ -71,3 +71,26 @@ def test_full_size_sampled(cuda, kind):
     yref = oracle.row_apply(rm, gids, x)
     absrow = np.array([_absrow(rm, g, x) for g in gids])
     check_close(yg[slots], yref, absrow, kind, "L6 3D sampled")
+
+
+@pytest.mark.parametrize("kind", ["f64", "f32"])
+def test_level7_row_kernel_sampled(cuda, kind):
+    """Level 7 (n = 128) is above the shared-memory slab kernel's limit and runs
+    the row-sweep kernel with the stencil interface step: sampled rows."""
+    coarse = unit_cube_kuhn_mesh(1, 0.1, 4)
+    L = 7
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    ns, ng = M.num_slots(L)
+    smap = M.dof_map(L)
+    x = random_vector(ng, 6)
+    if kind == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    yg = gpu_apply(M, L, x[smap], kind)
+    assert np.all(np.isfinite(yg))
+    rm = oracle.RefinedMesh(coarse.coords, coarse.cells, L)
+    rng = np.random.default_rng(29)
+    slots = rng.integers(0, ns, 300)
+    gids = smap[slots]
+    yref = oracle.row_apply(rm, gids, x)
+    absrow = np.array([_absrow(rm, g, x) for g in gids])
+    check_close(yg[slots], yref, absrow, kind, "3D L7 sampled")
