@@ -46,6 +46,12 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-variants", action="store_true", help="skip the fp32 / 3D / native-fp64 lines")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default=WORKLOAD, help="workload to time (default: the 2D level-11 case)")
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32", "f64_ieee"])
+    p.add_argument("--level", type=int, default=None,
+                   help="override the refinement level (smaller cases for ncu captures; not a bench line)")
+    p.add_argument("--profile", action="store_true",
+                   help="only run warm-up + timed applies (for profilers): no e2e, variants or CPU baseline")
     return p.parse_args()
 
 
@@ -139,11 +145,11 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- setup
-def setup(name, device, dtype_code):
+def setup(name, device, dtype_code, level=None):
     import torch
     import paper_2305_15116_gb300 as H
     from inputs import workload, random_vector
-    coarse, L, seed = workload(name)
+    coarse, L, seed = workload(name, level)
     M = H.Mesh(coarse.coords, coarse.cells).refine(L)
     ns, ng = M.num_slots(L)
     smap = M.dof_map(L)
@@ -153,8 +159,10 @@ def setup(name, device, dtype_code):
     ys = torch.empty_like(xs)
     n = 1 << L
     interior = coarse.n_cells * ((n - 1) * (n - 2) // 2 if coarse.dim == 2 else (n - 1) * (n - 2) * (n - 3) // 6)
+    slab = coarse.dim == 3 and n <= 64  # the 3D slab kernel writes every slot
     return dict(M=M, L=L, ns=ns, ng=ng, xs=xs, ys=ys, smap=smap, x_global=x, coarse=coarse,
-                interior=interior, elem=4 if dtype_code == H.F32 else 8, code=dtype_code)
+                interior=interior, elem=4 if dtype_code == H.F32 else 8, code=dtype_code, slab=slab,
+                kernel=("k_slab3d" if slab else ("k_interior2d" if coarse.dim == 2 else "k_interior3d")))
 
 
 def timed_applies(w, steps, warmup, stream, barrier=None):
@@ -193,10 +201,11 @@ def timed_applies(w, steps, warmup, stream, barrier=None):
 
 
 def interior_bytes(w):
-    """Algorithmic bytes of one macro-interior launch: every slot of every
-    macro is read once (interior points and the macro-boundary halo) and
-    every interior point is written once."""
-    return w["elem"] * (w["ns"] + w["interior"])
+    """Algorithmic bytes of one launch of the dominant kernel: every slot of
+    every macro is read once (interior points and the macro-boundary halo);
+    every interior point is written once (2D and row kernels), or every slot
+    (the 3D slab kernel, which also writes the macro-boundary partials)."""
+    return w["elem"] * (w["ns"] + (w["ns"] if w["slab"] else w["interior"]))
 
 
 def measured_peaks():
@@ -288,8 +297,16 @@ def main():
     import paper_2305_15116_gb300 as H
 
     stream = torch.cuda.Stream(device=device)
-    w = setup(WORKLOAD, device, H.F64)
+    code = {"f64": H.F64, "f32": H.F32, "f64_ieee": H.F64_IEEE}[args.dtype]
+    w = setup(args.workload, device, code, args.level)
     torch.cuda.synchronize()
+    if args.profile:
+        r = timed_applies(w, args.steps, args.warmup, stream)
+        if rank == 0:
+            print(json.dumps({"profile": args.workload, "level": w["L"], "dtype": args.dtype,
+                              "ms_per_step": r["total_ms"] / args.steps, "kernel_ms": r["interior_ms"],
+                              "interface_ms": r["iface_ms"]}), flush=True)
+        return 0
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     time.sleep(0.2)
@@ -303,6 +320,8 @@ def main():
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = w["ng"] * args.steps * world / (total_ms * 1e-3) / 1e9
+    dtype_label = {"f64": "f64 data, float-float (2 x f32) arithmetic", "f32": "f32",
+                   "f64_ieee": "f64 (native fp64 FMA)"}[args.dtype]
 
     # end to end through the C ABI with host buffers (copies inside the call)
     xh = w["xs"].cpu().pin_memory()
@@ -327,17 +346,17 @@ def main():
     peak, peak_kind = measured_peaks()
     ib = interior_bytes(w)
     achieved = ib / (r["interior_ms"] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_interior2d<ArF64FF>", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": f"{w['kernel']} ({args.dtype})", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
-                "traffic": ncu_traffic("interior2d_f64ff_square32jit_L11"),
+                "traffic": ncu_traffic(f"{w['kernel']}_{args.dtype}_{args.workload}"),
                 "algorithmic_bytes_per_launch": ib,
                 "interior_ms": r["interior_ms"], "interface_ms": r["iface_ms"]}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64 data, float-float (2 x f32) arithmetic", "data": "synthetic",
-        "config": {"workload": describe(WORKLOAD, w["ng"], w["ns"]), "dofs": w["ng"], "slots": w["ns"],
+        "vs_baseline": None, "dtype": dtype_label, "data": "synthetic",
+        "config": {"workload": describe(args.workload, w["ng"], w["ns"]), "dofs": w["ng"], "slots": w["ns"],
                    "l2": "inputs larger than L2 (x+y = %.2f GB per apply), no flush" % (2 * w["ns"] * 8 / 1e9),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
@@ -349,18 +368,24 @@ def main():
     del w
     torch.cuda.empty_cache()
 
+    if args.level is not None:
+        line["config"]["note"] = f"level overridden to {args.level}: not the benchmark configuration"
     if rank == 0 and world == 1 and not args.no_variants:
         variants = []
-        for name, code, label in ((WORKLOAD, H.F32, "f32"), (WORKLOAD, H.F64_IEEE, "f64 native fma"),
-                                  ("cube384jit_L6", H.F64, "f64 data, float-float arithmetic"),
-                                  ("cube384jit_L6", H.F32, "f32"),
-                                  ("cube384jit_L6", H.F64_IEEE, "f64 native fma")):
-            v = setup(name, device, code)
+        for name, vcode, label in ((WORKLOAD, H.F64, "f64 data, float-float arithmetic"),
+                                   (WORKLOAD, H.F32, "f32"), (WORKLOAD, H.F64_IEEE, "f64 native fma"),
+                                   ("cube384jit_L6", H.F64, "f64 data, float-float arithmetic"),
+                                   ("cube384jit_L6", H.F32, "f32"),
+                                   ("cube384jit_L6", H.F64_IEEE, "f64 native fma")):
+            if name == args.workload and vcode == code:
+                continue
+            v = setup(name, device, vcode)
             steps = min(args.steps, 100)
             rv = timed_applies(v, steps, args.warmup, stream)
             vb = interior_bytes(v)
             variants.append({
-                "workload": name, "dtype": label, "value": v["ng"] * steps / (rv["total_ms"] * 1e-3) / 1e9,
+                "workload": name, "dtype": label, "kernel": v["kernel"],
+                "value": v["ng"] * steps / (rv["total_ms"] * 1e-3) / 1e9,
                 "unit": UNIT, "ms_per_step": rv["total_ms"] / steps,
                 "interior_GBps": vb / (rv["interior_ms"] * 1e-3) / 1e9,
                 "interior_frac": vb / (rv["interior_ms"] * 1e-3) / 1e9 / peak,
@@ -369,7 +394,7 @@ def main():
             torch.cuda.empty_cache()
         line["variants"] = variants
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         ng, ts, sample = cpu_oracle_run(5, 1)
         line["cpu_baseline"] = {"value": ng / min(ts) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": sample + " (best of 5)"}

@@ -144,6 +144,11 @@ struct ArF32 {
     ra = a.x;
     rb = a.y;
   }
+  // acc += w * (u + v) for a symmetric pair of neighbours
+  static __device__ __forceinline__ void add_sym(Acc& a, W w, P2 u, P2 v) {
+    a.x = __fmaf_rn(w, __fadd_rn(u.x, v.x), a.x);
+    a.y = __fmaf_rn(w, __fadd_rn(u.y, v.y), a.y);
+  }
   // single-point forms (3D kernel)
   static __device__ __forceinline__ void first1(float& a, W w, V v) { a = __fmul_rn(w, v); }
   static __device__ __forceinline__ void add1(float& a, W w, V v) { a = __fmaf_rn(w, v, a); }
@@ -175,6 +180,10 @@ struct ArF64Native {
   static __device__ __forceinline__ void finish(const Acc& a, T& ra, T& rb) {
     ra = a.x;
     rb = a.y;
+  }
+  static __device__ __forceinline__ void add_sym(Acc& a, W w, P2 u, P2 v) {
+    a.x = __fma_rn(w, __dadd_rn(u.x, v.x), a.x);
+    a.y = __fma_rn(w, __dadd_rn(u.y, v.y), a.y);
   }
   static __device__ __forceinline__ void first1(double& a, W w, V v) { a = __dmul_rn(w, v); }
   static __device__ __forceinline__ void add1(double& a, W w, V v) { a = __fma_rn(w, v, a); }
@@ -240,6 +249,16 @@ struct ArF64FF {
     e = f2_add(e, pe);
     e = f2_fma(w.h, v.l, e);
     a.e = f2_fma(w.l, v.h, e);
+  }
+  // acc += w * (u + v) for a symmetric pair of neighbours: the high parts are
+  // added exactly with TwoSum, the low parts and the TwoSum error go to the
+  // low part of the (unnormalised) pair sum, then one product-accumulate.
+  static __device__ __forceinline__ void add_sym(Acc& a, const W& w, const P2& u, const P2& v) {
+    const f2_t sh = f2_add(u.h, v.h);
+    const f2_t bb = f2_sub(sh, u.h);
+    const f2_t er = f2_add(f2_sub(u.h, f2_sub(sh, bb)), f2_sub(v.h, bb));
+    const f2_t sl = f2_add(f2_add(u.l, v.l), er);
+    add(a, w, P2{sh, sl});
   }
   static __device__ __forceinline__ void finish(const Acc& a, T& ra, T& rb) {
     float sa, sb, ea, eb;

@@ -8,18 +8,16 @@
 // row-major with x contiguous; row r starts at r(n+2) - r(r+1)/2 and holds
 // n+1-r points (Sec. 3).
 //
-// GPU mapping: one warp per tile of 32 consecutive columns and up to 64 rows.
-// The tile's rows are split into two halves that the warp walks up in
-// lockstep ("streams" A and B), so every lane evaluates two independent
-// points per step and the float-float arithmetic runs on packed f32x2
-// instructions.  Each lane stages its column of the next RING rows of both
-// streams in shared memory with cp.async, which keeps 2 x RING loads per warp
-// in flight without spending registers on them.  Each lane owns one column and
-// keeps three rows per stream in registers (the layer condition of Sec. 2.3
-// held in the register file); left/right neighbours come from the adjacent
-// lanes by warp shuffles, so every value is read from memory once per stream
-// plus two halo rows.  The 30 inner lanes write; lanes 0 and 31 only supply
-// the horizontal halo.
+// GPU mapping: one warp per tile of 64 consecutive columns and up to 64 rows.
+// Each lane owns two adjacent columns, so it evaluates two points per row and
+// the float-float arithmetic of the pair runs on packed f32x2 instructions.
+// Each lane stages its two columns of the next RING rows in shared memory with
+// cp.async, which keeps RING rows per warp in flight without spending
+// registers on them, and keeps three rows in registers (the layer condition
+// of Sec. 2.3 held in the register file).  The neighbour columns beyond its
+// pair come from the adjacent lanes by warp shuffles, so every value is read
+// from memory once per tile plus two halo rows.  62 of the 64 columns are
+// written; the outermost two only supply the horizontal halo.
 #include "arith.cuh"
 #include "hyteg_internal.h"
 
@@ -27,30 +25,33 @@ namespace hyteg {
 
 namespace {
 
+// One row as seen by a lane that owns the two adjacent columns A = c and
+// B = c + 1, packed per term (first half: column A, second half: column B):
+// the lane's own values, their right neighbours (B, and A of the next lane)
+// and their left neighbours (B of the previous lane, and A).
 template <class P>
 struct Row {
-  typename P::V v, w, e;  // value of this lane's column, of column-1, of column+1
+  typename P::P2 v, e, w;
 };
 
 template <class P>
-__device__ __forceinline__ Row<P> make_row(typename P::V v) {
-  return Row<P>{v, P::up(v), P::down(v)};
+__device__ __forceinline__ Row<P> make_row(typename P::V a, typename P::V b) {
+  const typename P::V right_of_b = P::down(a);  // column c + 2: A of the next lane
+  const typename P::V left_of_a = P::up(b);     // column c - 1: B of the previous lane
+  return Row<P>{P::pair(a, b), P::pair(b, right_of_b), P::pair(left_of_a, a)};
 }
 
 // Row-walking cursor: offset of row r inside the macro array and its length.
 struct Cursor {
   int off;  // r(n+2) - r(r+1)/2
   int len;  // n + 1 - r
-  int r;
   __device__ __forceinline__ void init(int n, int row) {
-    r = row;
     off = row * (n + 2) - (row * (row + 1)) / 2;
     len = n + 1 - row;
   }
   __device__ __forceinline__ void next() {
     off += len;
     len -= 1;
-    r += 1;
   }
 };
 
@@ -65,9 +66,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Rows in flight per stream: each lane stages its own column of the next RING
-// rows of both streams in shared memory with cp.async, so a warp keeps
-// 2 x RING loads outstanding without holding them in registers.
+// Rows in flight per warp: each lane stages its two columns of the next RING
+// rows in shared memory with cp.async, so a warp keeps RING rows outstanding
+// without holding them in registers.
 constexpr int RING = 8;
 constexpr int THREADS2D = 256;
 
@@ -77,98 +78,69 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* _
                                                           const int4* __restrict__ tiles, int n_tiles,
                                                           int64_t n_warps, int64_t S, int n, StencilPtr st) {
   using T = typename P::T;
-  __shared__ T ring_all[THREADS2D / 32][2][RING][32];
+  __shared__ T ring_all[THREADS2D / 32][RING][32][2];
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= n_warps) return;  // whole warps leave together
   const int lane = threadIdx.x & 31;
-  T(*ring)[RING][32] = ring_all[threadIdx.x >> 5];
+  T(*ring)[32][2] = ring_all[threadIdx.x >> 5];
   const int64_t m = warp / n_tiles;
   const int4 t = tiles[warp - m * n_tiles];
-  const int col = t.x - 1 + lane;
+  const int ca = t.x - 1 + 2 * lane;  // column A; column B = ca + 1
+  const int cb = ca + 1;
   const T* __restrict__ xm = x + m * S;
   T* __restrict__ ym = y + m * S;
 
   const int64_t wb = m * (int64_t)(NCLS2 * NW2);  // class 0: the full interior stencil
-  const typename P::W wS = P::weight(st, wb + 0), wSE = P::weight(st, wb + 1), wW = P::weight(st, wb + 2),
-                      wC = P::weight(st, wb + 3), wE = P::weight(st, wb + 4), wNW = P::weight(st, wb + 5),
+  const typename P::W wSE = P::weight(st, wb + 1), wC = P::weight(st, wb + 3), wE = P::weight(st, wb + 4),
                       wN = P::weight(st, wb + 6);
 
-  // stream A writes rows [t.y, t.y + h), stream B rows [t.y + h, t.z); each
-  // stream reads rows from one below its first to one above its last output
-  const int h = (t.z - t.y + 1) >> 1;
-  const int nb = t.z - t.y - h;  // nb == h or h - 1
-  const int steps = h + 2;       // rows read per stream
-  Cursor ia, ib;                 // next row to stage, per stream
-  ia.init(n, t.y - 1);
-  ib.init(n, t.y + h - 1);
-  // prologue: stage rows 0 .. RING-1 of both streams
+  // rows t.y - 1 .. t.z are read, rows t.y .. t.z - 1 written
+  const int steps = t.z - t.y + 2;
+  Cursor is;  // next row to stage
+  is.init(n, t.y - 1);
+  auto stage = [&](int slot) {
+    if (ca < is.len) cp_async(&ring[slot][lane][0], xm + is.off + ca, sizeof(T));
+    if (cb < is.len) cp_async(&ring[slot][lane][1], xm + is.off + cb, sizeof(T));
+    is.next();
+  };
 #pragma unroll
   for (int k = 0; k < RING; ++k) {
-    if (k < steps) {
-      if (col < ia.len) cp_async(&ring[0][k][lane], xm + ia.off + col, sizeof(T));
-      if (col < ib.len) cp_async(&ring[1][k][lane], xm + ib.off + col, sizeof(T));
-      ia.next();
-      ib.next();
-    }
+    if (k < steps) stage(k);
     cp_async_commit();
   }
-  Cursor ca, cb;  // row being consumed, per stream
-  ca.init(n, t.y - 1);
-  cb.init(n, t.y + h - 1);
-  auto take = [&](int k, int s, const Cursor& c) -> typename P::V {
-    // value of this lane's column in the row consumed at step k of stream s
-    const T v = ring[s][k % RING][lane];
-    return (col < c.len) ? P::conv(v) : P::zero();
-  };
-  auto refill = [&](int k) {
-    // the slot of step k is free again: stage step k + RING
-    if (k + RING < steps) {
-      if (col < ia.len) cp_async(&ring[0][k % RING][lane], xm + ia.off + col, sizeof(T));
-      if (col < ib.len) cp_async(&ring[1][k % RING][lane], xm + ib.off + col, sizeof(T));
-      ia.next();
-      ib.next();
-    }
-    cp_async_commit();
-  };
-  cp_async_wait<RING - 1>();
-  Row<P> pa = make_row<P>(take(0, 0, ca));
-  Row<P> pb = make_row<P>(take(0, 1, cb));
-  refill(0);
-  ca.next();
-  cb.next();
-  cp_async_wait<RING - 1>();
-  Row<P> qa = make_row<P>(take(1, 0, ca));
-  Row<P> qb = make_row<P>(take(1, 1, cb));
-  refill(1);
-  const bool writer = lane >= 1 && lane <= 30;
-  for (int i = 0; i < h; ++i) {
-    // ca / cb point at the rows being written; read the rows above them
-    Cursor na = ca, nbc = cb;
-    na.next();
-    nbc.next();
+  Cursor cr;  // row being consumed
+  cr.init(n, t.y - 1);
+  auto take = [&](int k) -> Row<P> {
     cp_async_wait<RING - 1>();
-    const Row<P> ra = make_row<P>(take(i + 2, 0, na));
-    const Row<P> rb = make_row<P>(take(i + 2, 1, nbc));
-    refill(i + 2);
+    const T va = ring[k % RING][lane][0], vb = ring[k % RING][lane][1];
+    const Row<P> r = make_row<P>(ca < cr.len ? P::conv(va) : P::zero(), cb < cr.len ? P::conv(vb) : P::zero());
+    // the slot of step k is free again: stage step k + RING
+    if (k + RING < steps) stage(k % RING);
+    cp_async_commit();
+    cr.next();
+    return r;
+  };
+  Row<P> prv = take(0);
+  Cursor out = cr;  // the row being written
+  Row<P> cur = take(1);
+  const bool wa = lane >= 1, wbb = lane <= 30;  // lane 0's A and lane 31's B are halo
+  for (int k = 2; k < steps; ++k) {
+    const Row<P> nxt = take(k);
+    // the interior stencil is symmetric (w(d) = w(-d), made bitwise equal on
+    // the host): add opposite neighbours first
     typename P::Acc a;
-    P::first(a, wC, P::pair(qa.v, qb.v));
-    P::add(a, wE, P::pair(qa.e, qb.e));
-    P::add(a, wW, P::pair(qa.w, qb.w));
-    P::add(a, wN, P::pair(ra.v, rb.v));
-    P::add(a, wS, P::pair(pa.v, pb.v));
-    P::add(a, wSE, P::pair(pa.e, pb.e));
-    P::add(a, wNW, P::pair(ra.w, rb.w));
-    typename P::T outa, outb;
+    P::first(a, wC, cur.v);
+    P::add_sym(a, wE, cur.e, cur.w);
+    P::add_sym(a, wN, nxt.v, prv.v);
+    P::add_sym(a, wSE, prv.e, nxt.w);
+    T outa, outb;
     P::finish(a, outa, outb);
-    // point (col, r) is interior when col <= n - 1 - r, i.e. col < len - 1
-    if (writer && col < ca.len - 1) ym[ca.off + col] = outa;
-    if (writer && i < nb && col < cb.len - 1) ym[cb.off + col] = outb;
-    pa = qa;
-    qa = ra;
-    pb = qb;
-    qb = rb;
-    ca = na;
-    cb = nbc;
+    // point (c, r) is interior when c <= n - 1 - r, i.e. c < len - 1
+    if (wa && ca < out.len - 1) ym[out.off + ca] = outa;
+    if (wbb && cb < out.len - 1) ym[out.off + cb] = outb;
+    out.next();
+    prv = cur;
+    cur = nxt;
   }
   cp_async_wait<0>();
 }

@@ -368,6 +368,20 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
           }
     }
   }
+  // The operator is symmetric with constant coefficients inside a macro, so
+  // the interior stencil satisfies w(d) = w(-d); the sums above give equal
+  // values up to rounding.  Make them bitwise equal, so kernels may add
+  // opposite neighbours before multiplying.
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    double* W = &st[size_t(c) * ncls * nw];
+    if (d == 2) {
+      const int pairs[3][2] = {{0, 6}, {1, 5}, {2, 4}};  // S/N, SE/NW, W/E
+      for (auto& pr : pairs) W[pr[0]] = W[pr[1]] = 0.5 * (W[pr[0]] + W[pr[1]]);
+    } else {
+      const int pairs[7][2] = {{1, 2}, {3, 4}, {5, 6}, {7, 11}, {8, 12}, {9, 13}, {10, 14}};
+      for (auto& pr : pairs) W[pr[0]] = W[pr[1]] = 0.5 * (W[pr[0]] + W[pr[1]]);
+    }
+  }
   std::vector<float> st32(st.size()), sth(st.size()), stl(st.size());
   for (size_t i = 0; i < st.size(); ++i) {
     st32[i] = float(st[i]);
@@ -375,12 +389,13 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
     stl[i] = float(st[i] - double(sth[i]));
   }
 
-  // ---- macro-interior work list: strips of 30 columns x chunks of rows ----
-  // A warp loads 32 consecutive columns and writes the 30 inner ones.
-  constexpr int TW = 30, TH = 64;
+  // ---- macro-interior work list: strips of columns x chunks of rows ----
+  // 2D: a warp loads 64 consecutive columns and writes the 62 inner ones;
+  // 3D (row kernel of the larger levels): 32 columns, 30 written.
+  constexpr int TW2 = 62, TW = 30, TH = 64;
   std::vector<int4> tiles;
   if (d == 2) {
-    for (int x0 = 1; x0 <= n - 2; x0 += TW) {
+    for (int x0 = 1; x0 <= n - 2; x0 += TW2) {
       const int ymax = n - 1 - x0;
       for (int y0 = 1; y0 <= ymax; y0 += TH) tiles.push_back(make_int4(x0, y0, std::min(y0 + TH, ymax + 1), 0));
     }

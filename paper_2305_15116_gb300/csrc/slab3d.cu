@@ -101,6 +101,9 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
   SV* ring0 = reinterpret_cast<SV*>(smem_raw + ((size_t)buf_elems * sizeof(T) + 15) / 16 * 16);
   const int stride = buf_elems + 2 * guard;
   auto ring = [&](int z) -> SV* { return ring0 + (size_t)(((z % 3) + 3) % 3) * stride + guard; };
+  // class stencils of this macro (16 classes x 15 weights)
+  typename P::W* wcls = reinterpret_cast<typename P::W*>(
+      reinterpret_cast<unsigned char*>(ring0) + ((3 * (size_t)stride * sizeof(SV) + 15) / 16 * 16));
 
   const int4 it = items[blockIdx.x];
   const int m = it.x, z0 = it.y, z1 = it.z;
@@ -111,6 +114,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
 
   // zero the ring (guards and stale tails must hold finite values)
   for (int i = tid; i < 3 * stride; i += SLAB_THREADS) ring0[i] = SS::zero();
+  for (int i = tid; i < NCLS3 * NW3; i += SLAB_THREADS) wcls[i] = P::weight(st, (int64_t)m * (NCLS3 * NW3) + i);
   __syncthreads();
   // load slices z0-1 .. z0+1 synchronously
   for (int z = max(z0 - 1, 0); z <= min(z0 + 1, n); ++z) {
@@ -126,6 +130,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
   typename P::W w[NW3];
 #pragma unroll
   for (int k = 0; k < NW3; ++k) w[k] = P::weight(st, wb + k);
+  const int warp = tid >> 5, lane = tid & 31;
 
   for (int z = z0; z < z1; ++z) {
     // stage slice z+2 asynchronously (needed when computing slice z+1)
@@ -142,32 +147,44 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
     const SV* __restrict__ bu = ring(z + 1);
     const SV* __restrict__ bd = ring(z - 1);
 
-    // ---- interior points: x, y >= 1, x + y <= M - 2 (z >= 1) -------------
+    // ---- interior points: x, y >= 1, x + y <= K = M - 2 (z >= 1) ---------
+    // Row y holds K - y points; rows y and K - y together hold K <= 63
+    // points, so one warp takes such a pair and each lane two points
+    // (positions lane and lane + 32), evaluated together.
     if (z >= 1 && M >= 4) {
-      const int K = M - 2;                  // row j = y - 1 holds K - 1 - j points
-      const int cnt = (K - 1) * K / 2;
-      for (int q = tid; q < cnt; q += SLAB_THREADS) {
-        const int j = tri_row(q, K - 1);
-        const int yy = j + 1;
-        const int xx = q - (j * (K - 1) - (j * (j - 1)) / 2) + 1;
-        const int p = yy * M - (yy * (yy - 1)) / 2 + xx;
-        typename P::Acc1 a;
-        P::first1(a, w[0], SS::get(bz[p]));
-        P::add1(a, w[1], SS::get(bz[p + 1]));
-        P::add1(a, w[2], SS::get(bz[p - 1]));
-        P::add1(a, w[3], SS::get(bz[p + M - yy]));
-        P::add1(a, w[4], SS::get(bz[p - M + yy - 1]));
-        P::add1(a, w[5], SS::get(bz[p - M + yy]));
-        P::add1(a, w[6], SS::get(bz[p + M - yy - 1]));
-        P::add1(a, w[7], SS::get(bu[p - yy]));
-        P::add1(a, w[8], SS::get(bu[p - yy - 1]));
-        P::add1(a, w[9], SS::get(bu[p - M]));
-        P::add1(a, w[10], SS::get(bu[p - M + 1]));
-        P::add1(a, w[11], SS::get(bd[p + yy]));
-        P::add1(a, w[12], SS::get(bd[p + yy + 1]));
-        P::add1(a, w[13], SS::get(bd[p + M + 1]));
-        P::add1(a, w[14], SS::get(bd[p + M]));
-        ym[zoff + p] = P::finish1(a);
+      const int K = M - 2;
+      const int units = K / 2;  // pairs y = 1 .. (K-1)/2, plus the middle row when K is even
+      for (int u = warp; u < units; u += SLAB_THREADS / 32) {
+        const int ya = u + 1, yb = K - ya;  // yb == ya: the middle row, alone
+        const int la = K - ya;              // points in row ya
+        const int total = (ya == yb) ? la : K;
+        int px[2], py[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int t = min(lane + 32 * h, total - 1);  // out-of-range lanes repeat a valid point
+          const bool first_row = t < la;
+          py[h] = first_row ? ya : yb;
+          px[h] = first_row ? t + 1 : t - la + 1;
+        }
+        int p[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) p[h] = py[h] * M - (py[h] * (py[h] - 1)) / 2 + px[h];
+        auto at = [&](const SV* b, int i0, int i1) { return P::pair(SS::get(b[i0]), SS::get(b[i1])); };
+        typename P::Acc a;
+        P::first(a, w[0], at(bz, p[0], p[1]));
+        P::add_sym(a, w[1], at(bz, p[0] + 1, p[1] + 1), at(bz, p[0] - 1, p[1] - 1));
+        P::add_sym(a, w[3], at(bz, p[0] + M - py[0], p[1] + M - py[1]),
+                   at(bz, p[0] - M + py[0] - 1, p[1] - M + py[1] - 1));
+        P::add_sym(a, w[5], at(bz, p[0] - M + py[0], p[1] - M + py[1]),
+                   at(bz, p[0] + M - py[0] - 1, p[1] + M - py[1] - 1));
+        P::add_sym(a, w[7], at(bu, p[0] - py[0], p[1] - py[1]), at(bd, p[0] + py[0], p[1] + py[1]));
+        P::add_sym(a, w[8], at(bu, p[0] - py[0] - 1, p[1] - py[1] - 1), at(bd, p[0] + py[0] + 1, p[1] + py[1] + 1));
+        P::add_sym(a, w[9], at(bu, p[0] - M, p[1] - M), at(bd, p[0] + M + 1, p[1] + M + 1));
+        P::add_sym(a, w[10], at(bu, p[0] - M + 1, p[1] - M + 1), at(bd, p[0] + M, p[1] + M));
+        T r0, r1;
+        P::finish(a, r0, r1);
+        if (lane < total) ym[zoff + p[0]] = r0;
+        if (lane + 32 < total) ym[zoff + p[1]] = r1;
       }
     }
     // ---- macro-boundary points of the slice: partial rows ---------------------
@@ -195,24 +212,24 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
         }
         const int cls = (xx == 0 ? 1 : 0) | (yy == 0 ? 2 : 0) | (z == 0 ? 4 : 0) | (xx + yy == M - 1 ? 8 : 0);
         const int p = yy * M - (yy * (yy - 1)) / 2 + xx;
-        const int64_t cb = wb + (int64_t)cls * NW3;
+        const typename P::W* cw = wcls + cls * NW3;
         // invalid neighbours carry weight 0 and read guard or stale (finite) values
         typename P::Acc1 a;
-        P::first1(a, P::weight(st, cb + 0), SS::get(bz[p]));
-        P::add1(a, P::weight(st, cb + 1), SS::get(bz[p + 1]));
-        P::add1(a, P::weight(st, cb + 2), SS::get(bz[p - 1]));
-        P::add1(a, P::weight(st, cb + 3), SS::get(bz[p + M - yy]));
-        P::add1(a, P::weight(st, cb + 4), SS::get(bz[p - M + yy - 1]));
-        P::add1(a, P::weight(st, cb + 5), SS::get(bz[p - M + yy]));
-        P::add1(a, P::weight(st, cb + 6), SS::get(bz[p + M - yy - 1]));
-        P::add1(a, P::weight(st, cb + 7), SS::get(bu[p - yy]));
-        P::add1(a, P::weight(st, cb + 8), SS::get(bu[p - yy - 1]));
-        P::add1(a, P::weight(st, cb + 9), SS::get(bu[p - M]));
-        P::add1(a, P::weight(st, cb + 10), SS::get(bu[p - M + 1]));
-        P::add1(a, P::weight(st, cb + 11), SS::get(bd[p + yy]));
-        P::add1(a, P::weight(st, cb + 12), SS::get(bd[p + yy + 1]));
-        P::add1(a, P::weight(st, cb + 13), SS::get(bd[p + M + 1]));
-        P::add1(a, P::weight(st, cb + 14), SS::get(bd[p + M]));
+        P::first1(a, cw[0], SS::get(bz[p]));
+        P::add1(a, cw[1], SS::get(bz[p + 1]));
+        P::add1(a, cw[2], SS::get(bz[p - 1]));
+        P::add1(a, cw[3], SS::get(bz[p + M - yy]));
+        P::add1(a, cw[4], SS::get(bz[p - M + yy - 1]));
+        P::add1(a, cw[5], SS::get(bz[p - M + yy]));
+        P::add1(a, cw[6], SS::get(bz[p + M - yy - 1]));
+        P::add1(a, cw[7], SS::get(bu[p - yy]));
+        P::add1(a, cw[8], SS::get(bu[p - yy - 1]));
+        P::add1(a, cw[9], SS::get(bu[p - M]));
+        P::add1(a, cw[10], SS::get(bu[p - M + 1]));
+        P::add1(a, cw[11], SS::get(bd[p + yy]));
+        P::add1(a, cw[12], SS::get(bd[p + yy + 1]));
+        P::add1(a, cw[13], SS::get(bd[p + M + 1]));
+        P::add1(a, cw[14], SS::get(bd[p + M]));
         ym[zoff + p] = P::finish1(a);
       }
     }
@@ -235,7 +252,8 @@ cudaError_t launch_t(const LevelDev& L, const void* x, void* y, cudaStream_t s) 
   const int buf = (n + 1) * (n + 2) / 2;
   const int guard = n + 3;
   const size_t raw_bytes = ((size_t)buf * sizeof(typename P::T) + 15) / 16 * 16;
-  const size_t bytes = raw_bytes + 3 * (size_t)(buf + 2 * guard) * sizeof(SV);
+  const size_t ring_bytes = (3 * (size_t)(buf + 2 * guard) * sizeof(SV) + 15) / 16 * 16;
+  const size_t bytes = raw_bytes + ring_bytes + (size_t)NCLS3 * NW3 * sizeof(typename P::W);
   cudaError_t e = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
