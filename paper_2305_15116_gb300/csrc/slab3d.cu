@@ -7,9 +7,10 @@
 // slice z only to slices z-1 and z+1 (offsets 0, ±(1,0,0), ±(0,1,0),
 // ±(0,0,1), ±(1,-1,0), ±(1,0,-1), ±(0,1,-1), ±(1,-1,1)), so one CTA walks up a
 // range of slices of one macro with three slices resident in shared memory —
-// the paper's layer condition (Sec. 2.3, Sec. 4.2) one dimension up.  The next
-// slice is staged with cp.async while the current one is computed, then split
-// once (float-float path) into the ring.
+// the paper's layer condition (Sec. 2.3, Sec. 4.2) one dimension up.  A fourth
+// ring buffer receives the next slice by cp.async while the current one is
+// computed (through a staging buffer and one split into float-float for the
+// fp64 path), so each slice costs one barrier.
 //
 // For every slice the CTA writes ALL its points:
 //  * interior points (x, y, z >= 1, x+y+z <= n-1): the full stencil of the
@@ -43,11 +44,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Shared-memory element of a staged point and its conversion from memory.
+// `direct`: the staged element is the memory element itself, so cp.async can
+// land it in the ring without a conversion pass.
 template <class P>
 struct Stage;
 template <>
 struct Stage<ArF32> {
   using S = float;
+  static constexpr bool direct = true;
   static __device__ __forceinline__ S from(float v) { return v; }
   static __device__ __forceinline__ float get(S s) { return s; }
   static __device__ __forceinline__ S zero() { return 0.0f; }
@@ -55,6 +59,7 @@ struct Stage<ArF32> {
 template <>
 struct Stage<ArF64Native> {
   using S = double;
+  static constexpr bool direct = true;
   static __device__ __forceinline__ S from(double v) { return v; }
   static __device__ __forceinline__ double get(S s) { return s; }
   static __device__ __forceinline__ S zero() { return 0.0; }
@@ -62,6 +67,7 @@ struct Stage<ArF64Native> {
 template <>
 struct Stage<ArF64FF> {
   using S = float2;
+  static constexpr bool direct = false;
   static __device__ __forceinline__ S from(double v) {
     const FF f = ff_split(v);
     return make_float2(f.h, f.l);
@@ -70,7 +76,7 @@ struct Stage<ArF64FF> {
   static __device__ __forceinline__ S zero() { return make_float2(0.0f, 0.0f); }
 };
 
-__device__ __forceinline__ int64_t t3(int64_t k) { return k * (k + 1) * (k + 2) / 6; }
+__device__ __forceinline__ int t3i(int k) { return k * (k + 1) * (k + 2) / 6; }
 __device__ __forceinline__ int slice_count(int n, int z) {
   const int M = n + 1 - z;
   return M * (M + 1) / 2;
@@ -87,23 +93,25 @@ __device__ __forceinline__ int tri_row(int q, int K) {
   return y;
 }
 
+constexpr int NRING = 4;  // slices z-1, z, z+1 being read, z+2 being filled
+
 template <class P>
 __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __restrict__ x,
                                                          typename P::T* __restrict__ y,
                                                          const int4* __restrict__ items, int n, int64_t S,
-                                                         int buf_elems, int guard, StencilPtr st) {
+                                                         int buf_elems, int guard, int raw_bytes, StencilPtr st) {
   using SS = Stage<P>;
   using SV = typename SS::S;
   using T = typename P::T;
+  using W = typename P::W;
+  // layout: [class weights: NCLS3*NW3 W] [ring: NRING x (guard + buf + guard) SV] [raw staging: buf T]
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // layout: [raw staging: buf_elems T] [3 ring buffers: (guard + buf_elems + guard) SV]
-  T* raw = reinterpret_cast<T*>(smem_raw);
-  SV* ring0 = reinterpret_cast<SV*>(smem_raw + ((size_t)buf_elems * sizeof(T) + 15) / 16 * 16);
+  W* wcls = reinterpret_cast<W*>(smem_raw);
+  SV* ring = reinterpret_cast<SV*>(smem_raw + (NCLS3 * NW3 * sizeof(W) + 15) / 16 * 16);
   const int stride = buf_elems + 2 * guard;
-  auto ring = [&](int z) -> SV* { return ring0 + (size_t)(((z % 3) + 3) % 3) * stride + guard; };
-  // class stencils of this macro (16 classes x 15 weights)
-  typename P::W* wcls = reinterpret_cast<typename P::W*>(
-      reinterpret_cast<unsigned char*>(ring0) + ((3 * (size_t)stride * sizeof(SV) + 15) / 16 * 16));
+  T* raw = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(ring) + ((size_t)NRING * stride * sizeof(SV) + 15) / 16 * 16);
+  // offset of element 0 of slice z's buffer inside `ring`
+  auto roff = [&](int z) -> int { return (z & (NRING - 1)) * stride + guard; };
 
   const int4 it = items[blockIdx.x];
   const int m = it.x, z0 = it.y, z1 = it.z;
@@ -111,41 +119,44 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
   T* __restrict__ ym = y + (int64_t)m * S;
   const int N = n + 1;
   const int tid = threadIdx.x;
-
-  // zero the ring (guards and stale tails must hold finite values)
-  for (int i = tid; i < 3 * stride; i += SLAB_THREADS) ring0[i] = SS::zero();
-  for (int i = tid; i < NCLS3 * NW3; i += SLAB_THREADS) wcls[i] = P::weight(st, (int64_t)m * (NCLS3 * NW3) + i);
-  __syncthreads();
-  // load slices z0-1 .. z0+1 synchronously
-  for (int z = max(z0 - 1, 0); z <= min(z0 + 1, n); ++z) {
-    const int cnt = slice_count(n, z);
-    const int64_t off = t3(N) - t3(N - z);
-    SV* b = ring(z);
-    for (int i = tid; i < cnt; i += SLAB_THREADS) b[i] = SS::from(__ldg(xm + off + i));
-  }
-  __syncthreads();
-
-  // interior weights (class 0) in registers
-  const int64_t wb = (int64_t)m * (NCLS3 * NW3);
-  typename P::W w[NW3];
-#pragma unroll
-  for (int k = 0; k < NW3; ++k) w[k] = P::weight(st, wb + k);
   const int warp = tid >> 5, lane = tid & 31;
 
-  for (int z = z0; z < z1; ++z) {
-    // stage slice z+2 asynchronously (needed when computing slice z+1)
-    const bool pre = (z + 1 < z1) && (z + 2 <= n);
-    if (pre) {
-      const int cnt = slice_count(n, z + 2);
-      const int64_t off = t3(N) - t3(N - z - 2);
-      for (int i = tid; i < cnt; i += SLAB_THREADS) cp_async(raw + i, xm + off + i, sizeof(T));
-      cp_async_commit();
+  // zero the ring (guards and stale tails must hold finite values), class weights
+  for (int i = tid; i < NRING * stride; i += SLAB_THREADS) ring[i] = SS::zero();
+  for (int i = tid; i < NCLS3 * NW3; i += SLAB_THREADS) wcls[i] = P::weight(st, (int64_t)m * (NCLS3 * NW3) + i);
+  __syncthreads();
+  // slices z0-1 .. z0+1 directly
+  for (int z = max(z0 - 1, 0); z <= min(z0 + 1, n); ++z) {
+    const int cnt = slice_count(n, z);
+    const int off = t3i(N) - t3i(N - z);
+    const int rb = roff(z);
+    for (int i = tid; i < cnt; i += SLAB_THREADS) ring[rb + i] = SS::from(__ldg(xm + off + i));
+  }
+  // stage slice z0+2 (read when computing z0+1)
+  auto stage = [&](int zs) {
+    if (zs < z1 + 1 && zs <= n) {
+      const int cnt = slice_count(n, zs);
+      const int off = t3i(N) - t3i(N - zs);
+      if (SS::direct) {
+        const int rb = roff(zs);
+        for (int i = tid; i < cnt; i += SLAB_THREADS) cp_async(&ring[rb + i], xm + off + i, sizeof(T));
+      } else {
+        for (int i = tid; i < cnt; i += SLAB_THREADS) cp_async(raw + i, xm + off + i, sizeof(T));
+      }
     }
+    cp_async_commit();
+  };
+  stage(z0 + 2);
+  __syncthreads();
+
+  W w[NW3];  // interior weights (class 0) in registers
+#pragma unroll
+  for (int k = 0; k < NW3; ++k) w[k] = wcls[k];
+
+  for (int z = z0; z < z1; ++z) {
     const int M = N - z;
-    const int64_t zoff = t3(N) - t3(N - z);
-    const SV* __restrict__ bz = ring(z);
-    const SV* __restrict__ bu = ring(z + 1);
-    const SV* __restrict__ bd = ring(z - 1);
+    const int zoff = t3i(N) - t3i(N - z);
+    const int bz = roff(z), bu = roff(z + 1), bd = roff(z - 1);
 
     // ---- interior points: x, y >= 1, x + y <= K = M - 2 (z >= 1) ---------
     // Row y holds K - y points; rows y and K - y together hold K <= 63
@@ -158,29 +169,30 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
         const int ya = u + 1, yb = K - ya;  // yb == ya: the middle row, alone
         const int la = K - ya;              // points in row ya
         const int total = (ya == yb) ? la : K;
-        int px[2], py[2];
+        int p[2], yy[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int t = min(lane + 32 * h, total - 1);  // out-of-range lanes repeat a valid point
           const bool first_row = t < la;
-          py[h] = first_row ? ya : yb;
-          px[h] = first_row ? t + 1 : t - la + 1;
+          yy[h] = first_row ? ya : yb;
+          const int xx = first_row ? t + 1 : t - la + 1;
+          p[h] = yy[h] * M - (yy[h] * (yy[h] - 1)) / 2 + xx;
         }
-        int p[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) p[h] = py[h] * M - (py[h] * (py[h] - 1)) / 2 + px[h];
-        auto at = [&](const SV* b, int i0, int i1) { return P::pair(SS::get(b[i0]), SS::get(b[i1])); };
+        // ring offsets of the point in slices z, z+1, z-1 and the row gap A = M - y
+        const int qz0 = bz + p[0], qz1 = bz + p[1];
+        const int qu0 = bu + p[0] - yy[0], qu1 = bu + p[1] - yy[1];
+        const int qd0 = bd + p[0] + yy[0], qd1 = bd + p[1] + yy[1];
+        const int A0 = M - yy[0], A1 = M - yy[1];
+        auto at = [&](int i0, int i1) { return P::pair(SS::get(ring[i0]), SS::get(ring[i1])); };
         typename P::Acc a;
-        P::first(a, w[0], at(bz, p[0], p[1]));
-        P::add_sym(a, w[1], at(bz, p[0] + 1, p[1] + 1), at(bz, p[0] - 1, p[1] - 1));
-        P::add_sym(a, w[3], at(bz, p[0] + M - py[0], p[1] + M - py[1]),
-                   at(bz, p[0] - M + py[0] - 1, p[1] - M + py[1] - 1));
-        P::add_sym(a, w[5], at(bz, p[0] - M + py[0], p[1] - M + py[1]),
-                   at(bz, p[0] + M - py[0] - 1, p[1] + M - py[1] - 1));
-        P::add_sym(a, w[7], at(bu, p[0] - py[0], p[1] - py[1]), at(bd, p[0] + py[0], p[1] + py[1]));
-        P::add_sym(a, w[8], at(bu, p[0] - py[0] - 1, p[1] - py[1] - 1), at(bd, p[0] + py[0] + 1, p[1] + py[1] + 1));
-        P::add_sym(a, w[9], at(bu, p[0] - M, p[1] - M), at(bd, p[0] + M + 1, p[1] + M + 1));
-        P::add_sym(a, w[10], at(bu, p[0] - M + 1, p[1] - M + 1), at(bd, p[0] + M, p[1] + M));
+        P::first(a, w[0], at(qz0, qz1));
+        P::add_sym(a, w[1], at(qz0 + 1, qz1 + 1), at(qz0 - 1, qz1 - 1));                  // (±1,0,0)
+        P::add_sym(a, w[3], at(qz0 + A0, qz1 + A1), at(qz0 - A0 - 1, qz1 - A1 - 1));      // (0,±1,0)
+        P::add_sym(a, w[5], at(qz0 - A0, qz1 - A1), at(qz0 + A0 - 1, qz1 + A1 - 1));      // ±(1,-1,0)
+        P::add_sym(a, w[7], at(qu0, qu1), at(qd0, qd1));                                  // (0,0,±1)
+        P::add_sym(a, w[8], at(qu0 - 1, qu1 - 1), at(qd0 + 1, qd1 + 1));                  // ±(-1,0,1)
+        P::add_sym(a, w[9], at(qu0 - A0, qu1 - A1), at(qd0 + A0 + 1, qd1 + A1 + 1));      // ±(0,-1,1)
+        P::add_sym(a, w[10], at(qu0 - A0 + 1, qu1 - A1 + 1), at(qd0 + A0, qd1 + A1));     // ±(1,-1,1)
         T r0, r1;
         P::finish(a, r0, r1);
         if (lane < total) ym[zoff + p[0]] = r0;
@@ -189,59 +201,64 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
     }
     // ---- macro-boundary points of the slice: partial rows ---------------------
     // z = 0: the whole slice lies on the face z = 0; otherwise the rows y = 0,
-    // the column x = 0 and the diagonal x + y = M - 1.
+    // the column x = 0 and the diagonal x + y = M - 1.  Invalid neighbours
+    // carry weight 0 and read guard cells or stale (finite) values.
     {
       const int nb = (z == 0) ? M * (M + 1) / 2 : (M >= 2 ? 3 * (M - 1) : 1);
       for (int q = tid; q < nb; q += SLAB_THREADS) {
-        int xx, yy;
+        int xx, yv;
         if (z == 0) {
-          yy = tri_row(q, M);
-          xx = q - (yy * M - (yy * (yy - 1)) / 2);
+          yv = tri_row(q, M);
+          xx = q - (yv * M - (yv * (yv - 1)) / 2);
         } else if (M == 1) {
           xx = 0;
-          yy = 0;
+          yv = 0;
         } else if (q < M) {  // y = 0
           xx = q;
-          yy = 0;
+          yv = 0;
         } else if (q < 2 * M - 1) {  // x = 0, y = 1 .. M-1
           xx = 0;
-          yy = q - M + 1;
+          yv = q - M + 1;
         } else {  // diagonal, y = 1 .. M-2
-          yy = q - (2 * M - 1) + 1;
-          xx = M - 1 - yy;
+          yv = q - (2 * M - 1) + 1;
+          xx = M - 1 - yv;
         }
-        const int cls = (xx == 0 ? 1 : 0) | (yy == 0 ? 2 : 0) | (z == 0 ? 4 : 0) | (xx + yy == M - 1 ? 8 : 0);
-        const int p = yy * M - (yy * (yy - 1)) / 2 + xx;
-        const typename P::W* cw = wcls + cls * NW3;
-        // invalid neighbours carry weight 0 and read guard or stale (finite) values
+        const int cls = (xx == 0 ? 1 : 0) | (yv == 0 ? 2 : 0) | (z == 0 ? 4 : 0) | (xx + yv == M - 1 ? 8 : 0);
+        const int p = yv * M - (yv * (yv - 1)) / 2 + xx;
+        const W* cw = wcls + cls * NW3;
+        const int qz = bz + p, qu = bu + p - yv, qd = bd + p + yv, A = M - yv;
         typename P::Acc1 a;
-        P::first1(a, cw[0], SS::get(bz[p]));
-        P::add1(a, cw[1], SS::get(bz[p + 1]));
-        P::add1(a, cw[2], SS::get(bz[p - 1]));
-        P::add1(a, cw[3], SS::get(bz[p + M - yy]));
-        P::add1(a, cw[4], SS::get(bz[p - M + yy - 1]));
-        P::add1(a, cw[5], SS::get(bz[p - M + yy]));
-        P::add1(a, cw[6], SS::get(bz[p + M - yy - 1]));
-        P::add1(a, cw[7], SS::get(bu[p - yy]));
-        P::add1(a, cw[8], SS::get(bu[p - yy - 1]));
-        P::add1(a, cw[9], SS::get(bu[p - M]));
-        P::add1(a, cw[10], SS::get(bu[p - M + 1]));
-        P::add1(a, cw[11], SS::get(bd[p + yy]));
-        P::add1(a, cw[12], SS::get(bd[p + yy + 1]));
-        P::add1(a, cw[13], SS::get(bd[p + M + 1]));
-        P::add1(a, cw[14], SS::get(bd[p + M]));
+        P::first1(a, cw[0], SS::get(ring[qz]));
+        P::add1(a, cw[1], SS::get(ring[qz + 1]));
+        P::add1(a, cw[2], SS::get(ring[qz - 1]));
+        P::add1(a, cw[3], SS::get(ring[qz + A]));
+        P::add1(a, cw[4], SS::get(ring[qz - A - 1]));
+        P::add1(a, cw[5], SS::get(ring[qz - A]));
+        P::add1(a, cw[6], SS::get(ring[qz + A - 1]));
+        P::add1(a, cw[7], SS::get(ring[qu]));
+        P::add1(a, cw[8], SS::get(ring[qu - 1]));
+        P::add1(a, cw[9], SS::get(ring[qu - A]));
+        P::add1(a, cw[10], SS::get(ring[qu - A + 1]));
+        P::add1(a, cw[11], SS::get(ring[qd]));
+        P::add1(a, cw[12], SS::get(ring[qd + 1]));
+        P::add1(a, cw[13], SS::get(ring[qd + A + 1]));
+        P::add1(a, cw[14], SS::get(ring[qd + A]));
         ym[zoff + p] = P::finish1(a);
       }
     }
-    if (pre) cp_async_wait_all();
-    __syncthreads();  // slice z-1 is no longer read; staged slice z+2 has landed
-    if (pre) {
+    // slice z+2 has landed (staged during the previous iteration): convert it
+    // into its ring buffer when it was staged raw; then one barrier publishes
+    // it and retires slice z-1, whose buffer receives slice z+3.
+    cp_async_wait_all();
+    if (!SS::direct && z + 2 < z1 + 1 && z + 2 <= n) {
       const int cnt = slice_count(n, z + 2);
-      SV* b = ring(z + 2);
-      for (int i = tid; i < cnt; i += SLAB_THREADS) b[i] = SS::from(raw[i]);
+      const int rb = roff(z + 2);
+      for (int i = tid; i < cnt; i += SLAB_THREADS) ring[rb + i] = SS::from(raw[i]);
     }
     __syncthreads();
+    stage(z + 3);
   }
+  cp_async_wait_all();
 }
 
 template <class P>
@@ -251,14 +268,15 @@ cudaError_t launch_t(const LevelDev& L, const void* x, void* y, cudaStream_t s) 
   const int n = L.n;
   const int buf = (n + 1) * (n + 2) / 2;
   const int guard = n + 3;
-  const size_t raw_bytes = ((size_t)buf * sizeof(typename P::T) + 15) / 16 * 16;
-  const size_t ring_bytes = (3 * (size_t)(buf + 2 * guard) * sizeof(SV) + 15) / 16 * 16;
-  const size_t bytes = raw_bytes + ring_bytes + (size_t)NCLS3 * NW3 * sizeof(typename P::W);
+  const size_t w_bytes = ((size_t)NCLS3 * NW3 * sizeof(typename P::W) + 15) / 16 * 16;
+  const size_t ring_bytes = ((size_t)NRING * (buf + 2 * guard) * sizeof(SV) + 15) / 16 * 16;
+  const size_t raw_bytes = Stage<P>::direct ? 0 : (size_t)buf * sizeof(typename P::T);
+  const size_t bytes = w_bytes + ring_bytes + raw_bytes;
   cudaError_t e = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
   k_slab3d<P><<<L.n_slabs, SLAB_THREADS, bytes, s>>>((const typename P::T*)x, (typename P::T*)y, L.slabs, n,
-                                                    L.slots_per_macro, buf, guard, st);
+                                                    L.slots_per_macro, buf, guard, (int)raw_bytes, st);
   return cudaGetLastError();
 }
 
