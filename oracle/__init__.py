@@ -18,6 +18,10 @@ Performance Analysis of the HyTeG Finite Element Framework" (PASC '23):
   (Sec. 1.2, Sec. 2).
 * `layout`   — the paper's closed-form DoF counts and memory volumes (Sec. 2.1,
   Table "memory level 10") and the triangular index map.
+* `multigrid` — a textbook V-cycle on the refinement hierarchy (levels as the
+  multigrid hierarchy, Sec. 1.2; smoothers, Sec. 4.1): linear prolongation,
+  R = P^T, weighted Jacobi, direct coarsest solve, lumped-mass right-hand
+  side.
 
 Everything is float64 and deliberately plain: per-element matrices, a sparse
 sum of duplicates, a row loop product.  Parity pins live in tests/ (run with
