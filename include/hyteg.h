@@ -145,6 +145,74 @@ int hyteg_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* 
 int hyteg_apply_host(hyteg_mesh* mesh, int level, int dtype, const void* x_host, void* y_host,
                      void* stream);
 
+/* ---- geometry queries (host only, any level 0..15, no refine needed) ----- */
+
+/* Coordinates of every slot: xyz[n_slots * dim] (host), slot s at
+ * xyz[s*dim + c].  Copies of one refined vertex get bitwise equal values.
+ * Errors: HYTEG_EINVAL. */
+int hyteg_slot_coords(const hyteg_mesh* mesh, int level, double* xyz);
+
+/* Lumped P1 mass of every slot, |supp phi_i| / (dim+1) (the row sums of the
+ * mass matrix), with every copy holding the full value: mass[n_slots] (host).
+ * The right-hand side of -Lap u = f is then b = mass * f at the vertices
+ * (zero on Dirichlet DoFs).  Errors: HYTEG_EINVAL. */
+int hyteg_lumped_mass(const hyteg_mesh* mesh, int level, double* mass);
+
+/* 1 for every slot of a Dirichlet DoF (a refined vertex on the domain
+ * boundary of a mesh created with HYTEG_BC_DIRICHLET), else 0: mask[n_slots]
+ * (host).  Errors: HYTEG_EINVAL. */
+int hyteg_dirichlet_mask(const hyteg_mesh* mesh, int level, uint8_t* mask);
+
+/* ---- multigrid on the refinement hierarchy ------------------------------
+ * The refinement levels are the multigrid hierarchy (Sec. 1.2) and smoothers
+ * are among the generated kernels (Sec. 4.1).  The cycle is the textbook
+ * V(nu1, nu2): weighted Jacobi with the stencil apply of this library,
+ * restriction P^T and linear prolongation P between consecutive levels, and a
+ * dense direct solve on level 0 (the coarse mesh, at most 4096 vertices).
+ * Needs a mesh created with HYTEG_BC_DIRICHLET; vectors are device arrays in
+ * the slot layout of their level with consistent copies. */
+
+#define HYTEG_SOLVE_F64    1  /* float64 V-cycles (float-float apply) */
+#define HYTEG_SOLVE_MIXED  2  /* fp32 V-cycles inside float64 iterative refinement */
+
+/* Builds the solver workspace for levels 0..max_level (refined already):
+ * inverse diagonals, norm weights, transfer tables, the inverse of the level-0
+ * operator and eight work vectors per level (4 float64 + 4 fp32), all with
+ * cudaMalloc and owned by the mesh.  nu1/nu2 pre/post smoothing sweeps
+ * (0..64, nu1+nu2 >= 1), omega the Jacobi weight in (0, 2) (2/3 is the usual).
+ * Synchronous.  Calling it again replaces the workspace.
+ * Errors: HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA, HYTEG_ENOMEM. */
+int hyteg_solver_setup(hyteg_mesh* mesh, int max_level, int nu1, int nu2, double omega);
+
+/* b_coarse = P^T r_fine on level fine_level-1 with zeroed Dirichlet rows
+ * (P: linear interpolation from fine_level-1 to fine_level).  dtype HYTEG_F64
+ * or HYTEG_F32 (element type of both vectors).  Asynchronous on `stream`.
+ * Errors: HYTEG_EINVAL, HYTEG_ESTATE (solver not set up for fine_level). */
+int hyteg_restrict(const hyteg_mesh* mesh, int fine_level, int dtype, const void* r_fine, void* b_coarse,
+                   void* stream);
+
+/* u_fine += P e_coarse (linear interpolation from fine_level-1).  As above. */
+int hyteg_prolong_add(const hyteg_mesh* mesh, int fine_level, int dtype, const void* e_coarse, void* u_fine,
+                      void* stream);
+
+/* One V(nu1, nu2) cycle for A u = b on `level`, u updated in place (b and u
+ * device arrays of dtype HYTEG_F64 or HYTEG_F32).  Uses the workspace of the
+ * levels below; calls on one mesh must not overlap.  Asynchronous.
+ * Errors: HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA. */
+int hyteg_vcycle(hyteg_mesh* mesh, int level, int dtype, const void* b, void* u, void* stream);
+
+/* Solves A u = b on `level` (float64 device vectors; u holds the initial
+ * guess and receives the solution) until ||b - A u||_2 <= rtol ||b||_2, the
+ * norms taken over the non-Dirichlet DoFs (one copy each) with the float64
+ * residual, or max_iter iterations.  HYTEG_SOLVE_F64: one float64 V-cycle per
+ * iteration; HYTEG_SOLVE_MIXED: one fp32 V-cycle on the residual equation per
+ * iteration and a float64 update (iterative refinement).  Synchronises
+ * `stream` once per iteration to read the residual norm.  *iters receives the
+ * iterations done, *relres the final relative residual.
+ * Errors: HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA. */
+int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double rtol, int max_iter,
+                void* stream, int* iters, double* relres);
+
 /* Staging limit of hyteg_apply_host_static: bytes per vector (16 MiB, i.e.
  * 2,097,152 float64 or 4,194,304 float32 slots). */
 #define HYTEG_STATIC_STAGE_BYTES (16u << 20)

@@ -10,6 +10,7 @@ from .meshes import (
     unit_square_mesh,
     unit_cube_kuhn_mesh,
     random_vector,
+    random_normal,
     workload,
     WORKLOADS,
 )
@@ -19,6 +20,7 @@ __all__ = [
     "unit_square_mesh",
     "unit_cube_kuhn_mesh",
     "random_vector",
+    "random_normal",
     "workload",
     "WORKLOADS",
 ]

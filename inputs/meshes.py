@@ -124,6 +124,11 @@ def random_vector(n: int, seed: int, low: float = -1.0, high: float = 1.0) -> np
     return _rng(seed).uniform(low, high, size=n)
 
 
+def random_normal(n: int, seed: int) -> np.ndarray:
+    """n float64 values ~ N(0, 1) from PCG64(seed), in index order."""
+    return _rng(seed).standard_normal(n)
+
+
 # The measured workloads: coarse mesh recipe, refinement level, vector seed.
 WORKLOADS = {
     # two right triangles, level 7: the small case an apply is checked on exactly
@@ -132,6 +137,8 @@ WORKLOADS = {
     "square32jit_L11": dict(dim=2, k=4, jitter=0.15, mesh_seed=0, level=11, x_seed=1),
     # 384 jittered Kuhn macro-tets, level 6 (~17M DoFs): the 3D throughput case
     "cube384jit_L6": dict(dim=3, k=4, jitter=0.1, mesh_seed=0, level=6, x_seed=1),
+    # Poisson solve: 32 jittered macro-triangles at level 10, noise seed 2
+    "square32jit_L10_solve": dict(dim=2, k=4, jitter=0.15, mesh_seed=0, level=10, x_seed=2),
 }
 
 

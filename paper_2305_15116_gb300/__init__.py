@@ -6,6 +6,8 @@ coarse mesh of triangles or tetrahedra, every macro refined uniformly to level
 L, and y = A x with constant per-macro stencils plus an interface step
 (Sec. 1.2, Sec. 4).  PyTorch provides device memory and streams only.
 """
-from .mesh import Mesh, F64, F32, F64_IEEE, BC_NONE, BC_DIRICHLET, HytegError, version
+from .mesh import (Mesh, F64, F32, F64_IEEE, BC_NONE, BC_DIRICHLET, SOLVE_F64, SOLVE_MIXED, HytegError,
+                   version)
 
-__all__ = ["Mesh", "F64", "F32", "F64_IEEE", "BC_NONE", "BC_DIRICHLET", "HytegError", "version"]
+__all__ = ["Mesh", "F64", "F32", "F64_IEEE", "BC_NONE", "BC_DIRICHLET", "SOLVE_F64", "SOLVE_MIXED", "HytegError",
+           "version"]

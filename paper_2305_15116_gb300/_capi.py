@@ -44,6 +44,24 @@ lib.hyteg_apply_host.restype = ctypes.c_int
 lib.hyteg_apply_host_static.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]
 lib.hyteg_apply_host_static.restype = ctypes.c_int
+lib.hyteg_slot_coords.argtypes = [ctypes.c_void_p, ctypes.c_int, c_dblp]
+lib.hyteg_slot_coords.restype = ctypes.c_int
+lib.hyteg_lumped_mass.argtypes = [ctypes.c_void_p, ctypes.c_int, c_dblp]
+lib.hyteg_lumped_mass.restype = ctypes.c_int
+lib.hyteg_dirichlet_mask.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+lib.hyteg_dirichlet_mask.restype = ctypes.c_int
+lib.hyteg_solver_setup.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+lib.hyteg_solver_setup.restype = ctypes.c_int
+for _f in (lib.hyteg_restrict, lib.hyteg_prolong_add):
+    _f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    _f.restype = ctypes.c_int
+lib.hyteg_vcycle.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p]
+lib.hyteg_vcycle.restype = ctypes.c_int
+lib.hyteg_solve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_double)]
+lib.hyteg_solve.restype = ctypes.c_int
 lib.hyteg_last_error.argtypes = []
 lib.hyteg_last_error.restype = ctypes.c_char_p
 lib.hyteg_version.argtypes = []
@@ -53,6 +71,7 @@ lib.hyteg_version.restype = ctypes.c_char_p
 OK, EINVAL, ENOMEM, ECUDA, EMESH, ESTATE = 0, -1, -2, -3, -4, -5
 F64, F32, F64_IEEE = 1, 2, 3
 BC_NONE, BC_DIRICHLET = 0, 1
+SOLVE_F64, SOLVE_MIXED = 1, 2
 
 
 class HytegError(RuntimeError):

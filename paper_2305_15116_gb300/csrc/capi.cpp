@@ -126,6 +126,7 @@ void hyteg_mesh_destroy(hyteg_mesh* mesh) {
     cudaFree(m.d_incs);
     cudaFree(m.stage_x);
     cudaFree(m.stage_y);
+    hyteg::solver_free(m);
     cudaSetDevice(cur);
   }
   delete mesh;
@@ -206,6 +207,97 @@ int hyteg_apply_host(hyteg_mesh* mesh, int level, int dtype, const void* x_host,
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   return HYTEG_OK;
+}
+
+int hyteg_slot_coords(const hyteg_mesh* mesh, int level, double* xyz) {
+  if (int r = check_host_level(mesh, level)) return r;
+  if (!xyz) return fail(HYTEG_EINVAL, "xyz is NULL");
+  hyteg::compute_slot_coords(mesh->m, level, xyz);
+  return HYTEG_OK;
+}
+
+int hyteg_lumped_mass(const hyteg_mesh* mesh, int level, double* mass) {
+  if (int r = check_host_level(mesh, level)) return r;
+  if (!mass) return fail(HYTEG_EINVAL, "mass is NULL");
+  hyteg::compute_lumped_mass(mesh->m, level, mass);
+  return HYTEG_OK;
+}
+
+int hyteg_dirichlet_mask(const hyteg_mesh* mesh, int level, uint8_t* mask) {
+  if (int r = check_host_level(mesh, level)) return r;
+  if (!mask) return fail(HYTEG_EINVAL, "mask is NULL");
+  hyteg::compute_dirichlet_mask(mesh->m, level, mask);
+  return HYTEG_OK;
+}
+
+int hyteg_solver_setup(hyteg_mesh* mesh, int max_level, int nu1, int nu2, double omega) {
+  if (int r = check_level(mesh, max_level)) return r;
+  if (nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || nu1 > 64 || nu2 > 64) return fail(HYTEG_EINVAL, "bad sweep counts");
+  if (!(omega > 0.0 && omega < 2.0)) return fail(HYTEG_EINVAL, "omega must lie in (0, 2)");
+  if (mesh->m.bc != HYTEG_BC_DIRICHLET) return fail(HYTEG_EINVAL, "the solver needs Dirichlet boundary rows");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != mesh->m.device) return fail(HYTEG_ESTATE, "current device is not the mesh's device");
+  try {
+    const std::string err = hyteg::solver_setup(mesh->m, max_level, nu1, nu2, omega);
+    if (!err.empty()) {
+      hyteg::solver_free(mesh->m);
+      return fail(err.rfind("cuda", 0) == 0 ? HYTEG_ECUDA : HYTEG_EINVAL, err);
+    }
+  } catch (const std::bad_alloc&) {
+    hyteg::solver_free(mesh->m);
+    return fail(HYTEG_ENOMEM, "host allocation failed");
+  }
+  return HYTEG_OK;
+}
+
+namespace {
+int check_solver(const hyteg_mesh* mesh, int level, int min_level) {
+  if (int r = check_level(mesh, level)) return r;
+  if (!mesh->m.solver || level > mesh->m.solver->max_level)
+    return fail(HYTEG_ESTATE, "hyteg_solver_setup has not covered this level");
+  if (level < min_level) return fail(HYTEG_EINVAL, "level too small for this operation");
+  return HYTEG_OK;
+}
+}  // namespace
+
+int hyteg_restrict(const hyteg_mesh* mesh, int fine_level, int dtype, const void* r_fine, void* b_coarse,
+                   void* stream) {
+  if (int r = check_solver(mesh, fine_level, 1)) return r;
+  if (dtype != HYTEG_F64 && dtype != HYTEG_F32) return fail(HYTEG_EINVAL, "dtype must be HYTEG_F64 or HYTEG_F32");
+  if (!r_fine || !b_coarse) return fail(HYTEG_EINVAL, "NULL vector");
+  const cudaError_t e =
+      hyteg::mg_restrict(mesh->m, fine_level, dtype, r_fine, b_coarse, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "restriction");
+}
+
+int hyteg_prolong_add(const hyteg_mesh* mesh, int fine_level, int dtype, const void* e_coarse, void* u_fine,
+                      void* stream) {
+  if (int r = check_solver(mesh, fine_level, 1)) return r;
+  if (dtype != HYTEG_F64 && dtype != HYTEG_F32) return fail(HYTEG_EINVAL, "dtype must be HYTEG_F64 or HYTEG_F32");
+  if (!e_coarse || !u_fine) return fail(HYTEG_EINVAL, "NULL vector");
+  const cudaError_t e =
+      hyteg::mg_prolong_add(mesh->m, fine_level, dtype, e_coarse, u_fine, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "prolongation");
+}
+
+int hyteg_vcycle(hyteg_mesh* mesh, int level, int dtype, const void* b, void* u, void* stream) {
+  if (int r = check_solver(mesh, level, 0)) return r;
+  if (dtype != HYTEG_F64 && dtype != HYTEG_F32) return fail(HYTEG_EINVAL, "dtype must be HYTEG_F64 or HYTEG_F32");
+  if (!b || !u) return fail(HYTEG_EINVAL, "NULL vector");
+  const cudaError_t e = hyteg::mg_vcycle(mesh->m, level, dtype, b, u, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "V-cycle");
+}
+
+int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double rtol, int max_iter,
+                void* stream, int* iters, double* relres) {
+  if (int r = check_solver(mesh, level, 0)) return r;
+  if (mode != HYTEG_SOLVE_F64 && mode != HYTEG_SOLVE_MIXED) return fail(HYTEG_EINVAL, "unknown mode");
+  if (!b || !u || !iters || !relres) return fail(HYTEG_EINVAL, "NULL argument");
+  if (!(rtol > 0.0) || max_iter < 0) return fail(HYTEG_EINVAL, "bad rtol or max_iter");
+  const cudaError_t e = hyteg::mg_solve(mesh->m, level, mode, b, u, rtol, max_iter,
+                                        static_cast<cudaStream_t>(stream), iters, relres);
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "solve");
 }
 
 const char* hyteg_last_error(void) { return g_last_error.c_str(); }

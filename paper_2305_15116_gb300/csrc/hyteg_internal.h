@@ -46,6 +46,8 @@ struct LevelDev {
   // 3D slab work list (levels with n <= 64): int4 (macro, z0, z1, 0)
   int4* slabs = nullptr;
   int n_slabs = 0;
+  // host copy of the class stencils (multigrid set-up)
+  std::vector<double> st_host;
 };
 
 // Interface primitive (coarse vertex, edge or face) and its incident cells.
@@ -61,6 +63,32 @@ struct Prim {
 struct Inc {
   int cell;
   int corner[3];
+};
+
+// Multigrid workspace of one level (device memory, slot layout).
+struct MgLevel {
+  int level = -1;
+  double* dinv64 = nullptr;   // 1 / diag(A), per slot (Dirichlet rows: 1)
+  float* dinv32 = nullptr;
+  unsigned char* owner = nullptr;  // 1 on one copy of every non-Dirichlet DoF
+  unsigned* lpts = nullptr;   // local coordinates of the S points of one macro
+  double* multinv64 = nullptr;  // [cell][class]: 1 / number of macros sharing the point
+  float* multinv32 = nullptr;
+  double *u64 = nullptr, *b64 = nullptr, *y64 = nullptr, *r64 = nullptr;
+  float *u32 = nullptr, *b32 = nullptr, *y32 = nullptr, *r32 = nullptr;
+};
+
+struct Solver {
+  int max_level = -1;
+  int nu1 = 3, nu2 = 3;
+  double omega = 2.0 / 3.0;
+  std::vector<MgLevel> lv;
+  int nv0 = 0;                   // coarse (level 0) vertices
+  double* a0inv64 = nullptr;     // [nv0 * nv0] inverse of the level-0 operator
+  float* a0inv32 = nullptr;
+  int* v_of_slot0 = nullptr;     // level-0 slot -> vertex
+  int* slot_of_v0 = nullptr;     // vertex -> one level-0 slot
+  double* red = nullptr;         // reduction scratch: [RED_BLOCKS partials][2 results]
 };
 
 struct Mesh {
@@ -86,6 +114,8 @@ struct Mesh {
   void* stage_x = nullptr;
   void* stage_y = nullptr;
   size_t stage_bytes = 0;
+
+  Solver* solver = nullptr;
 };
 
 // Records the message returned by hyteg_last_error() on this thread.
@@ -99,6 +129,18 @@ void free_level(LevelDev& L);
 void compute_dof_map(const Mesh& m, int level, int64_t* gid);
 int64_t n_global_dofs(const Mesh& m, int level);
 int64_t slots_per_macro(int dim, int level);
+
+// ---- multigrid (mg_setup.cpp, multigrid.cu) -----------------------------------
+void compute_slot_coords(const Mesh& m, int level, double* xyz);
+void compute_lumped_mass(const Mesh& m, int level, double* mass);
+void compute_dirichlet_mask(const Mesh& m, int level, unsigned char* mask);
+std::string solver_setup(Mesh& m, int max_level, int nu1, int nu2, double omega);
+void solver_free(Mesh& m);
+cudaError_t mg_restrict(const Mesh& m, int fine_level, int dtype, const void* rf, void* bc, cudaStream_t s);
+cudaError_t mg_prolong_add(const Mesh& m, int fine_level, int dtype, const void* ec, void* uf, cudaStream_t s);
+cudaError_t mg_vcycle(Mesh& m, int level, int dtype, const void* b, void* u, cudaStream_t s);
+cudaError_t mg_solve(Mesh& m, int level, int mode, const double* b, double* u, double rtol, int max_iter,
+                     cudaStream_t s, int* iters, double* relres);
 
 // ---- kernels ----------------------------------------------------------------
 // dtype: 1 = f64 (float-float arithmetic), 2 = f32, 3 = f64 native.

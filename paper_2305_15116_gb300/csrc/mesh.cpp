@@ -382,6 +382,7 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
       for (auto& pr : pairs) W[pr[0]] = W[pr[1]] = 0.5 * (W[pr[0]] + W[pr[1]]);
     }
   }
+  L.st_host = st;
   std::vector<float> st32(st.size()), sth(st.size()), stl(st.size());
   for (size_t i = 0; i < st.size(); ++i) {
     st32[i] = float(st[i]);

@@ -1,0 +1,425 @@
+// Geometric multigrid on the refinement hierarchy: V(nu1, nu2) cycles with
+// weighted Jacobi smoothing, linear prolongation P and restriction P^T, a
+// dense direct solve on level 0, and the float64 solve — either plain
+// float64 V-cycles or fp32 V-cycles inside float64 iterative refinement.
+//
+// The paper takes the refinement levels as the natural multigrid hierarchy
+// (Sec. 1.2) and lists smoothers among the kernels HyTeG generates (Sec. 4.1);
+// the operator apply of every smoothing step is the stencil apply of this
+// library (interior2d.cu / slab3d.cu + interface.cu).
+//
+// Vectors are in the slot layout of their level.  Restriction works on
+// consistent fine vectors: each macro sums the fine values around each of
+// its coarse points (weight 1 at the coincident point, 1/2 at the midpoints of
+// the coarse micro-edges), dividing every fine value by the number of macros
+// that hold a copy of it; the interface step then sums the partials of the
+// copies of every coarse interface point and zeroes the Dirichlet rows.
+#include <vector>
+
+#include "arith.cuh"
+#include "hyteg_internal.h"
+
+namespace hyteg {
+
+namespace {
+
+constexpr int RED_BLOCKS = 1024;
+constexpr int THREADS = 256;
+
+__device__ __forceinline__ int64_t slot2(int n, int x, int y) {
+  return (int64_t)y * (n + 2) - ((int64_t)y * (y + 1)) / 2 + x;
+}
+__device__ __forceinline__ int64_t slot3(int n, int x, int y, int z) {
+  const int64_t N = n + 1, b = N - z;
+  const int64_t zs = N * (N + 1) * (N + 2) / 6 - b * (b + 1) * (b + 2) / 6;
+  return zs + (int64_t)y * b - ((int64_t)y * (y - 1)) / 2 + x;
+}
+template <int DIM>
+__device__ __forceinline__ int64_t slotq(int n, const int q[3]) {
+  return DIM == 2 ? slot2(n, q[0], q[1]) : slot3(n, q[0], q[1], q[2]);
+}
+template <int DIM>
+__device__ __forceinline__ void unpack(unsigned v, int q[3]) {
+  if (DIM == 2) {
+    q[0] = int(v & 0xFFFFu);
+    q[1] = int(v >> 16);
+    q[2] = 0;
+  } else {
+    q[0] = int(v & 0x7FFu);
+    q[1] = int((v >> 11) & 0x7FFu);
+    q[2] = int(v >> 22);
+  }
+}
+template <int DIM>
+__device__ __forceinline__ int pclass(int n, const int q[3]) {
+  return DIM == 2 ? ((q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[0] + q[1] == n ? 4 : 0))
+                  : ((q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[2] == 0 ? 4 : 0) |
+                     (q[0] + q[1] + q[2] == n ? 8 : 0));
+}
+template <int DIM>
+__device__ __forceinline__ bool inside(int n, const int q[3]) {
+  return q[0] >= 0 && q[1] >= 0 && q[2] >= 0 && q[0] + q[1] + q[2] <= n;
+}
+
+// micro-edge directions of the refinement (2D triangles, 3D Kuhn tets)
+__constant__ int c_dir2[3][2] = {{1, 0}, {0, 1}, {1, -1}};
+__constant__ int c_dir3[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, -1, 0}, {1, 0, -1}, {0, 1, -1}, {1, -1, 1}};
+
+// ---- elementwise kernels ------------------------------------------------------
+
+template <class T>
+__global__ void k_jacobi(T* __restrict__ u, const T* __restrict__ b, const T* __restrict__ y,
+                         const T* __restrict__ dinv, T omega, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = u[i] + omega * dinv[i] * (b[i] - y[i]);
+}
+
+template <class T>
+__global__ void k_residual(T* __restrict__ r, const T* __restrict__ b, const T* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - y[i];
+}
+
+__global__ void k_to_f32(float* __restrict__ o, const double* __restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = __double2float_rn(v[i]);
+}
+
+__global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ e, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = u[i] + (double)e[i];
+}
+
+// ---- transfers --------------------------------------------------------------
+
+// Per-macro partial of (P^T r) at every coarse slot.
+template <class T, int DIM>
+__global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ bc, const unsigned* __restrict__ lpts_c,
+                           const T* __restrict__ multinv, int nc, int64_t Sc, int64_t Sf, int64_t total) {
+  constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
+  constexpr int ND = DIM == 2 ? 3 : 7;
+  const int nf = 2 * nc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = i / Sc;
+    int q[3];
+    unpack<DIM>(lpts_c[i - cell * Sc], q);
+    const int f[3] = {2 * q[0], 2 * q[1], 2 * q[2]};
+    const T* __restrict__ r = rf + cell * Sf;
+    const T* __restrict__ mi = multinv + cell * NCLS;
+    T acc = r[slotq<DIM>(nf, f)] * mi[pclass<DIM>(nf, f)];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+#pragma unroll
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        int j[3];
+        if (DIM == 2) {
+          j[0] = f[0] + sgn * c_dir2[k][0];
+          j[1] = f[1] + sgn * c_dir2[k][1];
+          j[2] = 0;
+        } else {
+          j[0] = f[0] + sgn * c_dir3[k][0];
+          j[1] = f[1] + sgn * c_dir3[k][1];
+          j[2] = f[2] + sgn * c_dir3[k][2];
+        }
+        if (inside<DIM>(nf, j)) acc += T(0.5) * r[slotq<DIM>(nf, j)] * mi[pclass<DIM>(nf, j)];
+      }
+    }
+    bc[i] = acc;
+  }
+}
+
+// Sum the copies' partials of every interface point in ascending macro order
+// and write the sum to all copies; Dirichlet points get zero.
+template <class T, int DIM>
+__global__ void __launch_bounds__(128) k_iface_sum_zero(T* __restrict__ v, const int4* __restrict__ items,
+                                                        const Prim* __restrict__ prims,
+                                                        const Inc* __restrict__ incs, int n, int64_t S) {
+  const int4 it = items[blockIdx.x];
+  const int a = it.z + threadIdx.x;
+  if (a >= it.w) return;
+  const Prim p = prims[it.x];
+  if (!p.boundary && p.inc_count == 1) return;
+  const int b = it.y;
+  int wv[3] = {0, 0, 0};
+  if (p.type == 0) {
+    wv[0] = n;
+  } else if (p.type == 1) {
+    wv[0] = n - a;
+    wv[1] = a;
+  } else {
+    wv[0] = n - a - b;
+    wv[1] = a;
+    wv[2] = b;
+  }
+  auto slot_of = [&](int i) -> int64_t {
+    const Inc inc = incs[p.inc_begin + i];
+    int q[3] = {0, 0, 0};
+    for (int j = 0; j <= p.type; ++j)
+      if (inc.corner[j] >= 1) q[inc.corner[j] - 1] += wv[j];
+    return (int64_t)inc.cell * S + slotq<DIM>(n, q);
+  };
+  T acc = T(0);
+  if (!p.boundary)
+    for (int i = 0; i < p.inc_count; ++i) acc += v[slot_of(i)];
+  for (int i = 0; i < p.inc_count; ++i) v[slot_of(i)] = acc;
+}
+
+// u_f += P e_c at every fine slot: coincident points copy, micro-edge
+// midpoints take the mean of the two coarse end points.
+template <class T, int DIM>
+__global__ void k_prolong_add(T* __restrict__ uf, const T* __restrict__ ec, const unsigned* __restrict__ lpts_f,
+                              int nc, int64_t Sc, int64_t Sf, int64_t total) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = i / Sf;
+    int q[3];
+    unpack<DIM>(lpts_f[i - cell * Sf], q);
+    const T* __restrict__ e = ec + cell * Sc;
+    const int px = q[0] & 1, py = q[1] & 1, pz = q[2] & 1;
+    T v;
+    if (!(px | py | pz)) {
+      const int c[3] = {q[0] >> 1, q[1] >> 1, q[2] >> 1};
+      v = e[slotq<DIM>(nc, c)];
+    } else {
+      int d[3] = {px, py, pz};
+      if (DIM == 2) {
+        if (px && py) d[1] = -1;  // the diagonal (1,-1)
+      } else {
+        if (px && py && !pz) d[1] = -1;        // (1,-1,0)
+        else if (px && pz && !py) d[2] = -1;   // (1,0,-1)
+        else if (py && pz && !px) d[2] = -1;   // (0,1,-1)
+        else if (px && py && pz) d[1] = -1;    // (1,-1,1)
+      }
+      const int c1[3] = {(q[0] - d[0]) >> 1, (q[1] - d[1]) >> 1, (q[2] - d[2]) >> 1};
+      const int c2[3] = {(q[0] + d[0]) >> 1, (q[1] + d[1]) >> 1, (q[2] + d[2]) >> 1};
+      v = T(0.5) * (e[slotq<DIM>(nc, c1)] + e[slotq<DIM>(nc, c2)]);
+    }
+    uf[i] = uf[i] + v;
+  }
+}
+
+// Level 0: e = A0^{-1} r on the coarse vertices, written to every copy.
+template <class T>
+__global__ void k_coarse_solve(T* __restrict__ e, const T* __restrict__ r, const T* __restrict__ a0inv,
+                               const int* __restrict__ v_of_slot, const int* __restrict__ slot_of_v, int V,
+                               int64_t nslots) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots; s += (int64_t)gridDim.x * blockDim.x) {
+    const T* __restrict__ row = a0inv + (int64_t)v_of_slot[s] * V;
+    T acc = T(0);
+    for (int j = 0; j < V; ++j) acc += row[j] * r[slot_of_v[j]];
+    e[s] = acc;
+  }
+}
+
+// Deterministic two-stage sum of owner[i] * a[i] * b[i] (float64).
+template <class T>
+__global__ void k_dot_partial(const T* __restrict__ a, const T* __restrict__ b, const unsigned char* __restrict__ owner,
+                              int64_t n, double* __restrict__ partial) {
+  __shared__ double sm[THREADS];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (owner[i]) acc += (double)a[i] * (double)b[i];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+__global__ void k_dot_final(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  __shared__ double sm[THREADS];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += THREADS) acc += partial[i];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
+int grid_for(int64_t n) {
+  const int64_t g = (n + THREADS - 1) / THREADS;
+  return int(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
+}
+
+template <class T>
+struct Vecs;
+template <>
+struct Vecs<float> {
+  static float* u(MgLevel& g) { return g.u32; }
+  static float* b(MgLevel& g) { return g.b32; }
+  static float* y(MgLevel& g) { return g.y32; }
+  static float* r(MgLevel& g) { return g.r32; }
+  static const float* dinv(const MgLevel& g) { return g.dinv32; }
+  static const float* multinv(const MgLevel& g) { return g.multinv32; }
+  static const float* a0inv(const Solver& s) { return s.a0inv32; }
+  static constexpr int dtype = 2;  // fp32 apply
+};
+template <>
+struct Vecs<double> {
+  static double* u(MgLevel& g) { return g.u64; }
+  static double* b(MgLevel& g) { return g.b64; }
+  static double* y(MgLevel& g) { return g.y64; }
+  static double* r(MgLevel& g) { return g.r64; }
+  static const double* dinv(const MgLevel& g) { return g.dinv64; }
+  static const double* multinv(const MgLevel& g) { return g.multinv64; }
+  static const double* a0inv(const Solver& s) { return s.a0inv64; }
+  static constexpr int dtype = 1;  // float64 data, float-float apply
+};
+
+#define HY_TRY(x)                          \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) return e_;      \
+  } while (0)
+
+template <class T>
+cudaError_t restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t s) {
+  const Solver& sv = *m.solver;
+  const LevelDev& Lc = m.levels[lf - 1];
+  const LevelDev& Lf = m.levels[lf];
+  const int64_t total = Lc.slots_per_macro * m.n_cells;
+  const MgLevel& gc = sv.lv[lf - 1];
+  if (m.dim == 2)
+    k_restrict<T, 2><<<grid_for(total), THREADS, 0, s>>>(rf, bc, gc.lpts, Vecs<T>::multinv(gc), Lc.n,
+                                                          Lc.slots_per_macro, Lf.slots_per_macro, total);
+  else
+    k_restrict<T, 3><<<grid_for(total), THREADS, 0, s>>>(rf, bc, gc.lpts, Vecs<T>::multinv(gc), Lc.n,
+                                                          Lc.slots_per_macro, Lf.slots_per_macro, total);
+  HY_TRY(cudaGetLastError());
+  if (Lc.n_items > 0) {
+    if (m.dim == 2)
+      k_iface_sum_zero<T, 2><<<Lc.n_items, 128, 0, s>>>(bc, Lc.items, m.d_prims, m.d_incs, Lc.n, Lc.slots_per_macro);
+    else
+      k_iface_sum_zero<T, 3><<<Lc.n_items, 128, 0, s>>>(bc, Lc.items, m.d_prims, m.d_incs, Lc.n, Lc.slots_per_macro);
+  }
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t prolong_add_t(const Mesh& m, int lf, const T* ec, T* uf, cudaStream_t s) {
+  const Solver& sv = *m.solver;
+  const LevelDev& Lc = m.levels[lf - 1];
+  const LevelDev& Lf = m.levels[lf];
+  const int64_t total = Lf.slots_per_macro * m.n_cells;
+  if (m.dim == 2)
+    k_prolong_add<T, 2><<<grid_for(total), THREADS, 0, s>>>(uf, ec, sv.lv[lf].lpts, Lc.n, Lc.slots_per_macro,
+                                                             Lf.slots_per_macro, total);
+  else
+    k_prolong_add<T, 3><<<grid_for(total), THREADS, 0, s>>>(uf, ec, sv.lv[lf].lpts, Lc.n, Lc.slots_per_macro,
+                                                             Lf.slots_per_macro, total);
+  return cudaGetLastError();
+}
+
+// One V(nu1, nu2) cycle on level l for A u = b (u updated in place).
+template <class T>
+cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s) {
+  Solver& sv = *m.solver;
+  MgLevel& g = sv.lv[l];
+  const int64_t ns = m.levels[l].slots_per_macro * m.n_cells;
+  const char* what;
+  if (l == 0) {
+    k_coarse_solve<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, Vecs<T>::a0inv(sv), sv.v_of_slot0, sv.slot_of_v0,
+                                                       sv.nv0, ns);
+    return cudaGetLastError();
+  }
+  T* y = Vecs<T>::y(g);
+  T* r = Vecs<T>::r(g);
+  const T omega = T(sv.omega);
+  for (int it = 0; it < sv.nu1; ++it) {
+    HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
+    k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
+    HY_TRY(cudaGetLastError());
+  }
+  HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
+  k_residual<T><<<grid_for(ns), THREADS, 0, s>>>(r, b, y, ns);
+  HY_TRY(cudaGetLastError());
+  MgLevel& gc = sv.lv[l - 1];
+  T* bc = Vecs<T>::b(gc);
+  T* uc = Vecs<T>::u(gc);
+  HY_TRY(restrict_t<T>(m, l, r, bc, s));
+  HY_TRY(cudaMemsetAsync(uc, 0, sizeof(T) * m.levels[l - 1].slots_per_macro * m.n_cells, s));
+  HY_TRY(vcycle_t<T>(m, l - 1, bc, uc, s));
+  HY_TRY(prolong_add_t<T>(m, l, uc, u, s));
+  for (int it = 0; it < sv.nu2; ++it) {
+    HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
+    k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
+    HY_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+// ||v||_2 over one copy of every non-Dirichlet DoF, to host (synchronises s).
+template <class T>
+cudaError_t norm2(const Mesh& m, int l, const T* v, double* out, cudaStream_t s) {
+  const Solver& sv = *m.solver;
+  const int64_t ns = m.levels[l].slots_per_macro * m.n_cells;
+  k_dot_partial<T><<<RED_BLOCKS, THREADS, 0, s>>>(v, v, sv.lv[l].owner, ns, sv.red);
+  HY_TRY(cudaGetLastError());
+  k_dot_final<<<1, THREADS, 0, s>>>(sv.red, RED_BLOCKS, sv.red + RED_BLOCKS);
+  HY_TRY(cudaGetLastError());
+  double h = 0.0;
+  HY_TRY(cudaMemcpyAsync(&h, sv.red + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HY_TRY(cudaStreamSynchronize(s));
+  *out = sqrt(h);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t mg_restrict(const Mesh& m, int lf, int dtype, const void* rf, void* bc, cudaStream_t s) {
+  return dtype == 2 ? restrict_t<float>(m, lf, (const float*)rf, (float*)bc, s)
+                    : restrict_t<double>(m, lf, (const double*)rf, (double*)bc, s);
+}
+
+cudaError_t mg_prolong_add(const Mesh& m, int lf, int dtype, const void* ec, void* uf, cudaStream_t s) {
+  return dtype == 2 ? prolong_add_t<float>(m, lf, (const float*)ec, (float*)uf, s)
+                    : prolong_add_t<double>(m, lf, (const double*)ec, (double*)uf, s);
+}
+
+cudaError_t mg_vcycle(Mesh& m, int l, int dtype, const void* b, void* u, cudaStream_t s) {
+  return dtype == 2 ? vcycle_t<float>(m, l, (const float*)b, (float*)u, s)
+                    : vcycle_t<double>(m, l, (const double*)b, (double*)u, s);
+}
+
+cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, double rtol, int max_iter,
+                     cudaStream_t s, int* iters, double* relres) {
+  Solver& sv = *m.solver;
+  MgLevel& g = sv.lv[l];
+  const int64_t ns = m.levels[l].slots_per_macro * m.n_cells;
+  const char* what;
+  double nb = 0.0;
+  HY_TRY(norm2<double>(m, l, b, &nb, s));
+  if (nb == 0.0) nb = 1.0;
+  double rel = 0.0;
+  int it = 0;
+  for (;; ++it) {
+    // float64 residual r = b - A u
+    HY_TRY(launch_apply(m, l, 1, u, g.y64, s, nullptr, &what));
+    k_residual<double><<<grid_for(ns), THREADS, 0, s>>>(g.r64, b, g.y64, ns);
+    HY_TRY(cudaGetLastError());
+    double nr = 0.0;
+    HY_TRY(norm2<double>(m, l, g.r64, &nr, s));
+    rel = nr / nb;
+    if (rel <= rtol || it >= max_iter) break;
+    if (mode == 2) {
+      // fp32 V-cycle on the residual equation, float64 update
+      k_to_f32<<<grid_for(ns), THREADS, 0, s>>>(g.b32, g.r64, ns);
+      HY_TRY(cudaGetLastError());
+      HY_TRY(cudaMemsetAsync(g.u32, 0, sizeof(float) * ns, s));
+      HY_TRY(vcycle_t<float>(m, l, g.b32, g.u32, s));
+      k_add_f32<<<grid_for(ns), THREADS, 0, s>>>(u, g.u32, ns);
+      HY_TRY(cudaGetLastError());
+    } else {
+      HY_TRY(vcycle_t<double>(m, l, b, u, s));
+    }
+  }
+  *iters = it;
+  *relres = rel;
+  return cudaSuccess;
+}
+
+}  // namespace hyteg

@@ -6,7 +6,7 @@ import ctypes
 import numpy as np
 
 from . import _capi as C
-from ._capi import F64, F32, F64_IEEE, BC_NONE, BC_DIRICHLET, HytegError
+from ._capi import F64, F32, F64_IEEE, BC_NONE, BC_DIRICHLET, SOLVE_F64, SOLVE_MIXED, HytegError
 
 _ELEM = {F64: 8, F32: 4, F64_IEEE: 8}
 
@@ -127,3 +127,62 @@ class Mesh:
                                        ctypes.c_void_p(y_host.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
                 "hyteg_apply_host")
         return y_host
+
+    # ---- geometry -------------------------------------------------------------
+    def slot_coords(self, level: int) -> np.ndarray:
+        """Coordinates of every slot, float64 [n_slots, dim]."""
+        ns, _ = self.num_slots(level)
+        out = np.empty((ns, self.dim), dtype=np.float64)
+        C.check(C.lib.hyteg_slot_coords(self._h, level, out.ctypes.data_as(C.c_dblp)), "hyteg_slot_coords")
+        return out
+
+    def lumped_mass(self, level: int) -> np.ndarray:
+        """Lumped P1 mass of every slot (copies hold the full value)."""
+        ns, _ = self.num_slots(level)
+        out = np.empty(ns, dtype=np.float64)
+        C.check(C.lib.hyteg_lumped_mass(self._h, level, out.ctypes.data_as(C.c_dblp)), "hyteg_lumped_mass")
+        return out
+
+    def dirichlet_mask(self, level: int) -> np.ndarray:
+        """True for every slot of a Dirichlet DoF."""
+        ns, _ = self.num_slots(level)
+        out = np.empty(ns, dtype=np.uint8)
+        C.check(C.lib.hyteg_dirichlet_mask(self._h, level, ctypes.c_void_p(out.ctypes.data)), "hyteg_dirichlet_mask")
+        return out.astype(bool)
+
+    # ---- multigrid --------------------------------------------------------------
+    def solver_setup(self, max_level: int, nu1: int = 3, nu2: int = 3, omega: float = 2.0 / 3.0) -> "Mesh":
+        C.check(C.lib.hyteg_solver_setup(self._h, max_level, nu1, nu2, omega), "hyteg_solver_setup")
+        return self
+
+    def restrict(self, fine_level: int, r_fine, b_coarse, stream=None):
+        code = self._dtype_code(r_fine, False)
+        C.check(C.lib.hyteg_restrict(self._h, fine_level, code, ctypes.c_void_p(r_fine.data_ptr()),
+                                     ctypes.c_void_p(b_coarse.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+                "hyteg_restrict")
+        return b_coarse
+
+    def prolong_add(self, fine_level: int, e_coarse, u_fine, stream=None):
+        code = self._dtype_code(u_fine, False)
+        C.check(C.lib.hyteg_prolong_add(self._h, fine_level, code, ctypes.c_void_p(e_coarse.data_ptr()),
+                                        ctypes.c_void_p(u_fine.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+                "hyteg_prolong_add")
+        return u_fine
+
+    def vcycle(self, level: int, b, u, stream=None):
+        code = self._dtype_code(u, False)
+        C.check(C.lib.hyteg_vcycle(self._h, level, code, ctypes.c_void_p(b.data_ptr()),
+                                   ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+                "hyteg_vcycle")
+        return u
+
+    def solve(self, level: int, b, u, mode: int = SOLVE_MIXED, rtol: float = 1e-10, max_iter: int = 100,
+              stream=None):
+        """Solve A u = b (float64 device tensors, u = initial guess);
+        returns (iterations, relative residual)."""
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        C.check(C.lib.hyteg_solve(self._h, level, mode, ctypes.c_void_p(b.data_ptr()),
+                                  ctypes.c_void_p(u.data_ptr()), rtol, max_iter,
+                                  ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(it), ctypes.byref(rel)),
+                "hyteg_solve")
+        return it.value, rel.value

@@ -112,3 +112,21 @@ def test_boundary_modes_count(lib):
     for bc in (0, 1):
         M = lib.Mesh(m.coords, m.cells, bc)
         assert M.num_slots(2)[1] == 81
+
+
+@pytest.mark.parametrize("dim,k,L", [(2, 4, 0), (2, 4, 3), (3, 2, 2), (3, 1, 3)])
+def test_slot_coords_and_lumped_mass_match_oracle(lib, dim, k, L):
+    import oracle.multigrid as omg
+    m = unit_square_mesh(k, 0.15, 1) if dim == 2 else unit_cube_kuhn_mesh(k, 0.1, 1)
+    M = lib.Mesh(m.coords, m.cells)
+    rm = oracle.RefinedMesh(m.coords, m.cells, L)
+    smap = M.dof_map(L)
+    xyz = M.slot_coords(L)
+    np.testing.assert_allclose(xyz, rm.coords[smap], rtol=0, atol=1e-14)
+    mass = M.lumped_mass(L)
+    np.testing.assert_allclose(mass, omg.lumped_mass(rm)[smap], rtol=1e-13, atol=0)
+    # copies of one vertex are bitwise equal
+    order = np.argsort(smap, kind="stable")
+    same = smap[order][1:] == smap[order][:-1]
+    assert np.array_equal(xyz[order][1:][same], xyz[order][:-1][same])
+    assert np.array_equal(mass[order][1:][same], mass[order][:-1][same])
