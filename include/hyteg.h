@@ -206,9 +206,16 @@ int hyteg_vcycle(hyteg_mesh* mesh, int level, int dtype, const void* b, void* u,
  * norms taken over the non-Dirichlet DoFs (one copy each) with the float64
  * residual, or max_iter iterations.  HYTEG_SOLVE_F64: one float64 V-cycle per
  * iteration; HYTEG_SOLVE_MIXED: one fp32 V-cycle on the residual equation per
- * iteration and a float64 update (iterative refinement).  Synchronises
- * `stream` once per iteration to read the residual norm.  *iters receives the
- * iterations done, *relres the final relative residual.
+ * iteration and a float64 update (iterative refinement).  Both modes are
+ * residual corrections: the float64 residual is computed in difference form,
+ * sum_k a_ik (u_k - u_i), whose terms stay small for smooth u, so it remains
+ * accurate when A u nearly cancels b.  The loop also stops when two
+ * consecutive iterations fail to halve the residual: the attainable relative
+ * residual of a float64 u grows like h^-2 (about 1e-11 at level 8 and 2e-10
+ * at level 10 for the unit-square Poisson problem), and *relres then reports
+ * that floor.  Synchronises `stream` once per iteration to read the residual
+ * norm.  *iters receives the iterations done, *relres the final relative
+ * residual.
  * Errors: HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA. */
 int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double rtol, int max_iter,
                 void* stream, int* iters, double* relres);
