@@ -93,6 +93,18 @@ __device__ __forceinline__ int tri_row(int q, int K) {
   return y;
 }
 
+// tri_row with a fast reciprocal square root; the integer fix-ups make the
+// result exact whenever the estimate is within one row.
+__device__ __forceinline__ int tri_row_fast(int q, int K) {
+  const float b = 2.0f * K + 1.0f;
+  const float d = fmaxf(b * b - 8.0f * q, 1.0f);
+  int y = (int)((b - d * rsqrtf(d)) * 0.5f);
+  y = max(y, 0);
+  if (y * K - (y * (y - 1)) / 2 > q) --y;
+  if ((y + 1) * K - ((y + 1) * y) / 2 <= q) ++y;
+  return y;
+}
+
 constexpr int NRING = 4;  // slices z-1, z, z+1 being read, z+2 being filled
 
 template <class P>
@@ -119,7 +131,6 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
   T* __restrict__ ym = y + (int64_t)m * S;
   const int N = n + 1;
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
 
   // zero the ring (guards and stale tails must hold finite values), class weights
   for (int i = tid; i < NRING * stride; i += SLAB_THREADS) ring[i] = SS::zero();
@@ -159,23 +170,20 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
     const int bz = roff(z), bu = roff(z + 1), bd = roff(z - 1);
 
     // ---- interior points: x, y >= 1, x + y <= K = M - 2 (z >= 1) ---------
-    // Row y holds K - y points; rows y and K - y together hold K <= 63
-    // points, so one warp takes such a pair and each lane two points
-    // (positions lane and lane + 32), evaluated together.
+    // The cnt = (K-1)K/2 interior points of the slice are enumerated row by
+    // row; every thread evaluates two of them together (q and q + 256).
     if (z >= 1 && M >= 4) {
       const int K = M - 2;
-      const int units = K / 2;  // pairs y = 1 .. (K-1)/2, plus the middle row when K is even
-      for (int u = warp; u < units; u += SLAB_THREADS / 32) {
-        const int ya = u + 1, yb = K - ya;  // yb == ya: the middle row, alone
-        const int la = K - ya;              // points in row ya
-        const int total = (ya == yb) ? la : K;
+      const int cnt = (K - 1) * K / 2;
+      for (int q0 = tid; q0 < cnt; q0 += 2 * SLAB_THREADS) {
+        const int q1 = min(q0 + SLAB_THREADS, cnt - 1);  // past the end: repeat a valid point
         int p[2], yy[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int t = min(lane + 32 * h, total - 1);  // out-of-range lanes repeat a valid point
-          const bool first_row = t < la;
-          yy[h] = first_row ? ya : yb;
-          const int xx = first_row ? t + 1 : t - la + 1;
+          const int q = h ? q1 : q0;
+          const int j = tri_row_fast(q, K - 1);  // row y = j + 1 holds K - 1 - j points
+          yy[h] = j + 1;
+          const int xx = q - (j * (K - 1) - (j * (j - 1)) / 2) + 1;
           p[h] = yy[h] * M - (yy[h] * (yy[h] - 1)) / 2 + xx;
         }
         // ring offsets of the point in slices z, z+1, z-1 and the row gap A = M - y
@@ -195,8 +203,8 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
         P::add_sym(a, w[10], at(qu0 - A0 + 1, qu1 - A1 + 1), at(qd0 + A0, qd1 + A1));     // ±(1,-1,1)
         T r0, r1;
         P::finish(a, r0, r1);
-        if (lane < total) ym[zoff + p[0]] = r0;
-        if (lane + 32 < total) ym[zoff + p[1]] = r1;
+        ym[zoff + p[0]] = r0;
+        if (q0 + SLAB_THREADS < cnt) ym[zoff + p[1]] = r1;
       }
     }
     // ---- macro-boundary points of the slice: partial rows ---------------------
