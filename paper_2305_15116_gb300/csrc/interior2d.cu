@@ -69,7 +69,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Rows in flight per warp: each lane stages its two columns of the next RING
 // rows in shared memory with cp.async, so a warp keeps RING rows outstanding
 // without holding them in registers.
-constexpr int RING = 8;
+constexpr int RING = 8;  // a power of two
+static_assert((RING & (RING - 1)) == 0, "RING must be a power of two");
 constexpr int THREADS2D = 256;
 
 template <class P>
@@ -112,35 +113,47 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* _
   cr.init(n, t.y - 1);
   auto take = [&](int k) -> Row<P> {
     cp_async_wait<RING - 1>();
-    const T va = ring[k % RING][lane][0], vb = ring[k % RING][lane][1];
+    const T va = ring[k & (RING - 1)][lane][0], vb = ring[k & (RING - 1)][lane][1];
     const Row<P> r = make_row<P>(ca < cr.len ? P::conv(va) : P::zero(), cb < cr.len ? P::conv(vb) : P::zero());
     // the slot of step k is free again: stage step k + RING
-    if (k + RING < steps) stage(k % RING);
+    if (k + RING < steps) stage(k & (RING - 1));
     cp_async_commit();
     cr.next();
     return r;
   };
-  Row<P> prv = take(0);
-  Cursor out = cr;  // the row being written
-  Row<P> cur = take(1);
+  Cursor out = cr;  // the row being written (set after the first take)
   const bool wa = lane >= 1, wbb = lane <= 30;  // lane 0's A and lane 31's B are halo
-  for (int k = 2; k < steps; ++k) {
-    const Row<P> nxt = take(k);
+  // output row from (below, centre, above)
+  auto step = [&](const Row<P>& lo, const Row<P>& ce, const Row<P>& hi) {
     // the interior stencil is symmetric (w(d) = w(-d), made bitwise equal on
     // the host): add opposite neighbours first
     typename P::Acc a;
-    P::first(a, wC, cur.v);
-    P::add_sym(a, wE, cur.e, cur.w);
-    P::add_sym(a, wN, nxt.v, prv.v);
-    P::add_sym(a, wSE, prv.e, nxt.w);
+    P::first(a, wC, ce.v);
+    P::add_sym(a, wE, ce.e, ce.w);
+    P::add_sym(a, wN, hi.v, lo.v);
+    P::add_sym(a, wSE, lo.e, hi.w);
     T outa, outb;
     P::finish(a, outa, outb);
     // point (c, r) is interior when c <= n - 1 - r, i.e. c < len - 1
     if (wa && ca < out.len - 1) ym[out.off + ca] = outa;
     if (wbb && cb < out.len - 1) ym[out.off + cb] = outb;
     out.next();
-    prv = cur;
-    cur = nxt;
+  };
+  // three rows in registers whose roles rotate, unrolled by three so that no
+  // row is ever copied between registers
+  Row<P> r0 = take(0);
+  out = cr;
+  Row<P> r1 = take(1);
+  Row<P> r2;
+  for (int k = 2; k < steps; k += 3) {
+    r2 = take(k);
+    step(r0, r1, r2);
+    if (k + 1 >= steps) break;
+    r0 = take(k + 1);
+    step(r1, r2, r0);
+    if (k + 2 >= steps) break;
+    r1 = take(k + 2);
+    step(r2, r0, r1);
   }
   cp_async_wait<0>();
 }
