@@ -53,6 +53,9 @@ extern "C" {
 #define HYTEG_ECUDA     -3   /* a CUDA runtime call or kernel launch failed */
 #define HYTEG_EMESH     -4   /* coarse mesh is invalid (degenerate cell, non-conforming) */
 #define HYTEG_ESTATE    -5   /* call out of order (e.g. apply before refine) */
+#define HYTEG_EAGAIN    -6   /* admission refused for now: the request does not fit the server's
+                                memory cap beside the requests in flight; retry later */
+#define HYTEG_ETIMEDOUT -7   /* a bounded wait ran out before the awaited event */
 
 /* ---- arithmetic / storage types of the apply --------------------------- */
 #define HYTEG_F64       1    /* float64 vectors; float-float (2 x fp32) arithmetic
@@ -219,6 +222,117 @@ int hyteg_vcycle(hyteg_mesh* mesh, int level, int dtype, const void* b, void* u,
  * Errors: HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA. */
 int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double rtol, int max_iter,
                 void* stream, int* iters, double* relres);
+
+/* ---- the Poisson model problem -----------------------------------------
+ * -Laplace u = f in the domain of the coarse mesh, u = 0 on its boundary,
+ * discretised with the P1 stiffness matrix of the refined mesh (Sec. 1.1)
+ * and a lumped-mass load vector.  Both calls need hyteg_solver_setup to cover
+ * `level` (they use its per-level tables); vectors are float64 device arrays.
+ *
+ * hyteg_poisson_rhs writes, in the slot layout (every copy),
+ *   b_i = m_i (f(p_i) + noise * g_i) off the Dirichlet boundary, 0 on it,
+ * with m_i = |supp phi_i| / (d+1) (lumped P1 mass), f(p) = prod_k sin(pi p_k)
+ * at the DoF's point p_i, and g_i the standard normal deviate of global DoF id
+ * i under `seed`: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
+ * counter (i mod 2^32, i >> 32, 0, 0) and key (seed mod 2^32, seed >> 32);
+ * words w0, w1 give u1 = (w0 + 1) 2^-32, u2 = w1 2^-32 and
+ * g = sqrt(-2 ln u1) cos(2 pi u2).  Global ids as hyteg_dof_map.  The first
+ * call on a mesh uploads small geometry tables (synchronous); later calls are
+ * asynchronous on `stream`.
+ * Errors: HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA, HYTEG_ENOMEM. */
+int hyteg_poisson_rhs(hyteg_mesh* mesh, int level, uint64_t seed, double noise, double* b, void* stream);
+
+/* v_global[gid(s)] = v[s]: a slot-layout vector (copies equal) in the global
+ * numbering of hyteg_dof_map, v_global a device array of n_global float64.
+ * Asynchronous on `stream`.  Errors: HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA. */
+int hyteg_to_global(const hyteg_mesh* mesh, int level, const double* v, double* v_global, void* stream);
+
+/* ---- solve server -----------------------------------------------------------
+ * Serves Poisson solve requests, each a coarse mesh, a level and a right-hand
+ * side seed, on one GPU.  The paper has no serving layer; this one runs the
+ * solver above for many independent problems at once.
+ *  - Worker threads, each with its own CUDA stream, take requests in arrival
+ *    order as soon as they are free (continuous batching: a new request starts
+ *    while others are mid-solve, and their kernels share the GPU).
+ *  - Device memory comes from one arena of mem_cap bytes reserved at
+ *    creation; a request is admitted only while the estimated device bytes of
+ *    the requests in flight plus its own stay within the cap (else
+ *    HYTEG_EAGAIN).  Refined meshes with their solver workspace stay cached
+ *    after a request and serve later requests on the same coarse mesh and
+ *    level; idle cached meshes are dropped, least recently used first, when a
+ *    new one needs the room.
+ *  - Every request's result is independent of the others in flight: the same
+ *    request gives bitwise the same solution alone or in a batch. */
+typedef struct hyteg_server hyteg_server;  /* opaque, owned by the library */
+
+typedef struct hyteg_request {
+  int dim;                /* 2 or 3 */
+  int64_t n_verts;        /* coarse mesh as for hyteg_mesh_create (Dirichlet rows on its boundary); */
+  const double* coords;   /*   the arrays are copied by hyteg_server_submit                          */
+  int64_t n_cells;
+  const int64_t* cells;
+  int level;              /* refinement level of the solve, 1..12 (2D), 1..8 (3D) */
+  int mode;               /* HYTEG_SOLVE_MIXED or HYTEG_SOLVE_F64 */
+  double rtol;            /* relative residual target, > 0 */
+  int max_iter;           /* iteration limit, >= 0 */
+  uint64_t seed;          /* right-hand side as hyteg_poisson_rhs(seed, noise) */
+  double noise;
+  double* u_out;          /* nullable host array [n_global]: the solution in global numbering,
+                             written before the request turns HYTEG_REQ_DONE; must stay valid until then */
+  double* b_out;          /* nullable host array [n_global]: the right-hand side, likewise */
+} hyteg_request;
+
+#define HYTEG_REQ_QUEUED   0
+#define HYTEG_REQ_RUNNING  1
+#define HYTEG_REQ_DONE     2
+#define HYTEG_REQ_FAILED   3
+
+typedef struct hyteg_result {
+  int status;       /* HYTEG_REQ_* */
+  int error;        /* HYTEG_OK, or the error code of a failed request */
+  int iters;        /* solver iterations (done requests) */
+  int cache_hit;    /* 1 if the request reused a cached refined mesh */
+  double relres;    /* final relative residual (done requests) */
+  double queue_s;   /* seconds from submission to the start of the work */
+  double run_s;     /* seconds from the start to the end of the work */
+  int64_t n_global; /* DoFs of the request's problem */
+} hyteg_result;
+
+/* Creates a server on `device` with a device arena of mem_cap bytes and
+ * n_workers worker threads (1..64).  Errors: HYTEG_EINVAL, HYTEG_ENOMEM,
+ * HYTEG_ECUDA. */
+int hyteg_server_create(int device, size_t mem_cap, int n_workers, hyteg_server** out);
+
+/* Validates and enqueues a request; *ticket identifies it.  Errors:
+ * HYTEG_EINVAL (bad request, or one that can never fit the cap),
+ * HYTEG_EAGAIN (does not fit beside the requests in flight: retry later),
+ * HYTEG_ESTATE (server shutting down). */
+int hyteg_server_submit(hyteg_server* server, const hyteg_request* req, uint64_t* ticket);
+
+/* Current state of a request.  Errors: HYTEG_EINVAL (unknown ticket). */
+int hyteg_server_poll(hyteg_server* server, uint64_t ticket, hyteg_result* out);
+
+/* Waits at most timeout_s seconds for the request to finish, then reports
+ * as hyteg_server_poll.  Errors: HYTEG_EINVAL, HYTEG_ETIMEDOUT (not finished;
+ * *out still holds its current state). */
+int hyteg_server_wait(hyteg_server* server, uint64_t ticket, double timeout_s, hyteg_result* out);
+
+/* Forgets a finished request.  Errors: HYTEG_EINVAL (unknown ticket),
+ * HYTEG_ESTATE (not finished). */
+int hyteg_server_release(hyteg_server* server, uint64_t ticket);
+
+typedef struct hyteg_server_stats {
+  int64_t submitted, done, failed, in_flight;
+  int64_t cached_meshes, cache_hits, evictions;
+  size_t reserved_bytes;  /* estimated bytes of the requests in flight */
+  size_t arena_used;      /* bytes of the arena in use (requests and cache) */
+} hyteg_server_stats;
+
+int hyteg_server_stats_get(hyteg_server* server, hyteg_server_stats* out);
+
+/* Stops the server: queued requests fail with HYTEG_ESTATE, running ones are
+ * finished, the workers are joined and all device memory is released. */
+void hyteg_server_destroy(hyteg_server* server);
 
 /* Staging limit of hyteg_apply_host_static: bytes per vector (16 MiB, i.e.
  * 2,097,152 float64 or 4,194,304 float32 slots). */

@@ -9,6 +9,8 @@ from .meshes import (
     CoarseMesh,
     unit_square_mesh,
     unit_cube_kuhn_mesh,
+    rect_mesh,
+    box_kuhn_mesh,
     random_vector,
     random_normal,
     workload,
@@ -19,6 +21,8 @@ __all__ = [
     "CoarseMesh",
     "unit_square_mesh",
     "unit_cube_kuhn_mesh",
+    "rect_mesh",
+    "box_kuhn_mesh",
     "random_vector",
     "random_normal",
     "workload",

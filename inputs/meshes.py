@@ -60,51 +60,68 @@ def _jitter_interior(coords: np.ndarray, amplitude: float, seed: int) -> np.ndar
 
 def unit_square_mesh(k: int, jitter: float = 0.0, seed: int = 0) -> CoarseMesh:
     """k x k cells of the unit square, each split along its (0,0)-(1,1)
-    diagonal into two right triangles.
+    diagonal into two right triangles (see `rect_mesh`)."""
+    return rect_mesh(k, k, jitter, seed)
 
-    Vertex id of grid point (i, j) is i + (k+1) j.  For cell (i, j) with
+
+def rect_mesh(kx: int, ky: int, jitter: float = 0.0, seed: int = 0) -> CoarseMesh:
+    """kx x ky cells of the unit square, each split along its (0,0)-(1,1)
+    diagonal into two triangles.
+
+    Vertex id of grid point (i, j) is i + (kx+1) j.  For cell (i, j) with
     corners a=(i,j), b=(i+1,j), c=(i,j+1), d=(i+1,j+1) the triangles are
-    (b, d, a) and (c, a, d): right angle first, counter-clockwise.  Cells are
-    listed cell-row by cell-row, lower-right triangle first.  `jitter` is the
-    amplitude as a fraction of the cell width h = 1/k.
+    (b, d, a) and (c, a, d): right angle (for square cells) first,
+    counter-clockwise.  Cells are listed cell-row by cell-row, lower-right
+    triangle first.  `jitter` is the amplitude as a fraction of the smaller
+    cell width min(1/kx, 1/ky).
     """
-    g = np.linspace(0.0, 1.0, k + 1)
-    xx, yy = np.meshgrid(g, g, indexing="xy")
+    gx = np.linspace(0.0, 1.0, kx + 1)
+    gy = np.linspace(0.0, 1.0, ky + 1)
+    xx, yy = np.meshgrid(gx, gy, indexing="xy")
     coords = np.stack([xx.ravel(), yy.ravel()], axis=1).astype(np.float64)
     cells = []
-    for j in range(k):
-        for i in range(k):
-            a = i + (k + 1) * j
+    for j in range(ky):
+        for i in range(kx):
+            a = i + (kx + 1) * j
             b = a + 1
-            c = a + (k + 1)
+            c = a + (kx + 1)
             d = c + 1
             cells.append((b, d, a))
             cells.append((c, a, d))
-    coords = _jitter_interior(coords, jitter / k, seed)
-    name = f"square{k}x{k}" + (f"_jit{jitter}_s{seed}" if jitter else "")
+    coords = _jitter_interior(coords, jitter / max(kx, ky), seed)
+    name = (f"square{kx}x{ky}" if kx == ky else f"rect{kx}x{ky}") + (f"_jit{jitter}_s{seed}" if jitter else "")
     return CoarseMesh(2, coords, np.asarray(cells, dtype=np.int64), name)
 
 
 def unit_cube_kuhn_mesh(k: int, jitter: float = 0.0, seed: int = 0) -> CoarseMesh:
     """k x k x k cells of the unit cube, each split into the 6 Kuhn tetrahedra
-    that share the cell's main diagonal.
+    that share the cell's main diagonal (see `box_kuhn_mesh`)."""
+    return box_kuhn_mesh(k, k, k, jitter, seed)
 
-    Vertex id of grid point (i, j, l) is i + (k+1) j + (k+1)^2 l.  The tet of a
-    permutation (p, q, r) of the axes has vertices corner, corner + e_p,
-    corner + e_p + e_q, corner + (1,1,1), in that order.  Permutations are taken
-    in itertools order; cells are listed cell by cell (i fastest).
+
+def box_kuhn_mesh(kx: int, ky: int, kz: int, jitter: float = 0.0, seed: int = 0) -> CoarseMesh:
+    """kx x ky x kz cells of the unit cube, each split into the 6 Kuhn
+    tetrahedra that share the cell's main diagonal.
+
+    Vertex id of grid point (i, j, l) is i + (kx+1) j + (kx+1)(ky+1) l.  The
+    tet of a permutation (p, q, r) of the axes has vertices corner,
+    corner + e_p, corner + e_p + e_q, corner + (1,1,1), in that order.
+    Permutations are taken in itertools order; cells are listed cell by cell
+    (i fastest).  `jitter` is a fraction of the smallest cell width.
     """
-    g = np.linspace(0.0, 1.0, k + 1)
-    zz, yy, xx = np.meshgrid(g, g, g, indexing="ij")
+    gx = np.linspace(0.0, 1.0, kx + 1)
+    gy = np.linspace(0.0, 1.0, ky + 1)
+    gz = np.linspace(0.0, 1.0, kz + 1)
+    zz, yy, xx = np.meshgrid(gz, gy, gx, indexing="ij")
     coords = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1).astype(np.float64)
 
     def vid(i, j, l):
-        return i + (k + 1) * j + (k + 1) ** 2 * l
+        return i + (kx + 1) * j + (kx + 1) * (ky + 1) * l
 
     cells = []
-    for l in range(k):
-        for j in range(k):
-            for i in range(k):
+    for l in range(kz):
+        for j in range(ky):
+            for i in range(kx):
                 base = np.array([i, j, l])
                 for perm in permutations(range(3)):
                     p0 = base.copy()
@@ -114,8 +131,9 @@ def unit_cube_kuhn_mesh(k: int, jitter: float = 0.0, seed: int = 0) -> CoarseMes
                     p2[perm[1]] += 1
                     p3 = base + 1
                     cells.append(tuple(vid(*p) for p in (p0, p1, p2, p3)))
-    coords = _jitter_interior(coords, jitter / k, seed)
-    name = f"cube{k}^3kuhn" + (f"_jit{jitter}_s{seed}" if jitter else "")
+    coords = _jitter_interior(coords, jitter / max(kx, ky, kz), seed)
+    name = (f"cube{kx}^3kuhn" if kx == ky == kz else f"box{kx}x{ky}x{kz}kuhn") + (
+        f"_jit{jitter}_s{seed}" if jitter else "")
     return CoarseMesh(3, coords, np.asarray(cells, dtype=np.int64), name)
 
 

@@ -8,6 +8,8 @@ L, and y = A x with constant per-macro stencils plus an interface step
 """
 from .mesh import (Mesh, F64, F32, F64_IEEE, BC_NONE, BC_DIRICHLET, SOLVE_F64, SOLVE_MIXED, HytegError,
                    version)
+from .server import Server, Result
+from ._capi import REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED
 
 __all__ = ["Mesh", "F64", "F32", "F64_IEEE", "BC_NONE", "BC_DIRICHLET", "SOLVE_F64", "SOLVE_MIXED", "HytegError",
-           "version"]
+           "version", "Server", "Result", "REQ_QUEUED", "REQ_RUNNING", "REQ_DONE", "REQ_FAILED"]

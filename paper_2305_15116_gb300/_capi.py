@@ -62,13 +62,57 @@ lib.hyteg_solve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.
                             ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_double)]
 lib.hyteg_solve.restype = ctypes.c_int
+lib.hyteg_poisson_rhs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p,
+                                  ctypes.c_void_p]
+lib.hyteg_poisson_rhs.restype = ctypes.c_int
+lib.hyteg_to_global.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+lib.hyteg_to_global.restype = ctypes.c_int
+
+
+class Request(ctypes.Structure):
+    """struct hyteg_request"""
+    _fields_ = [("dim", ctypes.c_int), ("n_verts", ctypes.c_int64), ("coords", c_dblp), ("n_cells", ctypes.c_int64),
+                ("cells", c_i64p), ("level", ctypes.c_int), ("mode", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("seed", ctypes.c_uint64), ("noise", ctypes.c_double),
+                ("u_out", c_dblp), ("b_out", c_dblp)]
+
+
+class Result(ctypes.Structure):
+    """struct hyteg_result"""
+    _fields_ = [("status", ctypes.c_int), ("error", ctypes.c_int), ("iters", ctypes.c_int),
+                ("cache_hit", ctypes.c_int), ("relres", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("run_s", ctypes.c_double), ("n_global", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    """struct hyteg_server_stats"""
+    _fields_ = [("submitted", ctypes.c_int64), ("done", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("cached_meshes", ctypes.c_int64), ("cache_hits", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("reserved_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t)]
+
+
+lib.hyteg_server_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+lib.hyteg_server_create.restype = ctypes.c_int
+lib.hyteg_server_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+lib.hyteg_server_submit.restype = ctypes.c_int
+lib.hyteg_server_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]
+lib.hyteg_server_poll.restype = ctypes.c_int
+lib.hyteg_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result)]
+lib.hyteg_server_wait.restype = ctypes.c_int
+lib.hyteg_server_release.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+lib.hyteg_server_release.restype = ctypes.c_int
+lib.hyteg_server_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerStats)]
+lib.hyteg_server_stats_get.restype = ctypes.c_int
+lib.hyteg_server_destroy.argtypes = [ctypes.c_void_p]
+lib.hyteg_server_destroy.restype = None
 lib.hyteg_last_error.argtypes = []
 lib.hyteg_last_error.restype = ctypes.c_char_p
 lib.hyteg_version.argtypes = []
 lib.hyteg_version.restype = ctypes.c_char_p
 
 # status codes, dtypes, boundary modes (values of include/hyteg.h)
-OK, EINVAL, ENOMEM, ECUDA, EMESH, ESTATE = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, EMESH, ESTATE, EAGAIN, ETIMEDOUT = 0, -1, -2, -3, -4, -5, -6, -7
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 F64, F32, F64_IEEE = 1, 2, 3
 BC_NONE, BC_DIRICHLET = 0, 1
 SOLVE_F64, SOLVE_MIXED = 1, 2

@@ -1,5 +1,6 @@
 // The C ABI of libhyteg.so (declared in include/hyteg.h): argument checks,
 // error codes and the launch sequence of one operator apply.
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -87,26 +88,28 @@ int hyteg_mesh_refine(hyteg_mesh* mesh, int max_level) {
   if (m.device >= 0 && m.device != dev) return fail(HYTEG_ESTATE, "refine called on a different device");
   try {
     if (!m.d_prims) {
-      e = cudaMalloc((void**)&m.d_prims, m.prims.size() * sizeof(hyteg::Prim));
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-      e = cudaMemcpy(m.d_prims, m.prims.data(), m.prims.size() * sizeof(hyteg::Prim), cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
-      e = cudaMalloc((void**)&m.d_incs, m.incs.size() * sizeof(hyteg::Inc));
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-      e = cudaMemcpy(m.d_incs, m.incs.data(), m.incs.size() * sizeof(hyteg::Inc), cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
-      m.device = dev;
+      m.device = dev;  // from here on destroy releases what was allocated
+      e = hyteg::dev_alloc(m, (void**)&m.d_prims, m.prims.size() * sizeof(hyteg::Prim));
+      if (e != cudaSuccess) return fail(HYTEG_ENOMEM, "device allocation failed");
+      e = hyteg::dev_upload(m, m.d_prims, m.prims.data(), m.prims.size() * sizeof(hyteg::Prim));
+      if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+      e = hyteg::dev_alloc(m, (void**)&m.d_incs, m.incs.size() * sizeof(hyteg::Inc));
+      if (e != cudaSuccess) return fail(HYTEG_ENOMEM, "device allocation failed");
+      e = hyteg::dev_upload(m, m.d_incs, m.incs.data(), m.incs.size() * sizeof(hyteg::Inc));
+      if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     }
     for (int l = m.max_level + 1; l <= max_level; ++l) {
       hyteg::LevelDev L;
       const std::string err = hyteg::build_level(m, l, L);
       if (!err.empty()) {
-        hyteg::free_level(L);
-        return fail(HYTEG_ECUDA, err);
+        hyteg::free_level(m, L);
+        return fail(err.rfind("device allocation", 0) == 0 ? HYTEG_ENOMEM : HYTEG_ECUDA, err);
       }
       m.levels.push_back(L);
       m.max_level = l;
     }
+    e = hyteg::dev_sync(m);
+    if (e != cudaSuccess) return cuda_fail(e, "refine");
   } catch (const std::bad_alloc&) {
     return fail(HYTEG_ENOMEM, "host allocation failed");
   }
@@ -120,13 +123,14 @@ void hyteg_mesh_destroy(hyteg_mesh* mesh) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(m.device);
-    cudaDeviceSynchronize();
-    for (auto& L : m.levels) hyteg::free_level(L);
-    cudaFree(m.d_prims);
-    cudaFree(m.d_incs);
+    if (!m.mem.arena) cudaDeviceSynchronize();
+    for (auto& L : m.levels) hyteg::free_level(m, L);
+    hyteg::dev_free(m, m.d_prims);
+    hyteg::dev_free(m, m.d_incs);
     cudaFree(m.stage_x);
     cudaFree(m.stage_y);
     hyteg::solver_free(m);
+    hyteg::problem_free(m);
     cudaSetDevice(cur);
   }
   delete mesh;
@@ -242,7 +246,10 @@ int hyteg_solver_setup(hyteg_mesh* mesh, int max_level, int nu1, int nu2, double
     const std::string err = hyteg::solver_setup(mesh->m, max_level, nu1, nu2, omega);
     if (!err.empty()) {
       hyteg::solver_free(mesh->m);
-      return fail(err.rfind("cuda", 0) == 0 ? HYTEG_ECUDA : HYTEG_EINVAL, err);
+      const int code = err.find("device allocation") != std::string::npos ? HYTEG_ENOMEM
+                       : err.rfind("cuda", 0) == 0                         ? HYTEG_ECUDA
+                                                                           : HYTEG_EINVAL;
+      return fail(code, err);
     }
   } catch (const std::bad_alloc&) {
     hyteg::solver_free(mesh->m);
@@ -298,6 +305,29 @@ int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* 
   const cudaError_t e = hyteg::mg_solve(mesh->m, level, mode, b, u, rtol, max_iter,
                                         static_cast<cudaStream_t>(stream), iters, relres);
   return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "solve");
+}
+
+int hyteg_poisson_rhs(hyteg_mesh* mesh, int level, uint64_t seed, double noise, double* b, void* stream) {
+  if (int r = check_solver(mesh, level, 0)) return r;
+  if (!b) return fail(HYTEG_EINVAL, "b is NULL");
+  if (!(noise >= 0.0) || !std::isfinite(noise)) return fail(HYTEG_EINVAL, "noise must be finite and >= 0");
+  hyteg::Mesh& m = mesh->m;
+  if (!m.problem.ready) {
+    const std::string err = hyteg::problem_setup(m);
+    if (!err.empty()) {
+      hyteg::problem_free(m);
+      return fail(err.find("allocation") != std::string::npos ? HYTEG_ENOMEM : HYTEG_ECUDA, err);
+    }
+  }
+  const cudaError_t e = hyteg::poisson_rhs(m, level, seed, noise, b, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "right-hand side");
+}
+
+int hyteg_to_global(const hyteg_mesh* mesh, int level, const double* v, double* v_global, void* stream) {
+  if (int r = check_solver(mesh, level, 0)) return r;
+  if (!v || !v_global) return fail(HYTEG_EINVAL, "NULL vector");
+  const cudaError_t e = hyteg::to_global(mesh->m, level, v, v_global, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "global gather");
 }
 
 const char* hyteg_last_error(void) { return g_last_error.c_str(); }

@@ -91,6 +91,24 @@ struct Solver {
   double* red = nullptr;         // reduction scratch: [RED_BLOCKS partials][2 results]
 };
 
+// Device memory source of a mesh (see devmem.cpp): cudaMalloc when `arena`
+// is null, else blocks of the arena; uploads and clears go to `stream`.
+struct Arena;
+struct DevMem {
+  Arena* arena = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
+// Level-independent tables of the Poisson model problem (problem.cu): cell
+// and primitive geometry for right-hand sides and global-order gathers.
+struct ProblemDev {
+  bool ready = false;
+  double* cell_x = nullptr;     // [n_cells][4][3] vertex coordinates
+  double* cell_vol = nullptr;   // [n_cells] |cell|
+  double* prim_x = nullptr;     // [n_prims][3][3] coordinates of the canonical vertices
+  double* prim_mass = nullptr;  // [n_prims] sum over incident cells of elements-at-point * |cell|
+};
+
 struct Mesh {
   int dim = 0;
   int bc = 0;
@@ -116,6 +134,8 @@ struct Mesh {
   size_t stage_bytes = 0;
 
   Solver* solver = nullptr;
+  ProblemDev problem;
+  DevMem mem;
 };
 
 // Records the message returned by hyteg_last_error() on this thread.
@@ -125,7 +145,29 @@ void set_last_error(const std::string& msg);
 // Returns an error message, empty on success.
 std::string build_topology(Mesh& m);
 std::string build_level(Mesh& m, int level, LevelDev& out);
-void free_level(LevelDev& L);
+void free_level(const Mesh& m, LevelDev& L);
+
+// ---- device memory (devmem.cpp) ---------------------------------------------
+Arena* arena_create(size_t bytes, std::string& err);
+void arena_destroy(Arena* a);
+void* arena_alloc(Arena* a, size_t bytes);
+void arena_free(Arena* a, void* p);
+size_t arena_used(Arena* a);
+size_t arena_largest_free(Arena* a);
+cudaError_t dev_alloc(const Mesh& m, void** p, size_t bytes);
+void dev_free(const Mesh& m, void* p);
+cudaError_t dev_upload(const Mesh& m, void* dst, const void* src, size_t bytes);
+cudaError_t dev_zero(const Mesh& m, void* p, size_t bytes);
+cudaError_t dev_sync(const Mesh& m);
+
+// ---- Poisson model problem (problem.cu) -------------------------------------
+std::string problem_setup(Mesh& m);
+void problem_free(Mesh& m);
+cudaError_t poisson_rhs(const Mesh& m, int level, uint64_t seed, double noise, double* b, cudaStream_t s);
+cudaError_t to_global(const Mesh& m, int level, const double* v, double* out, cudaStream_t s);
+// elements of one macro that contain a point of boundary class `cls`
+int elements_at_class(int dim, int cls);
+double cell_measure(const Mesh& m, int64_t c);
 void compute_dof_map(const Mesh& m, int level, int64_t* gid);
 int64_t n_global_dofs(const Mesh& m, int level);
 int64_t slots_per_macro(int dim, int level);
@@ -136,6 +178,8 @@ void compute_lumped_mass(const Mesh& m, int level, double* mass);
 void compute_dirichlet_mask(const Mesh& m, int level, unsigned char* mask);
 std::string solver_setup(Mesh& m, int max_level, int nu1, int nu2, double omega);
 void solver_free(Mesh& m);
+// inverse diagonals (fp64, fp32) and owner flags of one level, on the device
+cudaError_t mg_diag_setup(const Mesh& m, int level, MgLevel& g, cudaStream_t s);
 cudaError_t mg_restrict(const Mesh& m, int fine_level, int dtype, const void* rf, void* bc, cudaStream_t s);
 cudaError_t mg_prolong_add(const Mesh& m, int fine_level, int dtype, const void* ec, void* uf, cudaStream_t s);
 cudaError_t mg_vcycle(Mesh& m, int level, int dtype, const void* b, void* u, cudaStream_t s);

@@ -132,15 +132,18 @@ bool inside3(int cls, int dx, int dy, int dz) {
 }
 
 template <class T>
-std::string upload(T** dptr, const std::vector<T>& h) {
+std::string upload(const Mesh& m, T** dptr, const std::vector<T>& h) {
   if (h.empty()) {
     *dptr = nullptr;
     return "";
   }
-  cudaError_t e = cudaMalloc((void**)dptr, h.size() * sizeof(T));
-  if (e != cudaSuccess) return std::string("cudaMalloc: ") + cudaGetErrorString(e);
-  e = cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return std::string("cudaMemcpy: ") + cudaGetErrorString(e);
+  cudaError_t e = dev_alloc(m, (void**)dptr, h.size() * sizeof(T));
+  if (e != cudaSuccess) {
+    *dptr = nullptr;
+    return std::string("device allocation: ") + cudaGetErrorString(e);
+  }
+  e = dev_upload(m, *dptr, h.data(), h.size() * sizeof(T));
+  if (e != cudaSuccess) return std::string("host-to-device copy: ") + cudaGetErrorString(e);
   return "";
 }
 
@@ -287,14 +290,14 @@ std::string build_topology(Mesh& m) {
   return "";
 }
 
-void free_level(LevelDev& L) {
-  cudaFree(L.st64);
-  cudaFree(L.st32);
-  cudaFree(L.st_hi);
-  cudaFree(L.st_lo);
-  cudaFree(L.tiles);
-  cudaFree(L.items);
-  cudaFree(L.slabs);
+void free_level(const Mesh& m, LevelDev& L) {
+  dev_free(m, L.st64);
+  dev_free(m, L.st32);
+  dev_free(m, L.st_hi);
+  dev_free(m, L.st_lo);
+  dev_free(m, L.tiles);
+  dev_free(m, L.items);
+  dev_free(m, L.slabs);
   L = LevelDev{};
 }
 
@@ -453,13 +456,13 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   L.n_slabs = int(slabs.size());
 
   std::string err;
-  if (!(err = upload(&L.st64, st)).empty()) return err;
-  if (!(err = upload(&L.st32, st32)).empty()) return err;
-  if (!(err = upload(&L.st_hi, sth)).empty()) return err;
-  if (!(err = upload(&L.st_lo, stl)).empty()) return err;
-  if (!(err = upload(&L.tiles, tiles)).empty()) return err;
-  if (!(err = upload(&L.items, items)).empty()) return err;
-  if (!(err = upload(&L.slabs, slabs)).empty()) return err;
+  if (!(err = upload(m, &L.st64, st)).empty()) return err;
+  if (!(err = upload(m, &L.st32, st32)).empty()) return err;
+  if (!(err = upload(m, &L.st_hi, sth)).empty()) return err;
+  if (!(err = upload(m, &L.st_lo, stl)).empty()) return err;
+  if (!(err = upload(m, &L.tiles, tiles)).empty()) return err;
+  if (!(err = upload(m, &L.items, items)).empty()) return err;
+  if (!(err = upload(m, &L.slabs, slabs)).empty()) return err;
   return "";
 }
 

@@ -90,6 +90,32 @@ void for_each_interface_point(const Mesh& m, int n, F f) {
   }
 }
 
+template <class T>
+std::string upload_vec(const Mesh& m, T** dptr, const std::vector<T>& h) {
+  cudaError_t e = dev_alloc(m, (void**)dptr, std::max<size_t>(h.size(), 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    *dptr = nullptr;
+    return std::string("cuda: device allocation: ") + cudaGetErrorString(e);
+  }
+  e = dev_upload(m, *dptr, h.data(), h.size() * sizeof(T));
+  if (e != cudaSuccess) return std::string("cuda: host-to-device copy: ") + cudaGetErrorString(e);
+  return "";
+}
+
+template <class T>
+std::string alloc_vec(const Mesh& m, T** dptr, size_t count) {
+  cudaError_t e = dev_alloc(m, (void**)dptr, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    *dptr = nullptr;
+    return std::string("cuda: device allocation: ") + cudaGetErrorString(e);
+  }
+  e = dev_zero(m, *dptr, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return std::string("cuda: clear: ") + cudaGetErrorString(e);
+  return "";
+}
+
+}  // namespace
+
 double cell_measure(const Mesh& m, int64_t c) {
   const int d = m.dim;
   const int64_t* cv = &m.cells[c * (d + 1)];
@@ -151,27 +177,6 @@ int elements_at_class(int dim, int cls) {
   return count;
 }
 
-template <class T>
-std::string upload_vec(T** dptr, const std::vector<T>& h) {
-  cudaError_t e = cudaMalloc((void**)dptr, std::max<size_t>(h.size(), 1) * sizeof(T));
-  if (e != cudaSuccess) return std::string("cudaMalloc: ") + cudaGetErrorString(e);
-  if (!h.empty()) {
-    e = cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return std::string("cudaMemcpy: ") + cudaGetErrorString(e);
-  }
-  return "";
-}
-
-template <class T>
-std::string alloc_vec(T** dptr, size_t count) {
-  cudaError_t e = cudaMalloc((void**)dptr, std::max<size_t>(count, 1) * sizeof(T));
-  if (e != cudaSuccess) return std::string("cudaMalloc: ") + cudaGetErrorString(e);
-  e = cudaMemset(*dptr, 0, std::max<size_t>(count, 1) * sizeof(T));
-  if (e != cudaSuccess) return std::string("cudaMemset: ") + cudaGetErrorString(e);
-  return "";
-}
-
-}  // namespace
 
 void compute_slot_coords(const Mesh& m, int level, double* xyz) {
   // Every copy of an interface point gets the coordinates of the primitive's
@@ -281,26 +286,26 @@ void solver_free(Mesh& m) {
   if (!m.solver) return;
   Solver& sv = *m.solver;
   for (auto& L : sv.lv) {
-    cudaFree(L.dinv64);
-    cudaFree(L.dinv32);
-    cudaFree(L.owner);
-    cudaFree(L.lpts);
-    cudaFree(L.multinv64);
-    cudaFree(L.multinv32);
-    cudaFree(L.u64);
-    cudaFree(L.b64);
-    cudaFree(L.y64);
-    cudaFree(L.r64);
-    cudaFree(L.u32);
-    cudaFree(L.b32);
-    cudaFree(L.y32);
-    cudaFree(L.r32);
+    dev_free(m, L.dinv64);
+    dev_free(m, L.dinv32);
+    dev_free(m, L.owner);
+    dev_free(m, L.lpts);
+    dev_free(m, L.multinv64);
+    dev_free(m, L.multinv32);
+    dev_free(m, L.u64);
+    dev_free(m, L.b64);
+    dev_free(m, L.y64);
+    dev_free(m, L.r64);
+    dev_free(m, L.u32);
+    dev_free(m, L.b32);
+    dev_free(m, L.y32);
+    dev_free(m, L.r32);
   }
-  cudaFree(sv.a0inv64);
-  cudaFree(sv.a0inv32);
-  cudaFree(sv.v_of_slot0);
-  cudaFree(sv.slot_of_v0);
-  cudaFree(sv.red);
+  dev_free(m, sv.a0inv64);
+  dev_free(m, sv.a0inv32);
+  dev_free(m, sv.v_of_slot0);
+  dev_free(m, sv.slot_of_v0);
+  dev_free(m, sv.red);
   delete m.solver;
   m.solver = nullptr;
 }
@@ -362,46 +367,28 @@ std::string solver_setup(Mesh& m, int max_level, int nu1, int nu2, double omega)
     const int n = 1 << l;
     const int64_t S = L.slots_per_macro;
     const int64_t ns = S * m.n_cells;
-    MgLevel g;
+    sv.lv.push_back(MgLevel{});
+    MgLevel& g = sv.lv.back();
     g.level = l;
     const auto pts = local_points(d, n);
-    // partial diagonals -> interface sums -> Dirichlet rows -> inverse
-    std::vector<double> diag(ns);
-    std::vector<unsigned char> owner(ns, 1);
-    for (int64_t c = 0; c < m.n_cells; ++c)
-      for (int64_t s = 0; s < S; ++s) {
-        const int q[3] = {pts[s][0], pts[s][1], pts[s][2]};
-        diag[c * S + s] = L.st_host[(size_t(c) * ncls + point_class(d, n, q)) * nw + center];
-      }
-    for_each_interface_point(m, n, [&](const Prim& pr, const std::vector<PointRef>& refs) {
-      double sum = 0.0;
-      for (const auto& r : refs) sum += diag[r.cell * S + slot_of(d, n, r.q)];
-      bool first = true;
-      for (const auto& r : refs) {
-        const int64_t sl = r.cell * S + slot_of(d, n, r.q);
-        diag[sl] = pr.boundary ? 1.0 : sum;
-        owner[sl] = (first && !pr.boundary) ? 1 : 0;
-        first = false;
-      }
-    });
-    std::vector<double> dinv(ns);
-    for (int64_t i = 0; i < ns; ++i) dinv[i] = 1.0 / diag[i];
-    std::vector<float> dinv32(dinv.begin(), dinv.end());
     std::vector<unsigned> lp(S);
     for (int64_t s = 0; s < S; ++s)
       lp[s] = d == 2 ? unsigned(pts[s][0]) | (unsigned(pts[s][1]) << 16)
                      : unsigned(pts[s][0]) | (unsigned(pts[s][1]) << 11) | (unsigned(pts[s][2]) << 22);
-    if (!(err = upload_vec(&g.dinv64, dinv)).empty()) return err;
-    if (!(err = upload_vec(&g.dinv32, dinv32)).empty()) return err;
-    if (!(err = upload_vec(&g.owner, owner)).empty()) return err;
-    if (!(err = upload_vec(&g.lpts, lp)).empty()) return err;
-    if (!(err = upload_vec(&g.multinv64, multinv)).empty()) return err;
-    if (!(err = upload_vec(&g.multinv32, multinv32)).empty()) return err;
+    if (!(err = upload_vec(m, &g.lpts, lp)).empty()) return err;
+    if (!(err = upload_vec(m, &g.multinv64, multinv)).empty()) return err;
+    if (!(err = upload_vec(m, &g.multinv32, multinv32)).empty()) return err;
+    if (!(err = alloc_vec(m, &g.dinv64, ns)).empty()) return err;
+    if (!(err = alloc_vec(m, &g.dinv32, ns)).empty()) return err;
+    if (!(err = alloc_vec(m, &g.owner, ns)).empty()) return err;
     for (double** v : {&g.u64, &g.b64, &g.y64, &g.r64})
-      if (!(err = alloc_vec(v, ns)).empty()) return err;
+      if (!(err = alloc_vec(m, v, ns)).empty()) return err;
     for (float** v : {&g.u32, &g.b32, &g.y32, &g.r32})
-      if (!(err = alloc_vec(v, ns)).empty()) return err;
-    sv.lv.push_back(g);
+      if (!(err = alloc_vec(m, v, ns)).empty()) return err;
+    // inverse diagonals and owner flags on the device: partial diagonals ->
+    // interface sums in ascending macro order -> Dirichlet rows -> inverse
+    const cudaError_t e = mg_diag_setup(m, l, g, m.mem.stream);
+    if (e != cudaSuccess) return std::string("cuda: diagonal set-up: ") + cudaGetErrorString(e);
   }
 
   // level 0: the coarse operator on the coarse vertices, dense inverse
@@ -477,11 +464,13 @@ std::string solver_setup(Mesh& m, int max_level, int nu1, int nu2, double omega)
       }
   }
   std::vector<float> inv32(inv.begin(), inv.end());
-  if (!(err = upload_vec(&sv.a0inv64, inv)).empty()) return err;
-  if (!(err = upload_vec(&sv.a0inv32, inv32)).empty()) return err;
-  if (!(err = upload_vec(&sv.v_of_slot0, v_of_slot)).empty()) return err;
-  if (!(err = upload_vec(&sv.slot_of_v0, slot_of_v)).empty()) return err;
-  if (!(err = alloc_vec(&sv.red, size_t(1024 + 8))).empty()) return err;
+  if (!(err = upload_vec(m, &sv.a0inv64, inv)).empty()) return err;
+  if (!(err = upload_vec(m, &sv.a0inv32, inv32)).empty()) return err;
+  if (!(err = upload_vec(m, &sv.v_of_slot0, v_of_slot)).empty()) return err;
+  if (!(err = upload_vec(m, &sv.slot_of_v0, slot_of_v)).empty()) return err;
+  if (!(err = alloc_vec(m, &sv.red, size_t(1024 + 8))).empty()) return err;
+  const cudaError_t e = dev_sync(m);
+  if (e != cudaSuccess) return std::string("cuda: set-up: ") + cudaGetErrorString(e);
   return "";
 }
 

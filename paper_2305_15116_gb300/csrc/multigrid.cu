@@ -219,6 +219,73 @@ __global__ void __launch_bounds__(128) k_iface_sum_zero(T* __restrict__ v, const
   for (int i = 0; i < p.inc_count; ++i) v[slot_of(i)] = acc;
 }
 
+// ---- set-up: inverse diagonals and owner flags ----------------------------------
+// Every slot first takes the centre weight of its macro's class stencil (the
+// macro's part of the diagonal) and owner flag 1; then every interface point
+// sums the parts of its copies in ascending macro order (Dirichlet rows: 1),
+// writes the sum to every copy and keeps the owner flag on the first copy
+// only (none on Dirichlet points); finally the diagonal is inverted.
+template <int DIM>
+__global__ void k_diag_part(double* __restrict__ diag, unsigned char* __restrict__ owner,
+                            const unsigned* __restrict__ lpts, const double* __restrict__ st, int n, int64_t S,
+                            int64_t total) {
+  constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
+  constexpr int NW = DIM == 2 ? NW2 : NW3;
+  constexpr int CEN = DIM == 2 ? C2 : C3;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = i / S;
+    int q[3];
+    unpack<DIM>(lpts[i - cell * S], q);
+    diag[i] = st[(cell * NCLS + pclass<DIM>(n, q)) * NW + CEN];
+    owner[i] = 1;
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_diag_iface(double* __restrict__ diag, unsigned char* __restrict__ owner,
+                                                    const int4* __restrict__ items, const Prim* __restrict__ prims,
+                                                    const Inc* __restrict__ incs, int n, int64_t S) {
+  const int4 it = items[blockIdx.x];
+  const int a = it.z + threadIdx.x;
+  if (a >= it.w) return;
+  const Prim p = prims[it.x];
+  const int b = it.y;
+  int wv[3] = {0, 0, 0};
+  if (p.type == 0) {
+    wv[0] = n;
+  } else if (p.type == 1) {
+    wv[0] = n - a;
+    wv[1] = a;
+  } else {
+    wv[0] = n - a - b;
+    wv[1] = a;
+    wv[2] = b;
+  }
+  auto slot_of = [&](int i) -> int64_t {
+    const Inc inc = incs[p.inc_begin + i];
+    int q[3] = {0, 0, 0};
+    for (int j = 0; j <= p.type; ++j)
+      if (inc.corner[j] >= 1) q[inc.corner[j] - 1] += wv[j];
+    return (int64_t)inc.cell * S + slotq<DIM>(n, q);
+  };
+  double sum = 0.0;
+  for (int i = 0; i < p.inc_count; ++i) sum += diag[slot_of(i)];
+  if (p.boundary) sum = 1.0;
+  for (int i = 0; i < p.inc_count; ++i) {
+    const int64_t sl = slot_of(i);
+    diag[sl] = sum;
+    owner[sl] = (i == 0 && !p.boundary) ? 1 : 0;
+  }
+}
+
+__global__ void k_diag_invert(double* __restrict__ d64, float* __restrict__ d32, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = 1.0 / d64[i];
+    d64[i] = v;
+    d32[i] = __double2float_rn(v);
+  }
+}
+
 // u_f += P e_c at every fine slot: coincident points copy, micro-edge
 // midpoints take the mean of the two coarse end points.
 template <class T, int DIM>
@@ -500,6 +567,26 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
   *iters = it;
   *relres = rel;
   return cudaSuccess;
+}
+
+cudaError_t mg_diag_setup(const Mesh& m, int l, MgLevel& g, cudaStream_t s) {
+  const LevelDev& L = m.levels[l];
+  const int64_t S = L.slots_per_macro;
+  const int64_t total = S * m.n_cells;
+  if (m.dim == 2)
+    k_diag_part<2><<<grid_for(total), THREADS, 0, s>>>(g.dinv64, g.owner, g.lpts, L.st64, L.n, S, total);
+  else
+    k_diag_part<3><<<grid_for(total), THREADS, 0, s>>>(g.dinv64, g.owner, g.lpts, L.st64, L.n, S, total);
+  HY_TRY(cudaGetLastError());
+  if (L.n_items > 0) {
+    if (m.dim == 2)
+      k_diag_iface<2><<<L.n_items, 128, 0, s>>>(g.dinv64, g.owner, L.items, m.d_prims, m.d_incs, L.n, S);
+    else
+      k_diag_iface<3><<<L.n_items, 128, 0, s>>>(g.dinv64, g.owner, L.items, m.d_prims, m.d_incs, L.n, S);
+    HY_TRY(cudaGetLastError());
+  }
+  k_diag_invert<<<grid_for(total), THREADS, 0, s>>>(g.dinv64, g.dinv32, total);
+  return cudaGetLastError();
 }
 
 }  // namespace hyteg

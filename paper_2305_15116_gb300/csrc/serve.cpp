@@ -1,0 +1,474 @@
+// Solve server: many independent Poisson solve requests on one GPU.
+//
+// Worker threads with one CUDA stream each take requests in arrival order as
+// soon as they are free, so a new request starts while others are mid-solve
+// (continuous batching; their kernels share the GPU).  All device memory of
+// the requests and of the mesh cache comes from one arena reserved at
+// creation (devmem.cpp): admission keeps the estimated bytes of the requests
+// in flight within the cap, refined meshes stay cached for later requests on
+// the same coarse mesh and level, and idle cached meshes are dropped least
+// recently used first when a new build needs the room.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hyteg.h"
+#include "hyteg_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double seconds_since(Clock::time_point t0, Clock::time_point t1) {
+  return std::chrono::duration<double>(t1 - t0).count();
+}
+
+// A refined mesh with its solver workspace and the vectors of one request.
+struct Entry {
+  std::string key;
+  hyteg_mesh* mesh = nullptr;
+  double* b = nullptr;
+  double* u = nullptr;
+  double* glob = nullptr;
+  int64_t n_global = 0;
+  bool busy = false;
+};
+
+struct Req {
+  uint64_t ticket = 0;
+  int dim = 0, level = 0, mode = 0, max_iter = 0;
+  double rtol = 0, noise = 0;
+  uint64_t seed = 0;
+  std::vector<double> coords;
+  std::vector<int64_t> cells;
+  double* u_out = nullptr;
+  double* b_out = nullptr;
+  std::string key;
+  size_t est = 0;
+  hyteg_result res{};
+  std::string msg;
+  Clock::time_point t_submit, t_start;
+};
+
+int64_t slots_of(int dim, int level, int64_t n_cells) { return hyteg::slots_per_macro(dim, level) * n_cells; }
+
+// Device bytes of a request: per level the solver workspace (2 inverse
+// diagonals, owner flags, 4 float64 and 4 fp32 vectors: 61 B per slot) and
+// its tables, plus b, u (slot layout) and the global-order buffer on the
+// finest level, with a margin for tables and allocation rounding.
+size_t estimate_bytes(int dim, int level, int64_t n_cells, int64_t n_verts) {
+  size_t b = 0;
+  for (int l = 0; l <= level; ++l) {
+    const int64_t S = hyteg::slots_per_macro(dim, l);
+    b += size_t(61) * size_t(S * n_cells) + size_t(4) * size_t(S) + (size_t(64) << 10);
+  }
+  const int64_t ns = slots_of(dim, level, n_cells);
+  b += size_t(24) * size_t(ns);
+  b += size_t(8) * size_t(n_verts) * size_t(n_verts) * 2;  // dense level-0 inverse (fp64 + fp32 copy)
+  b += size_t(1) << 20;
+  return b;
+}
+
+std::string make_key(const Req& r) {
+  std::string k;
+  k.reserve(16 + r.coords.size() * 8 + r.cells.size() * 8);
+  const int head[2] = {r.dim, r.level};
+  k.append(reinterpret_cast<const char*>(head), sizeof(head));
+  k.append(reinterpret_cast<const char*>(r.coords.data()), r.coords.size() * sizeof(double));
+  k.append(reinterpret_cast<const char*>(r.cells.data()), r.cells.size() * sizeof(int64_t));
+  return k;
+}
+
+}  // namespace
+
+struct hyteg_server {
+  int device = 0;
+  size_t cap = 0;
+  hyteg::Arena* arena = nullptr;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;
+
+  std::mutex mu;
+  std::condition_variable cv_work;  // queue not empty or stopping
+  std::condition_variable cv_done;  // a request finished or an entry became idle
+  std::deque<Req*> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
+  uint64_t next_ticket = 1;
+  size_t reserved = 0;
+  bool stopping = false;
+
+  std::list<Entry*> idle;  // idle cached entries, most recently used first
+  std::vector<std::unique_ptr<Entry>> entries;
+  int64_t submitted = 0, done = 0, failed = 0, hits = 0, evictions = 0;
+
+  void worker(int w);
+  int run(Req& r, cudaStream_t s, bool* hit);
+  Entry* acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::string* msg);
+  void release(Entry* e);
+  bool evict_one();  // caller holds mu
+  void destroy_entry(Entry* e);
+};
+
+void hyteg_server::destroy_entry(Entry* e) {
+  if (e->mesh) {
+    hyteg::arena_free(arena, e->b);
+    hyteg::arena_free(arena, e->u);
+    hyteg::arena_free(arena, e->glob);
+    hyteg_mesh_destroy(e->mesh);
+  }
+  e->mesh = nullptr;
+}
+
+bool hyteg_server::evict_one() {
+  if (idle.empty()) return false;
+  Entry* e = idle.back();
+  idle.pop_back();
+  destroy_entry(e);
+  for (auto it = entries.begin(); it != entries.end(); ++it)
+    if (it->get() == e) {
+      entries.erase(it);
+      break;
+    }
+  ++evictions;
+  return true;
+}
+
+Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::string* msg) {
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto it = idle.begin(); it != idle.end(); ++it)
+      if ((*it)->key == r.key) {
+        Entry* e = *it;
+        idle.erase(it);
+        e->busy = true;
+        *hit = true;
+        return e;
+      }
+  }
+  *hit = false;
+  // build a new entry; on a full arena drop idle entries, then wait (bounded)
+  // for requests in flight to hand theirs back
+  const auto deadline = Clock::now() + std::chrono::seconds(120);
+  for (;;) {
+    auto e = std::make_unique<Entry>();
+    e->key = r.key;
+    e->busy = true;
+    int rc = hyteg_mesh_create(r.dim, int64_t(r.coords.size() / r.dim), r.coords.data(),
+                               int64_t(r.cells.size() / (r.dim + 1)), r.cells.data(), HYTEG_BC_DIRICHLET, &e->mesh);
+    if (rc != HYTEG_OK) {
+      *err = rc;
+      *msg = hyteg_last_error();
+      return nullptr;
+    }
+    hyteg::Mesh& m = e->mesh->m;
+    m.mem.arena = arena;
+    m.mem.stream = s;
+    rc = hyteg_mesh_refine(e->mesh, r.level);
+    if (rc == HYTEG_OK) rc = hyteg_solver_setup(e->mesh, r.level, 3, 3, 2.0 / 3.0);
+    std::string perr;
+    if (rc == HYTEG_OK) {
+      perr = hyteg::problem_setup(m);
+      if (!perr.empty()) rc = perr.find("allocation") != std::string::npos ? HYTEG_ENOMEM : HYTEG_ECUDA;
+    }
+    if (rc == HYTEG_OK) {
+      const int64_t ns = slots_of(r.dim, r.level, m.n_cells);
+      e->n_global = hyteg::n_global_dofs(m, r.level);
+      e->b = static_cast<double*>(hyteg::arena_alloc(arena, size_t(ns) * 8));
+      e->u = static_cast<double*>(hyteg::arena_alloc(arena, size_t(ns) * 8));
+      e->glob = static_cast<double*>(hyteg::arena_alloc(arena, size_t(e->n_global) * 8));
+      if (!e->b || !e->u || !e->glob) rc = HYTEG_ENOMEM;
+    }
+    if (rc == HYTEG_OK) {
+      Entry* raw = e.get();
+      std::lock_guard<std::mutex> lk(mu);
+      entries.push_back(std::move(e));
+      return raw;
+    }
+    const std::string why = perr.empty() ? std::string(hyteg_last_error()) : perr;
+    cudaStreamSynchronize(s);
+    destroy_entry(e.get());
+    if (rc != HYTEG_ENOMEM) {
+      *err = rc;
+      *msg = why;
+      return nullptr;
+    }
+    std::unique_lock<std::mutex> lk(mu);
+    if (evict_one()) continue;
+    if (Clock::now() > deadline ||
+        cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+      *err = HYTEG_ENOMEM;
+      *msg = "device arena exhausted: " + why;
+      return nullptr;
+    }
+  }
+}
+
+void hyteg_server::release(Entry* e) {
+  std::lock_guard<std::mutex> lk(mu);
+  e->busy = false;
+  idle.push_front(e);
+  cv_done.notify_all();
+}
+
+int hyteg_server::run(Req& r, cudaStream_t s, bool* hit) {
+  int err = HYTEG_OK;
+  Entry* e = acquire(r, s, hit, &err, &r.msg);
+  if (!e) return err;
+  hyteg::Mesh& m = e->mesh->m;
+  m.mem.stream = s;
+  const int64_t ns = slots_of(r.dim, r.level, m.n_cells);
+  r.res.n_global = e->n_global;
+  int rc = HYTEG_OK;
+  cudaError_t ce = hyteg::poisson_rhs(m, r.level, r.seed, r.noise, e->b, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(e->u, 0, size_t(ns) * 8, s);
+  if (ce != cudaSuccess) {
+    rc = HYTEG_ECUDA;
+    r.msg = std::string("right-hand side: ") + cudaGetErrorString(ce);
+  }
+  if (rc == HYTEG_OK) {
+    rc = hyteg_solve(e->mesh, r.level, r.mode, e->b, e->u, r.rtol, r.max_iter, s, &r.res.iters, &r.res.relres);
+    if (rc != HYTEG_OK) r.msg = hyteg_last_error();
+  }
+  for (int k = 0; k < 2 && rc == HYTEG_OK; ++k) {
+    double* host = k == 0 ? r.u_out : r.b_out;
+    if (!host) continue;
+    ce = hyteg::to_global(m, r.level, k == 0 ? e->u : e->b, e->glob, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(host, e->glob, size_t(e->n_global) * 8, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+      rc = HYTEG_ECUDA;
+      r.msg = std::string("result copy: ") + cudaGetErrorString(ce);
+    }
+  }
+  ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess && rc == HYTEG_OK) {
+    rc = HYTEG_ECUDA;
+    r.msg = cudaGetErrorString(ce);
+  }
+  if (rc == HYTEG_ECUDA) {
+    // leave a mesh whose last use failed out of the cache
+    std::lock_guard<std::mutex> lk(mu);
+    destroy_entry(e);
+    for (auto it = entries.begin(); it != entries.end(); ++it)
+      if (it->get() == e) {
+        entries.erase(it);
+        break;
+      }
+    cv_done.notify_all();
+  } else {
+    release(e);
+  }
+  return rc;
+}
+
+void hyteg_server::worker(int w) {
+  cudaSetDevice(device);
+  cudaStream_t s = streams[w];
+  for (;;) {
+    Req* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
+      if (queue.empty()) return;  // stopping
+      r = queue.front();
+      queue.pop_front();
+      r->res.status = HYTEG_REQ_RUNNING;
+      r->t_start = Clock::now();
+      r->res.queue_s = seconds_since(r->t_submit, r->t_start);
+    }
+    bool hit = false;
+    const int rc = run(*r, s, &hit);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      r->res.run_s = seconds_since(r->t_start, Clock::now());
+      r->res.cache_hit = hit ? 1 : 0;
+      r->res.error = rc;
+      r->res.status = rc == HYTEG_OK ? HYTEG_REQ_DONE : HYTEG_REQ_FAILED;
+      reserved -= r->est;
+      if (rc == HYTEG_OK) {
+        ++done;
+        hits += hit ? 1 : 0;
+      } else {
+        ++failed;
+      }
+      cv_done.notify_all();
+    }
+  }
+}
+
+namespace {
+int sfail(int code, const std::string& msg) {
+  hyteg::set_last_error(msg);
+  return code;
+}
+}  // namespace
+
+extern "C" {
+
+int hyteg_server_create(int device, size_t mem_cap, int n_workers, hyteg_server** out) {
+  if (!out) return sfail(HYTEG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_workers < 1 || n_workers > 64) return sfail(HYTEG_EINVAL, "n_workers must be in 1..64");
+  if (mem_cap < (size_t(1) << 20)) return sfail(HYTEG_EINVAL, "mem_cap below 1 MiB");
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return sfail(HYTEG_EINVAL, "no such device");
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return sfail(HYTEG_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  std::unique_ptr<hyteg_server> sv(new hyteg_server());
+  sv->device = device;
+  sv->cap = mem_cap;
+  std::string err;
+  sv->arena = hyteg::arena_create(mem_cap, err);
+  if (!sv->arena) return sfail(HYTEG_ENOMEM, err);
+  for (int w = 0; w < n_workers; ++w) {
+    cudaStream_t s = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (cudaStream_t t : sv->streams) cudaStreamDestroy(t);
+      hyteg::arena_destroy(sv->arena);
+      return sfail(HYTEG_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    sv->streams.push_back(s);
+  }
+  hyteg_server* raw = sv.release();
+  for (int w = 0; w < n_workers; ++w) raw->workers.emplace_back([raw, w] { raw->worker(w); });
+  *out = raw;
+  return HYTEG_OK;
+}
+
+int hyteg_server_submit(hyteg_server* sv, const hyteg_request* q, uint64_t* ticket) {
+  if (!sv || !q || !ticket) return sfail(HYTEG_EINVAL, "NULL argument");
+  if (q->dim != 2 && q->dim != 3) return sfail(HYTEG_EINVAL, "dim must be 2 or 3");
+  if (q->level < 1 || q->level > (q->dim == 2 ? 12 : 8)) return sfail(HYTEG_EINVAL, "level out of range");
+  if (q->mode != HYTEG_SOLVE_F64 && q->mode != HYTEG_SOLVE_MIXED) return sfail(HYTEG_EINVAL, "unknown mode");
+  if (!(q->rtol > 0.0) || q->max_iter < 0) return sfail(HYTEG_EINVAL, "bad rtol or max_iter");
+  if (!q->coords || !q->cells || q->n_verts < q->dim + 1 || q->n_cells < 1) return sfail(HYTEG_EINVAL, "bad mesh");
+  if (q->n_verts > 4096 || q->n_cells > (int64_t(1) << 20))
+    return sfail(HYTEG_EINVAL, "coarse mesh too large (at most 4096 vertices)");
+  if (!(q->noise >= 0.0) || !std::isfinite(q->noise)) return sfail(HYTEG_EINVAL, "noise must be finite and >= 0");
+  auto r = std::make_unique<Req>();
+  r->dim = q->dim;
+  r->level = q->level;
+  r->mode = q->mode;
+  r->rtol = q->rtol;
+  r->max_iter = q->max_iter;
+  r->seed = q->seed;
+  r->noise = q->noise;
+  r->coords.assign(q->coords, q->coords + q->n_verts * q->dim);
+  r->cells.assign(q->cells, q->cells + q->n_cells * (q->dim + 1));
+  r->u_out = q->u_out;
+  r->b_out = q->b_out;
+  r->key = make_key(*r);
+  r->est = estimate_bytes(q->dim, q->level, q->n_cells, q->n_verts);
+  if (r->est > sv->cap) return sfail(HYTEG_EINVAL, "request can never fit the memory cap");
+  r->res.status = HYTEG_REQ_QUEUED;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->stopping) return sfail(HYTEG_ESTATE, "server is shutting down");
+  if (sv->reserved + r->est > sv->cap) return sfail(HYTEG_EAGAIN, "memory cap reached: retry later");
+  sv->reserved += r->est;
+  r->ticket = sv->next_ticket++;
+  r->t_submit = Clock::now();
+  *ticket = r->ticket;
+  sv->queue.push_back(r.get());
+  sv->reqs[r->ticket] = std::move(r);
+  ++sv->submitted;
+  sv->cv_work.notify_one();
+  return HYTEG_OK;
+}
+
+int hyteg_server_poll(hyteg_server* sv, uint64_t ticket, hyteg_result* out) {
+  if (!sv || !out) return sfail(HYTEG_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return sfail(HYTEG_EINVAL, "unknown ticket");
+  *out = it->second->res;
+  if (out->status == HYTEG_REQ_FAILED) hyteg::set_last_error(it->second->msg);
+  return HYTEG_OK;
+}
+
+int hyteg_server_wait(hyteg_server* sv, uint64_t ticket, double timeout_s, hyteg_result* out) {
+  if (!sv || !out) return sfail(HYTEG_EINVAL, "NULL argument");
+  if (!(timeout_s >= 0.0)) return sfail(HYTEG_EINVAL, "timeout must be >= 0");
+  const auto deadline =
+      Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(std::min(timeout_s, 1e7)));
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return sfail(HYTEG_EINVAL, "unknown ticket");
+  Req* r = it->second.get();
+  auto finished = [&] { return r->res.status == HYTEG_REQ_DONE || r->res.status == HYTEG_REQ_FAILED; };
+  const bool ok = sv->cv_done.wait_until(lk, deadline, finished);
+  *out = r->res;
+  if (!ok) return sfail(HYTEG_ETIMEDOUT, "request not finished within the timeout");
+  if (out->status == HYTEG_REQ_FAILED) hyteg::set_last_error(r->msg);
+  return HYTEG_OK;
+}
+
+int hyteg_server_release(hyteg_server* sv, uint64_t ticket) {
+  if (!sv) return sfail(HYTEG_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return sfail(HYTEG_EINVAL, "unknown ticket");
+  const int st = it->second->res.status;
+  if (st != HYTEG_REQ_DONE && st != HYTEG_REQ_FAILED) return sfail(HYTEG_ESTATE, "request not finished");
+  sv->reqs.erase(it);
+  return HYTEG_OK;
+}
+
+int hyteg_server_stats_get(hyteg_server* sv, hyteg_server_stats* out) {
+  if (!sv || !out) return sfail(HYTEG_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  out->submitted = sv->submitted;
+  out->done = sv->done;
+  out->failed = sv->failed;
+  out->in_flight = sv->submitted - sv->done - sv->failed;
+  out->cached_meshes = int64_t(sv->entries.size());
+  out->cache_hits = sv->hits;
+  out->evictions = sv->evictions;
+  out->reserved_bytes = sv->reserved;
+  out->arena_used = hyteg::arena_used(sv->arena);
+  return HYTEG_OK;
+}
+
+void hyteg_server_destroy(hyteg_server* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stopping = true;
+    for (Req* r : sv->queue) {
+      r->res.status = HYTEG_REQ_FAILED;
+      r->res.error = HYTEG_ESTATE;
+      r->msg = "server shut down before the request started";
+      sv->reserved -= r->est;
+      ++sv->failed;
+    }
+    sv->queue.clear();
+    sv->cv_work.notify_all();
+    sv->cv_done.notify_all();
+  }
+  for (auto& t : sv->workers) t.join();
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(sv->device);
+  for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
+  for (auto& e : sv->entries) sv->destroy_entry(e.get());
+  sv->entries.clear();
+  sv->idle.clear();
+  for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+  hyteg::arena_destroy(sv->arena);
+  cudaSetDevice(cur);
+  delete sv;
+}
+
+}  // extern "C"

@@ -24,6 +24,8 @@
 //   z  : p±1, p+M-y (0,1,0), p+M-y-1 (-1,1,0), p-M+y-1 (0,-1,0), p-M+y (1,-1,0)
 //   z+1: p-y (0,0,1), p-y-1 (-1,0,1), p-M (0,-1,1), p-M+1 (1,-1,1)
 //   z-1: p+y (0,0,-1), p+y+1 (1,0,-1), p+M+1 (0,1,-1), p+M (-1,1,-1)
+#include <mutex>
+
 #include "arith.cuh"
 #include "hyteg_internal.h"
 
@@ -280,8 +282,22 @@ cudaError_t launch_t(const LevelDev& L, const void* x, void* y, cudaStream_t s) 
   const size_t ring_bytes = ((size_t)NRING * (buf + 2 * guard) * sizeof(SV) + 15) / 16 * 16;
   const size_t raw_bytes = Stage<P>::direct ? 0 : (size_t)buf * sizeof(typename P::T);
   const size_t bytes = w_bytes + ring_bytes + raw_bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
+  // The shared-memory limit is a property of the kernel shared by every
+  // thread and stream of the process: raise it once, to what the largest slab
+  // level needs, so that concurrent launches for different levels never see a
+  // limit set for another level.
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    constexpr int nmax = 64;
+    const int bmax = (nmax + 1) * (nmax + 2) / 2;
+    const size_t wb = ((size_t)NCLS3 * NW3 * sizeof(typename P::W) + 15) / 16 * 16;
+    const size_t rb = ((size_t)NRING * (bmax + 2 * (nmax + 3)) * sizeof(SV) + 15) / 16 * 16;
+    const size_t xb = Stage<P>::direct ? 0 : (size_t)bmax * sizeof(typename P::T);
+    attr = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wb + rb + xb));
+  });
+  if (attr != cudaSuccess) return attr;
+  if (n > 64) return cudaErrorInvalidValue;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
   k_slab3d<P><<<L.n_slabs, SLAB_THREADS, bytes, s>>>((const typename P::T*)x, (typename P::T*)y, L.slabs, n,
                                                     L.slots_per_macro, buf, guard, (int)raw_bytes, st);

@@ -186,3 +186,18 @@ class Mesh:
                                   ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(it), ctypes.byref(rel)),
                 "hyteg_solve")
         return it.value, rel.value
+
+    # ---- Poisson model problem -------------------------------------------------
+    def poisson_rhs(self, level: int, seed: int, noise: float, b, stream=None):
+        """b (float64 device tensor, slot layout) = lumped mass * (prod sin(pi p)
+        + noise * Philox normal of the global DoF id), 0 on Dirichlet DoFs."""
+        C.check(C.lib.hyteg_poisson_rhs(self._h, level, seed, noise, ctypes.c_void_p(b.data_ptr()),
+                                        ctypes.c_void_p(_stream_ptr(stream))), "hyteg_poisson_rhs")
+        return b
+
+    def to_global(self, level: int, v, v_global, stream=None):
+        """v_global[gid] = v (float64 device tensors)."""
+        C.check(C.lib.hyteg_to_global(self._h, level, ctypes.c_void_p(v.data_ptr()),
+                                      ctypes.c_void_p(v_global.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+                "hyteg_to_global")
+        return v_global
