@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "f64_ieee"])
     p.add_argument("--level", type=int, default=None,
                    help="override the refinement level (smaller cases for ncu captures; not a bench line)")
+    p.add_argument("--serve-requests", type=int, default=512,
+                   help="requests of the solve-server workload timed after the apply (0: skip)")
+    p.add_argument("--serve-workers", type=int, default=8)
     p.add_argument("--profile", action="store_true",
                    help="only run warm-up + timed applies (for profilers): no e2e, variants or CPU baseline")
     return p.parse_args()
@@ -282,6 +285,110 @@ def solve_workload(device, stream, reps=3, rtol=1e-10):
     return out
 
 
+# ---------------------------------------------------------------- solve server
+def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
+    """The solve server under the synthetic request stream of inputs.serving:
+    Poisson arrivals at 2000/s, half 2D (4..64 macro-triangles, levels 5..10),
+    half 3D (6..384 macro-tets, levels 3..6), each request a lumped-mass
+    right-hand side with its own noise seed, solved to rtol with fp32 V(3,3)
+    cycles in float64 refinement; the solution of every request is copied
+    back to host memory.  Requests refused by the memory cap are retried in
+    order.  Latency runs from a request's arrival to the end of its work."""
+    import collections
+    import paper_2305_15116_gb300 as H
+    from inputs.serving import request_stream, coarse_mesh
+    reqs = request_stream(n_requests)
+    ng_of = {}
+    for q in reqs:  # DoF counts from the library's host-side layout (untimed)
+        key = (q.dim, q.shape, q.level)
+        if key not in ng_of:
+            c = coarse_mesh(q.dim, q.shape)
+            M = H.Mesh(c.coords, c.cells)
+            ng_of[key] = M.num_slots(q.level)[1]
+            M.close()
+    pool = collections.defaultdict(list)
+
+    def buf(n):
+        return pool[n].pop() if pool[n] else np.empty(n)
+
+    sv = H.Server(cap_bytes, workers)
+    # warm-up: one small request per dimension (module load, first launches)
+    for dim, shape, lev in ((2, (2, 1), 5), (3, (1, 1, 1), 3)):
+        c = coarse_mesh(dim, shape)
+        t = sv.submit(c.coords, c.cells, lev, 1, 0.1, rtol=rtol)
+        sv.wait(t, 600)
+        sv.release(t)
+    pending = collections.deque(reqs)
+    retry = collections.deque()
+    outstanding = {}
+    lat, run, queue_s, iters, rels, ngs = [], [], [], [], [], []
+    hits = failed = eagain = 0
+    errors = collections.Counter()
+    t0 = time.perf_counter()
+    t_end = t0
+    while pending or retry or outstanding:
+        now = time.perf_counter() - t0
+        progressed = False
+        while retry or (pending and pending[0].arrival_s <= now):
+            q = retry[0] if retry else pending[0]
+            c = coarse_mesh(q.dim, q.shape)
+            n = ng_of[(q.dim, q.shape, q.level)]
+            u = buf(n)
+            ts = time.perf_counter() - t0
+            t = sv.submit(c.coords, c.cells, q.level, q.rhs_seed, 0.1, rtol=rtol, max_iter=100, u_out=u)
+            if t is None:
+                pool[n].append(u)
+                if not retry:
+                    retry.append(pending.popleft())
+                eagain += 1
+                break
+            (retry if retry and retry[0] is q else pending).popleft()
+            outstanding[t] = (q, ts, u, n)
+            progressed = True
+        for t in list(outstanding):
+            r = sv.poll(t)
+            if not r.finished:
+                continue
+            q, ts, u, n = outstanding.pop(t)
+            sv.release(t)
+            pool[n].append(u)
+            progressed = True
+            if r.status != H.REQ_DONE:
+                failed += 1
+                errors[f"{r.error}: {r.message}"] += 1
+                continue
+            done_at = ts + r.queue_s + r.run_s
+            t_end = max(t_end, t0 + done_at)
+            lat.append(done_at - q.arrival_s)
+            run.append(r.run_s)
+            queue_s.append(r.queue_s)
+            iters.append(r.iters)
+            rels.append(r.relres)
+            ngs.append(r.n_global)
+            hits += int(r.cache_hit)
+        if not progressed:
+            time.sleep(0.0002)
+    span = t_end - t0
+    st = sv.stats()
+    sv.close()
+    pct = lambda v, p: float(np.percentile(np.asarray(v) * 1e3, p)) if v else None
+    return {
+        "workload": (f"solve server, {n_requests} requests of the synthetic stream (Poisson arrivals 2000/s, seed 3; "
+                     "half 2D: 4..64 jittered macro-triangles, levels 5..10; half 3D: 6..384 jittered macro-tets, "
+                     f"levels 3..6; lumped-mass RHS with 0.1 N(0,1) Philox noise per request seed); rtol {rtol}, "
+                     "fp32 V(3,3) cycles in float64 refinement; every solution copied to host memory; "
+                     f"{workers} worker streams, {cap_bytes >> 30} GiB device arena"),
+        "solves_per_s": len(lat) / span, "gdofs_solved_per_s": float(np.sum(ngs)) / span / 1e9,
+        "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
+        "service_ms_p50": pct(run, 50), "service_ms_p99": pct(run, 99), "queue_ms_p50": pct(queue_s, 50),
+        "span_s": span, "done": len(lat), "failed": failed, "failures": dict(errors.most_common(5)),
+        "admission_retries": eagain,
+        "cache_hits": hits, "evictions": st["evictions"], "iterations_mean": float(np.mean(iters)) if iters else None,
+        "relres_max": float(np.max(rels)) if rels else None,
+        "reached_rtol": bool(rels and max(rels) <= rtol),
+    }
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_oracle_run(steps, warmup):
     """The oracle's CSR SpMV on a bounded sample of the workload: the same
@@ -441,6 +548,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_variants:
         line["solve"] = solve_workload(device, stream)
         torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1 and not args.no_variants and args.serve_requests > 0:
+        line["serving"] = serve_workload(args.serve_requests, args.serve_workers)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         ng, ts, sample = cpu_oracle_run(5, 1)

@@ -45,12 +45,12 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def _jitter_interior(coords: np.ndarray, amplitude: float, seed: int) -> np.ndarray:
-    """Move every vertex not on the boundary of the unit box by U[-a, a] per
+def _jitter_interior(coords: np.ndarray, amplitude: float, seed: int, hi=1.0) -> np.ndarray:
+    """Move every vertex not on the boundary of the box [0, hi] by U[-a, a] per
     coordinate, drawn in ascending vertex-id order (x, y[, z] per vertex)."""
     if amplitude == 0.0:
         return coords
-    on_bnd = np.any((coords <= 0.0) | (coords >= 1.0), axis=1)
+    on_bnd = np.any((coords <= 0.0) | (coords >= np.asarray(hi)), axis=1)
     interior = np.nonzero(~on_bnd)[0]
     d = _rng(seed).uniform(-amplitude, amplitude, size=(interior.size, coords.shape[1]))
     out = coords.copy()
@@ -64,19 +64,22 @@ def unit_square_mesh(k: int, jitter: float = 0.0, seed: int = 0) -> CoarseMesh:
     return rect_mesh(k, k, jitter, seed)
 
 
-def rect_mesh(kx: int, ky: int, jitter: float = 0.0, seed: int = 0) -> CoarseMesh:
-    """kx x ky cells of the unit square, each split along its (0,0)-(1,1)
-    diagonal into two triangles.
+def rect_mesh(kx: int, ky: int, jitter: float = 0.0, seed: int = 0, square_cells: bool = False) -> CoarseMesh:
+    """kx x ky cells, each split along its (0,0)-(1,1) diagonal into two
+    triangles: cells of the unit square, or (square_cells) square cells of
+    side 1/max(kx, ky) filling the rectangle [0, kx/k] x [0, ky/k].
 
     Vertex id of grid point (i, j) is i + (kx+1) j.  For cell (i, j) with
     corners a=(i,j), b=(i+1,j), c=(i,j+1), d=(i+1,j+1) the triangles are
     (b, d, a) and (c, a, d): right angle (for square cells) first,
     counter-clockwise.  Cells are listed cell-row by cell-row, lower-right
     triangle first.  `jitter` is the amplitude as a fraction of the smaller
-    cell width min(1/kx, 1/ky).
+    cell width 1/max(kx, ky).
     """
-    gx = np.linspace(0.0, 1.0, kx + 1)
-    gy = np.linspace(0.0, 1.0, ky + 1)
+    k = max(kx, ky)
+    hx, hy = (kx / k, ky / k) if square_cells else (1.0, 1.0)
+    gx = np.linspace(0.0, hx, kx + 1)
+    gy = np.linspace(0.0, hy, ky + 1)
     xx, yy = np.meshgrid(gx, gy, indexing="xy")
     coords = np.stack([xx.ravel(), yy.ravel()], axis=1).astype(np.float64)
     cells = []
@@ -88,8 +91,8 @@ def rect_mesh(kx: int, ky: int, jitter: float = 0.0, seed: int = 0) -> CoarseMes
             d = c + 1
             cells.append((b, d, a))
             cells.append((c, a, d))
-    coords = _jitter_interior(coords, jitter / max(kx, ky), seed)
-    name = (f"square{kx}x{ky}" if kx == ky else f"rect{kx}x{ky}") + (f"_jit{jitter}_s{seed}" if jitter else "")
+    coords = _jitter_interior(coords, jitter / k, seed, (hx, hy))
+    name = (f"square{kx}x{ky}" if kx == ky else f"rect{kx}x{ky}" + ("sq" if square_cells else "")) + (f"_jit{jitter}_s{seed}" if jitter else "")
     return CoarseMesh(2, coords, np.asarray(cells, dtype=np.int64), name)
 
 
@@ -99,9 +102,11 @@ def unit_cube_kuhn_mesh(k: int, jitter: float = 0.0, seed: int = 0) -> CoarseMes
     return box_kuhn_mesh(k, k, k, jitter, seed)
 
 
-def box_kuhn_mesh(kx: int, ky: int, kz: int, jitter: float = 0.0, seed: int = 0) -> CoarseMesh:
-    """kx x ky x kz cells of the unit cube, each split into the 6 Kuhn
-    tetrahedra that share the cell's main diagonal.
+def box_kuhn_mesh(kx: int, ky: int, kz: int, jitter: float = 0.0, seed: int = 0,
+                  cube_cells: bool = False) -> CoarseMesh:
+    """kx x ky x kz cells, each split into the 6 Kuhn tetrahedra that share
+    the cell's main diagonal: cells of the unit cube, or (cube_cells) cubes of
+    side 1/max(kx, ky, kz) filling the box [0, kx/k] x [0, ky/k] x [0, kz/k].
 
     Vertex id of grid point (i, j, l) is i + (kx+1) j + (kx+1)(ky+1) l.  The
     tet of a permutation (p, q, r) of the axes has vertices corner,
@@ -109,9 +114,11 @@ def box_kuhn_mesh(kx: int, ky: int, kz: int, jitter: float = 0.0, seed: int = 0)
     Permutations are taken in itertools order; cells are listed cell by cell
     (i fastest).  `jitter` is a fraction of the smallest cell width.
     """
-    gx = np.linspace(0.0, 1.0, kx + 1)
-    gy = np.linspace(0.0, 1.0, ky + 1)
-    gz = np.linspace(0.0, 1.0, kz + 1)
+    k = max(kx, ky, kz)
+    hx, hy, hz = (kx / k, ky / k, kz / k) if cube_cells else (1.0, 1.0, 1.0)
+    gx = np.linspace(0.0, hx, kx + 1)
+    gy = np.linspace(0.0, hy, ky + 1)
+    gz = np.linspace(0.0, hz, kz + 1)
     zz, yy, xx = np.meshgrid(gz, gy, gx, indexing="ij")
     coords = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1).astype(np.float64)
 
@@ -131,8 +138,8 @@ def box_kuhn_mesh(kx: int, ky: int, kz: int, jitter: float = 0.0, seed: int = 0)
                     p2[perm[1]] += 1
                     p3 = base + 1
                     cells.append(tuple(vid(*p) for p in (p0, p1, p2, p3)))
-    coords = _jitter_interior(coords, jitter / max(kx, ky, kz), seed)
-    name = (f"cube{kx}^3kuhn" if kx == ky == kz else f"box{kx}x{ky}x{kz}kuhn") + (
+    coords = _jitter_interior(coords, jitter / k, seed, (hx, hy, hz))
+    name = (f"cube{kx}^3kuhn" if kx == ky == kz else f"box{kx}x{ky}x{kz}kuhn" + ("cc" if cube_cells else "")) + (
         f"_jit{jitter}_s{seed}" if jitter else "")
     return CoarseMesh(3, coords, np.asarray(cells, dtype=np.int64), name)
 

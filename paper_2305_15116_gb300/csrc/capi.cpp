@@ -123,7 +123,10 @@ void hyteg_mesh_destroy(hyteg_mesh* mesh) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(m.device);
-    if (!m.mem.arena) cudaDeviceSynchronize();
+    if (m.mem.arena)
+      hyteg::dev_sync(m);
+    else
+      cudaDeviceSynchronize();
     for (auto& L : m.levels) hyteg::free_level(m, L);
     hyteg::dev_free(m, m.d_prims);
     hyteg::dev_free(m, m.d_incs);

@@ -93,6 +93,11 @@ size_t arena_used(Arena* a) {
   return a->used;
 }
 
+size_t arena_free_bytes(Arena* a) {
+  std::lock_guard<std::mutex> lk(a->mu);
+  return a->size - a->used;
+}
+
 size_t arena_largest_free(Arena* a) {
   std::lock_guard<std::mutex> lk(a->mu);
   size_t best = 0;
@@ -110,10 +115,15 @@ cudaError_t dev_alloc(const Mesh& m, void** p, size_t bytes) {
 
 void dev_free(const Mesh& m, void* p) {
   if (!p) return;
-  if (m.mem.arena)
+  if (m.mem.arena) {
+    // Arena blocks are handed to the next allocation at once, possibly on
+    // another stream: drain the work this mesh queued (uploads, clears,
+    // kernels) first, so that nothing of it lands in the block's next owner.
+    cudaStreamSynchronize(m.mem.stream);
     arena_free(m.mem.arena, p);
-  else
-    cudaFree(p);
+  } else {
+    cudaFree(p);  // synchronises the device itself
+  }
 }
 
 cudaError_t dev_upload(const Mesh& m, void* dst, const void* src, size_t bytes) {

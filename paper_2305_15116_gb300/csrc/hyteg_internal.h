@@ -154,6 +154,7 @@ void* arena_alloc(Arena* a, size_t bytes);
 void arena_free(Arena* a, void* p);
 size_t arena_used(Arena* a);
 size_t arena_largest_free(Arena* a);
+size_t arena_free_bytes(Arena* a);
 cudaError_t dev_alloc(const Mesh& m, void** p, size_t bytes);
 void dev_free(const Mesh& m, void* p);
 cudaError_t dev_upload(const Mesh& m, void* dst, const void* src, size_t bytes);

@@ -14,6 +14,7 @@
 // the coarse micro-edges), dividing every fine value by the number of macros
 // that hold a copy of it; the interface step then sums the partials of the
 // copies of every coarse interface point and zeroes the Dirichlet rows.
+#include <cmath>
 #include <vector>
 
 #include "arith.cuh"
@@ -542,7 +543,7 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
     double nr = 0.0;
     HY_TRY(norm2<double>(m, l, g.r64, &nr, s));
     rel = nr / nb;
-    if (rel <= rtol || it >= max_iter) break;
+    if (rel <= rtol || it >= max_iter || !std::isfinite(rel)) break;  // a non-finite residual ends the loop
     // A cycle reduces the residual by its convergence factor (about 0.4)
     // until the float64 representation of u is reached; two iterations in a
     // row that no longer halve it mean that floor has been reached.

@@ -112,7 +112,7 @@ struct hyteg_server {
   int64_t submitted = 0, done = 0, failed = 0, hits = 0, evictions = 0;
 
   void worker(int w);
-  int run(Req& r, cudaStream_t s, bool* hit);
+  int run(Req& r, cudaStream_t s, bool* hit, hyteg_result* res, std::string* msg);
   Entry* acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::string* msg);
   void release(Entry* e);
   bool evict_one();  // caller holds mu
@@ -156,8 +156,16 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
       }
   }
   *hit = false;
-  // build a new entry; on a full arena drop idle entries, then wait (bounded)
-  // for requests in flight to hand theirs back
+  // make room first: drop idle cached meshes, least recently used first,
+  // until the arena's free bytes cover the request's estimate
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    while (hyteg::arena_free_bytes(arena) < r.est && evict_one()) {
+    }
+  }
+  // build a new entry; should the arena still run out (fragmentation), drop
+  // more idle entries, then wait (bounded) for requests in flight to hand
+  // theirs back
   const auto deadline = Clock::now() + std::chrono::seconds(120);
   for (;;) {
     auto e = std::make_unique<Entry>();
@@ -214,30 +222,33 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
 }
 
 void hyteg_server::release(Entry* e) {
+  // its work has drained (the worker synchronised its stream); an idle mesh
+  // refers to no worker stream, so dropping it later waits for nothing
+  e->mesh->m.mem.stream = nullptr;
   std::lock_guard<std::mutex> lk(mu);
   e->busy = false;
   idle.push_front(e);
   cv_done.notify_all();
 }
 
-int hyteg_server::run(Req& r, cudaStream_t s, bool* hit) {
+int hyteg_server::run(Req& r, cudaStream_t s, bool* hit, hyteg_result* res, std::string* msg) {
   int err = HYTEG_OK;
-  Entry* e = acquire(r, s, hit, &err, &r.msg);
+  Entry* e = acquire(r, s, hit, &err, msg);
   if (!e) return err;
   hyteg::Mesh& m = e->mesh->m;
   m.mem.stream = s;
   const int64_t ns = slots_of(r.dim, r.level, m.n_cells);
-  r.res.n_global = e->n_global;
+  res->n_global = e->n_global;
   int rc = HYTEG_OK;
   cudaError_t ce = hyteg::poisson_rhs(m, r.level, r.seed, r.noise, e->b, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(e->u, 0, size_t(ns) * 8, s);
   if (ce != cudaSuccess) {
     rc = HYTEG_ECUDA;
-    r.msg = std::string("right-hand side: ") + cudaGetErrorString(ce);
+    *msg = std::string("right-hand side: ") + cudaGetErrorString(ce);
   }
   if (rc == HYTEG_OK) {
-    rc = hyteg_solve(e->mesh, r.level, r.mode, e->b, e->u, r.rtol, r.max_iter, s, &r.res.iters, &r.res.relres);
-    if (rc != HYTEG_OK) r.msg = hyteg_last_error();
+    rc = hyteg_solve(e->mesh, r.level, r.mode, e->b, e->u, r.rtol, r.max_iter, s, &res->iters, &res->relres);
+    if (rc != HYTEG_OK) *msg = hyteg_last_error();
   }
   for (int k = 0; k < 2 && rc == HYTEG_OK; ++k) {
     double* host = k == 0 ? r.u_out : r.b_out;
@@ -248,13 +259,13 @@ int hyteg_server::run(Req& r, cudaStream_t s, bool* hit) {
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) {
       rc = HYTEG_ECUDA;
-      r.msg = std::string("result copy: ") + cudaGetErrorString(ce);
+      *msg = std::string("result copy: ") + cudaGetErrorString(ce);
     }
   }
   ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess && rc == HYTEG_OK) {
     rc = HYTEG_ECUDA;
-    r.msg = cudaGetErrorString(ce);
+    *msg = cudaGetErrorString(ce);
   }
   if (rc == HYTEG_ECUDA) {
     // leave a mesh whose last use failed out of the cache
@@ -288,9 +299,15 @@ void hyteg_server::worker(int w) {
       r->res.queue_s = seconds_since(r->t_submit, r->t_start);
     }
     bool hit = false;
-    const int rc = run(*r, s, &hit);
+    hyteg_result res{};
+    std::string msg;
+    const int rc = run(*r, s, &hit, &res, &msg);
     {
       std::lock_guard<std::mutex> lk(mu);
+      r->res.iters = res.iters;
+      r->res.relres = res.relres;
+      r->res.n_global = res.n_global;
+      r->msg = msg;
       r->res.run_s = seconds_since(r->t_start, Clock::now());
       r->res.cache_hit = hit ? 1 : 0;
       r->res.error = rc;

@@ -20,6 +20,7 @@ class Result:
     queue_s: float
     run_s: float
     n_global: int
+    message: str = ""
 
     @property
     def finished(self) -> bool:
@@ -27,7 +28,8 @@ class Result:
 
 
 def _result(r: C.Result) -> Result:
-    return Result(r.status, r.error, r.iters, bool(r.cache_hit), r.relres, r.queue_s, r.run_s, r.n_global)
+    msg = C.lib.hyteg_last_error().decode(errors="replace") if r.status == REQ_FAILED else ""
+    return Result(r.status, r.error, r.iters, bool(r.cache_hit), r.relres, r.queue_s, r.run_s, r.n_global, msg)
 
 
 class Server:
