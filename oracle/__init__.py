@@ -18,6 +18,10 @@ Performance Analysis of the HyTeG Finite Element Framework" (PASC '23):
   (Sec. 1.2, Sec. 2).
 * `layout`   — the paper's closed-form DoF counts and memory volumes (Sec. 2.1,
   Table "memory level 10") and the triangular index map.
+* `p2`       — the P2 (vertex + edge DoF) stiffness of the refined 2D mesh:
+  the discretisation whose vertex-to-vertex, edge-to-vertex, vertex-to-edge
+  and edge-to-edge kernels the paper analyses (Sec. 2.1, Sec. 4.2-4.5),
+  assembled from quadratic element matrices.
 * `multigrid` — a textbook V-cycle on the refinement hierarchy (levels as the
   multigrid hierarchy, Sec. 1.2; smoothers, Sec. 4.1): linear prolongation,
   R = P^T, weighted Jacobi, direct coarsest solve, lumped-mass right-hand
