@@ -223,6 +223,48 @@ int hyteg_vcycle(hyteg_mesh* mesh, int level, int dtype, const void* b, void* u,
 int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double rtol, int max_iter,
                 void* stream, int* iters, double* relres);
 
+/* ---- P2: vertex + edge DoFs (2D) -----------------------------------------
+ * The discretisation of the paper's four kernels: quadratic elements on the
+ * refined triangles, one DoF per refined vertex and one per micro-edge
+ * (Sec. 2.1: #vertex + 3 #edge DoFs per macro, the edges grouped into the
+ * orientations X, Y and XY).  hyteg_p2_apply computes y = A x with A the P2
+ * stiffness matrix (Dirichlet identity rows on the domain boundary when the
+ * mesh was created with HYTEG_BC_DIRICHLET) in one pass over all four arrays:
+ * the vertex-to-vertex, edge-to-vertex, vertex-to-edge and edge-to-edge
+ * couplings of Sec. 4.2-4.5 merged, as the paper proposes (Sec. 6), then the
+ * interface reduction of the copies.  2D meshes only.
+ *
+ * Slot layout per macro (macros in cell order): the vertex array of the P1
+ * layout ((n+1)(n+2)/2 slots), then three edge arrays X, Y, XY of n(n+1)/2
+ * slots each; edge (x, y) of a group (x + y <= n-1) sits at
+ * y n - y(y-1)/2 + x; X(x,y) joins lattice points (x,y)-(x+1,y), Y(x,y)
+ * joins (x,y)-(x,y+1), XY(x,y) joins (x+1,y)-(x,y+1).  Interface DoFs have
+ * one copy per incident macro; inputs must have equal copies.
+ *
+ * Global numbering (hyteg_p2_dof_map): the vertices as hyteg_dof_map; then the
+ * micro-edges on coarse edges, coarse edges in sorted (low id, high id)
+ * order, n each, counted from the low-id end; then the macro-interior
+ * micro-edges, cell by cell, in slot order (X with y >= 1, Y with x >= 1, XY
+ * with x + y <= n-2). */
+
+/* Slot count of a P2 vector at `level` and the number of distinct P2 DoFs
+ * (host only).  Errors: HYTEG_EINVAL (NULL mesh, level outside 0..15, 3D). */
+int hyteg_p2_num_slots(const hyteg_mesh* mesh, int level, int64_t* n_slots, int64_t* n_global);
+
+/* Global P2 id of every slot (host array of hyteg_p2_num_slots entries). */
+int hyteg_p2_dof_map(const hyteg_mesh* mesh, int level, int64_t* global_id);
+
+/* y = A x for the P2 stiffness on a refined level; x, y device arrays of
+ * P2 slots of the dtype (as hyteg_apply).  Asynchronous on `stream`; three
+ * kernels (the merged apply, the vertex and the edge interface reductions).
+ * Errors: HYTEG_EINVAL, HYTEG_ESTATE (level not refined), HYTEG_ECUDA. */
+int hyteg_p2_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream);
+
+/* hyteg_p2_apply that records the caller's events before the apply kernel,
+ * between it and the interface kernels, and after them (each nullable). */
+int hyteg_p2_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream,
+                         void* ev_begin, void* ev_mid, void* ev_end);
+
 /* ---- the Poisson model problem -----------------------------------------
  * -Laplace u = f in the domain of the coarse mesh, u = 0 on its boundary,
  * discretised with the P1 stiffness matrix of the refined mesh (Sec. 1.1)

@@ -62,6 +62,17 @@ lib.hyteg_solve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.
                             ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_double)]
 lib.hyteg_solve.restype = ctypes.c_int
+lib.hyteg_p2_num_slots.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p, c_i64p]
+lib.hyteg_p2_num_slots.restype = ctypes.c_int
+lib.hyteg_p2_dof_map.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p]
+lib.hyteg_p2_dof_map.restype = ctypes.c_int
+lib.hyteg_p2_apply.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p]
+lib.hyteg_p2_apply.restype = ctypes.c_int
+lib.hyteg_p2_apply_timed.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]
+lib.hyteg_p2_apply_timed.restype = ctypes.c_int
 lib.hyteg_poisson_rhs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p,
                                   ctypes.c_void_p]
 lib.hyteg_poisson_rhs.restype = ctypes.c_int

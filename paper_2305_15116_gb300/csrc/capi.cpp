@@ -310,6 +310,53 @@ int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* 
   return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "solve");
 }
 
+int hyteg_p2_num_slots(const hyteg_mesh* mesh, int level, int64_t* n_slots, int64_t* n_global) {
+  if (int r = check_host_level(mesh, level)) return r;
+  if (mesh->m.dim != 2) return fail(HYTEG_EINVAL, "the P2 operator is built for 2D meshes");
+  if (n_slots) *n_slots = mesh->m.n_cells * hyteg::p2_slots_per_macro(level);
+  if (n_global) *n_global = hyteg::p2_n_global(mesh->m, level);
+  return HYTEG_OK;
+}
+
+int hyteg_p2_dof_map(const hyteg_mesh* mesh, int level, int64_t* global_id) {
+  if (int r = check_host_level(mesh, level)) return r;
+  if (mesh->m.dim != 2) return fail(HYTEG_EINVAL, "the P2 operator is built for 2D meshes");
+  if (!global_id) return fail(HYTEG_EINVAL, "global_id is NULL");
+  try {
+    hyteg::compute_p2_dof_map(mesh->m, level, global_id);
+  } catch (const std::exception& ex) {
+    return fail(HYTEG_EINVAL, ex.what());
+  }
+  return HYTEG_OK;
+}
+
+int hyteg_p2_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream,
+                         void* ev_begin, void* ev_mid, void* ev_end) {
+  if (int r = check_level(mesh, level)) return r;
+  if (mesh->m.dim != 2) return fail(HYTEG_EINVAL, "the P2 operator is built for 2D meshes");
+  if (!valid_dtype(dtype)) return fail(HYTEG_EINVAL, "unknown dtype");
+  if (!x || !y) return fail(HYTEG_EINVAL, "x or y is NULL");
+  const hyteg::Mesh& m = mesh->m;
+  const size_t bytes = size_t(m.n_cells) * size_t(hyteg::p2_slots_per_macro(level)) * elem_size(dtype);
+  const char* xb = static_cast<const char*>(x);
+  const char* yb = static_cast<const char*>(y);
+  if (xb < yb + bytes && yb < xb + bytes) return fail(HYTEG_EINVAL, "x and y overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (ev_begin && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), s)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventRecord");
+  const char* what = "";
+  e = hyteg::launch_p2_apply(m, level, dtype, x, y, s, static_cast<cudaEvent_t>(ev_mid), &what);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  if (ev_end && (e = cudaEventRecord(static_cast<cudaEvent_t>(ev_end), s)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventRecord");
+  return HYTEG_OK;
+}
+
+int hyteg_p2_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream) {
+  return hyteg_p2_apply_timed(mesh, level, dtype, x, y, stream, nullptr, nullptr, nullptr);
+}
+
 int hyteg_poisson_rhs(hyteg_mesh* mesh, int level, uint64_t seed, double noise, double* b, void* stream) {
   if (int r = check_solver(mesh, level, 0)) return r;
   if (!b) return fail(HYTEG_EINVAL, "b is NULL");

@@ -48,7 +48,25 @@ struct LevelDev {
   int n_slabs = 0;
   // host copy of the class stencils (multigrid set-up)
   std::vector<double> st_host;
+  // P2 (2D): class stencils [cell][P2W] and the edge interface work list
+  // int4 (prim, t0, t1, 0): micro-edges t0..t1-1 of a coarse edge
+  double* p2_st64 = nullptr;
+  float* p2_st32 = nullptr;
+  float* p2_hi = nullptr;
+  float* p2_lo = nullptr;
+  int4* p2_items = nullptr;
+  int n_p2_items = 0;
 };
+
+// P2 stencil table of one macro: 8 vertex classes x 19 weights, then for each
+// edge group (X, Y, XY) an interior and a macro-boundary class of 9 weights.
+constexpr int P2_NV = 19;
+constexpr int P2_NE = 9;
+constexpr int P2W = 8 * P2_NV + 3 * 2 * P2_NE;  // 206
+constexpr int P2_EOFF = 8 * P2_NV;               // first edge-class weight
+
+int64_t p2_edge_slots(int level);  // n(n+1)/2 edges of one group per macro
+int64_t p2_slots_per_macro(int level);
 
 // Interface primitive (coarse vertex, edge or face) and its incident cells.
 struct Prim {
@@ -146,6 +164,13 @@ void set_last_error(const std::string& msg);
 std::string build_topology(Mesh& m);
 std::string build_level(Mesh& m, int level, LevelDev& out);
 void free_level(const Mesh& m, LevelDev& L);
+
+// ---- P2 (p2_setup.cpp, p2.cu) ------------------------------------------------
+std::string build_p2_level(Mesh& m, int level, LevelDev& L);
+int64_t p2_n_global(const Mesh& m, int level);
+void compute_p2_dof_map(const Mesh& m, int level, int64_t* gid);
+cudaError_t launch_p2_apply(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
+                            cudaEvent_t ev_mid, const char** what);
 
 // ---- device memory (devmem.cpp) ---------------------------------------------
 Arena* arena_create(size_t bytes, std::string& err);

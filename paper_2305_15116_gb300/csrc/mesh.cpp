@@ -298,6 +298,11 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.tiles);
   dev_free(m, L.items);
   dev_free(m, L.slabs);
+  dev_free(m, L.p2_st64);
+  dev_free(m, L.p2_st32);
+  dev_free(m, L.p2_hi);
+  dev_free(m, L.p2_lo);
+  dev_free(m, L.p2_items);
   L = LevelDev{};
 }
 
@@ -463,6 +468,7 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   if (!(err = upload(m, &L.tiles, tiles)).empty()) return err;
   if (!(err = upload(m, &L.items, items)).empty()) return err;
   if (!(err = upload(m, &L.slabs, slabs)).empty()) return err;
+  if (d == 2) return build_p2_level(m, level, L);
   return "";
 }
 

@@ -201,3 +201,31 @@ class Mesh:
                                       ctypes.c_void_p(v_global.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
                 "hyteg_to_global")
         return v_global
+
+    # ---- P2 (vertex + edge DoFs, 2D) ---------------------------------------------
+    def p2_num_slots(self, level: int):
+        ns, ng = ctypes.c_int64(), ctypes.c_int64()
+        C.check(C.lib.hyteg_p2_num_slots(self._h, level, ctypes.byref(ns), ctypes.byref(ng)), "hyteg_p2_num_slots")
+        return ns.value, ng.value
+
+    def p2_dof_map(self, level: int) -> np.ndarray:
+        ns, _ = self.p2_num_slots(level)
+        out = np.empty(ns, dtype=np.int64)
+        C.check(C.lib.hyteg_p2_dof_map(self._h, level, out.ctypes.data_as(C.c_i64p)), "hyteg_p2_dof_map")
+        return out
+
+    def p2_apply(self, level: int, x, y, ieee: bool = False, stream=None):
+        """y = A x with the P2 stiffness (device tensors of P2 slots)."""
+        code = self._dtype_code(x, ieee)
+        C.check(C.lib.hyteg_p2_apply(self._h, level, code, ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+                "hyteg_p2_apply")
+        return y
+
+    def p2_apply_timed(self, level: int, dtype: int, x_ptr: int, y_ptr: int, stream_ptr: int,
+                       ev_begin: int, ev_mid: int, ev_end: int) -> None:
+        """P2 apply on raw pointers recording three raw cudaEvent_t handles
+        around the merged apply kernel and the interface kernels."""
+        C.check(C.lib.hyteg_p2_apply_timed(self._h, level, dtype, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
+                                           ctypes.c_void_p(stream_ptr), ctypes.c_void_p(ev_begin),
+                                           ctypes.c_void_p(ev_mid), ctypes.c_void_p(ev_end)), "hyteg_p2_apply_timed")

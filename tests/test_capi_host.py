@@ -130,3 +130,29 @@ def test_slot_coords_and_lumped_mass_match_oracle(lib, dim, k, L):
     same = smap[order][1:] == smap[order][:-1]
     assert np.array_equal(xyz[order][1:][same], xyz[order][:-1][same])
     assert np.array_equal(mass[order][1:][same], mass[order][:-1][same])
+
+
+@pytest.mark.parametrize("kx,ky,jit,L", [(1, 1, 0.0, 0), (1, 1, 0.0, 3), (3, 2, 0.15, 2), (4, 4, 0.15, 4)])
+def test_p2_dof_map_matches_oracle(lib, kx, ky, jit, L):
+    """The library's P2 global numbering and the oracle's name the same DoFs:
+    one bijection between the two id sets maps every slot."""
+    import oracle.p2 as p2
+    from inputs import rect_mesh
+    m = rect_mesh(kx, ky, jit, 0)
+    M = lib.Mesh(m.coords, m.cells)
+    pm = p2.P2Mesh(m.coords, m.cells, L)
+    ns, ng = M.p2_num_slots(L)
+    assert ng == pm.n_global
+    assert ns == m.n_cells * oracle.p2_dofs_per_macro(L)
+    mine, ref = M.p2_dof_map(L), pm.slot_map()
+    assert mine.shape == ref.shape
+    assert set(mine.tolist()) == set(range(ng))
+    fwd = {}
+    for a, b in zip(mine.tolist(), ref.tolist()):
+        assert fwd.setdefault(a, b) == b
+    assert len(set(fwd.values())) == ng
+    # vertices keep the P1 numbering
+    nv = oracle.slots_per_macro(2, L)
+    per = oracle.p2_dofs_per_macro(L)
+    vslots = np.concatenate([np.arange(c * per, c * per + nv) for c in range(m.n_cells)])
+    np.testing.assert_array_equal(mine[vslots], M.dof_map(L))
