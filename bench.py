@@ -80,7 +80,8 @@ def describe(name, n_global, n_slots):
         shape = f"unit cube, {w['k']}^3 cells x 6 Kuhn tets = {6 * w['k'] ** 3} macro-tets"
     jit = f", interior coarse vertices jittered U[-{w['jitter']}h, {w['jitter']}h] (seed {w['mesh_seed']})" \
         if w["jitter"] else ""
-    return (f"{name}: {w['dim']}D P1 Laplacian apply, {shape}{jit}, level {w['level']}, "
+    disc = "P2 (vertex + edge DoF)" if w.get("op") == "p2" else "P1"
+    return (f"{name}: {w['dim']}D {disc} Laplacian apply, {shape}{jit}, level {w['level']}, "
             f"{n_global} DoFs ({n_slots} slots), x ~ U[-1,1] seed {w['x_seed']}, Dirichlet rows identity")
 
 
@@ -152,10 +153,12 @@ def setup(name, device, dtype_code, level=None):
     import torch
     import paper_2305_15116_gb300 as H
     from inputs import workload, random_vector
+    from inputs import WORKLOADS
     coarse, L, seed = workload(name, level)
+    p2 = WORKLOADS[name].get("op") == "p2"
     M = H.Mesh(coarse.coords, coarse.cells).refine(L)
-    ns, ng = M.num_slots(L)
-    smap = M.dof_map(L)
+    ns, ng = M.p2_num_slots(L) if p2 else M.num_slots(L)
+    smap = M.p2_dof_map(L) if p2 else M.dof_map(L)
     x = random_vector(ng, seed)
     tdt = torch.float32 if dtype_code == H.F32 else torch.float64
     xs = torch.from_numpy(x[smap]).to(device=device, dtype=tdt)
@@ -163,9 +166,16 @@ def setup(name, device, dtype_code, level=None):
     n = 1 << L
     interior = coarse.n_cells * ((n - 1) * (n - 2) // 2 if coarse.dim == 2 else (n - 1) * (n - 2) * (n - 3) // 6)
     slab = coarse.dim == 3 and n <= 64  # the 3D slab kernel writes every slot
+    if p2:
+        kernel = "k_p2_apply"
+        raw = lambda l, c, xp, yp, sp: M.p2_apply_timed(l, c, xp, yp, sp, 0, 0, 0)
+        timed = M.p2_apply_timed
+    else:
+        kernel = "k_slab3d" if slab else ("k_interior2d" if coarse.dim == 2 else "k_interior3d")
+        raw, timed = M.apply_raw, M.apply_timed
     return dict(M=M, L=L, ns=ns, ng=ng, xs=xs, ys=ys, smap=smap, x_global=x, coarse=coarse,
-                interior=interior, elem=4 if dtype_code == H.F32 else 8, code=dtype_code, slab=slab,
-                kernel=("k_slab3d" if slab else ("k_interior2d" if coarse.dim == 2 else "k_interior3d")))
+                interior=interior, elem=4 if dtype_code == H.F32 else 8, code=dtype_code,
+                slab=slab or p2, kernel=kernel, apply_raw=raw, apply_timed=timed, op="p2" if p2 else "p1")
 
 
 def timed_applies(w, steps, warmup, stream, barrier=None):
@@ -181,7 +191,7 @@ def timed_applies(w, steps, warmup, stream, barrier=None):
             for e in row:
                 e.record(stream)
         for _ in range(warmup):
-            M.apply_raw(L, code, xp, yp, sp)
+            w["apply_raw"](L, code, xp, yp, sp)
     torch.cuda.synchronize()
     if barrier:
         barrier()
@@ -190,7 +200,7 @@ def timed_applies(w, steps, warmup, stream, barrier=None):
     t0 = time.time()
     start.record(stream)
     for k in range(steps):
-        M.apply_timed(L, code, xp, yp, sp, ev[k][0].cuda_event, ev[k][1].cuda_event, ev[k][2].cuda_event)
+        w["apply_timed"](L, code, xp, yp, sp, ev[k][0].cuda_event, ev[k][1].cuda_event, ev[k][2].cuda_event)
     end.record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
@@ -207,7 +217,8 @@ def interior_bytes(w):
     """Algorithmic bytes of one launch of the dominant kernel: every slot of
     every macro is read once (interior points and the macro-boundary halo);
     every interior point is written once (2D and row kernels), or every slot
-    (the 3D slab kernel, which also writes the macro-boundary partials)."""
+    (the 3D slab kernel and the P2 kernel, which also write the
+    macro-boundary partials)."""
     return w["elem"] * (w["ns"] + (w["ns"] if w["slab"] else w["interior"]))
 
 
@@ -527,7 +538,10 @@ def main():
                                    (WORKLOAD, H.F32, "f32"), (WORKLOAD, H.F64_IEEE, "f64 native fma"),
                                    ("cube384jit_L6", H.F64, "f64 data, float-float arithmetic"),
                                    ("cube384jit_L6", H.F32, "f32"),
-                                   ("cube384jit_L6", H.F64_IEEE, "f64 native fma")):
+                                   ("cube384jit_L6", H.F64_IEEE, "f64 native fma"),
+                                   ("square32jit_P2_L10", H.F64, "f64 data, float-float arithmetic"),
+                                   ("square32jit_P2_L10", H.F32, "f32"),
+                                   ("square32jit_P2_L10", H.F64_IEEE, "f64 native fma")):
             if name == args.workload and vcode == code:
                 continue
             v = setup(name, device, vcode)

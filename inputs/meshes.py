@@ -160,6 +160,9 @@ WORKLOADS = {
     "square2_L7": dict(dim=2, k=1, jitter=0.0, mesh_seed=0, level=7, x_seed=1),
     # 32 jittered macro-triangles, level 11 (~67M DoFs): the 2D throughput case
     "square32jit_L11": dict(dim=2, k=4, jitter=0.15, mesh_seed=0, level=11, x_seed=1),
+    # the same 32 macros with P2 (vertex + edge) DoFs at level 10: as many DoFs
+    # per macro as P1 at level 11 (the paper's #dof of Sec. 2.1, 67.2M slots)
+    "square32jit_P2_L10": dict(dim=2, k=4, jitter=0.15, mesh_seed=0, level=10, x_seed=1, op="p2"),
     # 384 jittered Kuhn macro-tets, level 6 (~17M DoFs): the 3D throughput case
     "cube384jit_L6": dict(dim=3, k=4, jitter=0.1, mesh_seed=0, level=6, x_seed=1),
     # Poisson solve: 32 jittered macro-triangles at level 10, noise seed 2

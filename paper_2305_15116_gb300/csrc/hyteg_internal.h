@@ -56,6 +56,10 @@ struct LevelDev {
   float* p2_lo = nullptr;
   int4* p2_items = nullptr;
   int n_p2_items = 0;
+  // P2 row-kernel work list: int4 (x0, y0, y1, 0): lattice columns x0..x0+29,
+  // rows y0..y1-1 of one macro
+  int4* p2_tiles = nullptr;
+  int n_p2_tiles = 0;
 };
 
 // P2 stencil table of one macro: 8 vertex classes x 19 weights, then for each

@@ -303,6 +303,7 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.p2_hi);
   dev_free(m, L.p2_lo);
   dev_free(m, L.p2_items);
+  dev_free(m, L.p2_tiles);
   L = LevelDev{};
 }
 

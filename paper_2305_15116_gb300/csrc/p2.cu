@@ -74,30 +74,297 @@ __device__ __forceinline__ typename P::T row(const typename P::T* __restrict__ x
   return P::finish1(a);
 }
 
+// DoFs on the macro's edges: every lattice point on the macro boundary or
+// next to its long edge, one thread each, evaluates those of its DoFs whose
+// class is not interior, with the class's partial stencil; neighbours outside
+// the macro carry weight 0 and are not read.  Points of one macro: row y = 0
+// (x = 0..n), column x = 0 (y = 1..n), the long edge x + y = n (x = 1..n-1)
+// and the line x + y = n-1 (x = 1..n-2).
 template <class P>
-__global__ void __launch_bounds__(128) k_p2_apply(const typename P::T* __restrict__ x, typename P::T* __restrict__ y,
-                                                  Geo G, StencilPtr st) {
-  const int px = blockIdx.x * blockDim.x + threadIdx.x;
-  const int py = blockIdx.y;
+__global__ void __launch_bounds__(128) k_p2_boundary(const typename P::T* __restrict__ x,
+                                                     typename P::T* __restrict__ y, Geo G, StencilPtr st,
+                                                     int n_points) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_points) return;
   const int n = G.n;
-  if (px > n - py) return;
-  const int64_t cell = blockIdx.z;
+  int px, py;
+  if (i <= n) {
+    px = i, py = 0;
+  } else if (i <= 2 * n) {
+    px = 0, py = i - n;
+  } else if (i < 3 * n) {
+    px = i - 2 * n, py = n - px;
+  } else {
+    px = i - 3 * n + 1, py = n - 1 - px;
+  }
+  const int64_t cell = blockIdx.y;
   const typename P::T* __restrict__ xm = x + cell * G.S2;
   typename P::T* __restrict__ ym = y + cell * G.S2;
   const int64_t wb = cell * P2W;
-  // vertex row; the first neighbour of every list is valid for every DoF of
-  // its kind, so it starts the sum unchecked
-  {
-    const int cls = (px == 0 ? 1 : 0) | (py == 0 ? 2 : 0) | (px + py == n ? 4 : 0);
-    ym[G.vidx(px, py)] = row<P, P2_NV>(xm, G, c_nbv, st, wb + cls * P2_NV, px, py, cls != 0);
-  }
+  const int cls = (px == 0 ? 1 : 0) | (py == 0 ? 2 : 0) | (px + py == n ? 4 : 0);
+  // the first neighbour of every list is valid for every DoF of its kind
+  if (cls != 0) ym[G.vidx(px, py)] = row<P, P2_NV>(xm, G, c_nbv, st, wb + cls * P2_NV, px, py, true);
   if (px + py <= n - 1) {
-    const int bnd[3] = {py == 0, px == 0, px + py == n - 1};
+    const bool bnd[3] = {py == 0, px == 0, px + py == n - 1};
 #pragma unroll
     for (int g = 0; g < 3; ++g)
-      ym[G.eidx(g, px, py)] = row<P, P2_NE>(xm, G, c_nbe[g], st, wb + P2_EOFF + (g * 2 + bnd[g]) * P2_NE, px, py,
-                                            bnd[g] != 0);
+      if (bnd[g])
+        ym[G.eidx(g, px, py)] = row<P, P2_NE>(xm, G, c_nbe[g], st, wb + P2_EOFF + (g * 2 + 1) * P2_NE, px, py, true);
   }
+}
+
+// ---- row kernel for the macro-interior DoFs -----------------------------------
+// One warp per tile of 32 lattice columns (30 written) and up to 64 rows of one
+// macro, walking up the rows as the P1 kernel does: every lane stages its
+// column of the next rows of all four arrays with cp.async, keeps three rows
+// of each array in registers (with the x-1 / x+1 neighbours fetched once per
+// row by warp shuffles) and evaluates the four DoFs of its lattice point
+// whose class is interior:
+//   V(x,y): x >= 1, y >= 1, x + y <= n-1     X(x,y): y >= 1, x + y <= n-1
+//   Y(x,y): x >= 1, x + y <= n-1              XY(x,y): x + y <= n-2
+// The DoFs on the macro's edges (their partial rows) come from k_p2_apply in
+// boundary mode.
+
+// One row r of the four arrays seen from one lane (column c): own values,
+// their right (x+1, "e") and left (x-1, "w") neighbours where a stencil needs them.
+template <class P>
+struct P2Row {
+  typename P::V vc, ve, vw, xc, xw, yc, ye, yw, dc, dw;
+};
+
+template <class P>
+__device__ __forceinline__ P2Row<P> make_p2row(typename P::V v, typename P::V ex, typename P::V ey,
+                                               typename P::V ed) {
+  P2Row<P> r;
+  r.vc = v;
+  r.ve = P::down(v);
+  r.vw = P::up(v);
+  r.xc = ex;
+  r.xw = P::up(ex);
+  r.yc = ey;
+  r.ye = P::down(ey);
+  r.yw = P::up(ey);
+  r.dc = ed;
+  r.dw = P::up(ed);
+  return r;
+}
+
+// The 46 interior weights of a macro (19 vertex row, 9 per edge group), kept
+// in registers for fp32 and in shared memory (one slice per warp) otherwise.
+template <class P, bool REG>
+struct P2W46;
+template <class P>
+struct P2W46<P, true> {
+  typename P::W w[46];
+  __device__ __forceinline__ void init(const StencilPtr& st, int64_t base, typename P::W*) {
+#pragma unroll
+    for (int k = 0; k < 46; ++k) w[k] = P::weight(st, k < P2_NV ? base + k : base + P2_EOFF + ((k - P2_NV) / P2_NE) * 2 * P2_NE + (k - P2_NV) % P2_NE);
+  }
+  __device__ __forceinline__ const typename P::W& operator[](int k) const { return w[k]; }
+};
+template <class P>
+struct P2W46<P, false> {
+  typename P::W* w;
+  __device__ __forceinline__ void init(const StencilPtr& st, int64_t base, typename P::W* slice) {
+    w = slice;
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < 46; k += 32)
+      w[k] = P::weight(st, k < P2_NV ? base + k : base + P2_EOFF + ((k - P2_NV) / P2_NE) * 2 * P2_NE + (k - P2_NV) % P2_NE);
+    __syncwarp();
+  }
+  __device__ __forceinline__ const typename P::W& operator[](int k) const { return w[k]; }
+};
+
+__device__ __forceinline__ void p2_cp_async(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void p2_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void p2_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// rows in flight per warp (a power of two): 8 for fp32, 4 for 8-byte data
+// (the static shared-memory limit)
+template <class T>
+struct P2Ring {
+  static constexpr int value = sizeof(T) == 4 ? 8 : 4;
+};
+constexpr int P2THREADS = 256;
+
+template <class P>
+__global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __restrict__ x, typename P::T* __restrict__ y,
+                                                       const int4* __restrict__ tiles, int n_tiles, int64_t n_warps,
+                                                       Geo G, StencilPtr st) {
+  using T = typename P::T;
+  using V = typename P::V;
+  constexpr bool REG = sizeof(typename P::W) <= 4;
+  constexpr int P2RING = P2Ring<T>::value;
+  __shared__ T ring_all[P2THREADS / 32][P2RING][4][32];
+  __shared__ typename P::W wslice_all[P2THREADS / 32][REG ? 1 : 46];
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= n_warps) return;  // whole warps leave together
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  T(*ring)[4][32] = ring_all[wid];
+  const int64_t m = warp / n_tiles;
+  const int4 t = tiles[warp - m * n_tiles];
+  const int n = G.n;
+  const int c = t.x - 1 + lane;  // this lane's lattice column
+  const T* __restrict__ xm = x + m * G.S2;
+  T* __restrict__ ym = y + m * G.S2;
+  P2W46<P, REG> W;
+  W.init(st, m * (int64_t)P2W, wslice_all[wid]);
+
+  const int steps = t.z - t.y + 2;  // rows t.y-1 .. t.z
+  // row cursors (32-bit offsets inside the macro block): vertex row r at
+  // r(n+2) - r(r+1)/2 with n+1-r entries, edge row r at r n - r(r-1)/2 with
+  // n-r entries; row -1 is empty and its successor starts at 0
+  struct Cur {
+    int ov, lv, oe, le;
+    __device__ __forceinline__ void init(int n, int r) {
+      ov = r * (n + 2) - (r * (r + 1)) / 2;
+      lv = n + 1 - r;
+      oe = r * n - (r * (r - 1)) / 2;
+      le = n - r;
+    }
+    __device__ __forceinline__ void next() {
+      ov += lv;
+      lv -= 1;
+      oe += le;
+      le -= 1;
+    }
+  };
+  const int se = (int)G.Se, sv = (int)G.Sv;
+  Cur cs;  // next row to stage
+  cs.init(n, t.y - 1);
+  int rs = t.y - 1;
+  auto stage = [&](int slot) {
+    if (rs >= 0) {
+      if (c >= 0 && c < cs.lv) p2_cp_async(&ring[slot][0][lane], xm + cs.ov + c, sizeof(T));
+      if (c >= 0 && c < cs.le) {
+        const T* e0 = xm + sv + cs.oe + c;
+        p2_cp_async(&ring[slot][1][lane], e0, sizeof(T));
+        p2_cp_async(&ring[slot][2][lane], e0 + se, sizeof(T));
+        p2_cp_async(&ring[slot][3][lane], e0 + 2 * se, sizeof(T));
+      }
+    }
+    ++rs;
+    cs.next();
+  };
+#pragma unroll
+  for (int k = 0; k < P2RING; ++k) {
+    if (k < steps) stage(k);
+    p2_commit();
+  }
+  Cur cr;  // row being consumed
+  cr.init(n, t.y - 1);
+  int rc = t.y - 1;
+  auto take = [&](int k) -> P2Row<P> {
+    p2_wait<P2RING - 1>();
+    const int slot = k & (P2RING - 1);
+    const bool okv = rc >= 0 && c >= 0 && c < cr.lv, oke = rc >= 0 && c >= 0 && c < cr.le;
+    const V v = okv ? P::conv(ring[slot][0][lane]) : P::zero();
+    const V ex = oke ? P::conv(ring[slot][1][lane]) : P::zero();
+    const V ey = oke ? P::conv(ring[slot][2][lane]) : P::zero();
+    const V ed = oke ? P::conv(ring[slot][3][lane]) : P::zero();
+    if (k + P2RING < steps) stage(slot);
+    p2_commit();
+    ++rc;
+    cr.next();
+    return make_p2row<P>(v, ex, ey, ed);
+  };
+  const bool writer = lane >= 1 && lane <= 30;
+  int yo = t.y;  // output row
+  Cur co;
+  co.init(n, t.y);
+  auto step = [&](const P2Row<P>& lo, const P2Row<P>& ce, const P2Row<P>& hi) {
+    const int cx = c;
+    // vertex row (NBV order)
+    if (writer && cx >= 1 && yo >= 1 && cx + yo <= n - 1) {
+      typename P::Acc1 a;
+      P::first1(a, W[0], ce.vc);
+      P::add1(a, W[1], ce.ve);
+      P::add1(a, W[2], ce.vw);
+      P::add1(a, W[3], hi.vc);
+      P::add1(a, W[4], lo.vc);
+      P::add1(a, W[5], lo.ve);
+      P::add1(a, W[6], hi.vw);
+      P::add1(a, W[7], ce.xc);
+      P::add1(a, W[8], ce.xw);
+      P::add1(a, W[9], lo.xc);
+      P::add1(a, W[10], hi.xw);
+      P::add1(a, W[11], ce.yc);
+      P::add1(a, W[12], lo.yc);
+      P::add1(a, W[13], ce.yw);
+      P::add1(a, W[14], lo.ye);
+      P::add1(a, W[15], ce.dc);
+      P::add1(a, W[16], ce.dw);
+      P::add1(a, W[17], lo.dc);
+      P::add1(a, W[18], lo.dw);
+      ym[co.ov + cx] = P::finish1(a);
+    }
+    if (writer && cx + yo <= n - 1) {
+      T* e0 = ym + sv + co.oe + cx;
+      if (yo >= 1) {  // X (NBX order)
+        typename P::Acc1 a;
+        P::first1(a, W[19], ce.vc);
+        P::add1(a, W[20], ce.ve);
+        P::add1(a, W[21], hi.vc);
+        P::add1(a, W[22], lo.ve);
+        P::add1(a, W[23], ce.xc);
+        P::add1(a, W[24], ce.yc);
+        P::add1(a, W[25], lo.ye);
+        P::add1(a, W[26], ce.dc);
+        P::add1(a, W[27], lo.dc);
+        e0[0] = P::finish1(a);
+      }
+      if (cx >= 1) {  // Y (NBY order)
+        typename P::Acc1 a;
+        P::first1(a, W[28], ce.vc);
+        P::add1(a, W[29], hi.vc);
+        P::add1(a, W[30], ce.ve);
+        P::add1(a, W[31], hi.vw);
+        P::add1(a, W[32], ce.yc);
+        P::add1(a, W[33], ce.xc);
+        P::add1(a, W[34], hi.xw);
+        P::add1(a, W[35], ce.dc);
+        P::add1(a, W[36], ce.dw);
+        e0[se] = P::finish1(a);
+      }
+      if (cx + yo <= n - 2) {  // XY (NBD order)
+        typename P::Acc1 a;
+        P::first1(a, W[37], ce.ve);
+        P::add1(a, W[38], hi.vc);
+        P::add1(a, W[39], ce.vc);
+        P::add1(a, W[40], hi.ve);
+        P::add1(a, W[41], ce.dc);
+        P::add1(a, W[42], ce.xc);
+        P::add1(a, W[43], hi.xc);
+        P::add1(a, W[44], ce.yc);
+        P::add1(a, W[45], ce.ye);
+        e0[2 * se] = P::finish1(a);
+      }
+    }
+    ++yo;
+    co.next();
+  };
+  P2Row<P> r0 = take(0);
+  P2Row<P> r1 = take(1);
+  P2Row<P> r2;
+  for (int k = 2; k < steps; k += 3) {
+    r2 = take(k);
+    step(r0, r1, r2);
+    if (k + 1 >= steps) break;
+    r0 = take(k + 1);
+    step(r1, r2, r0);
+    if (k + 2 >= steps) break;
+    r1 = take(k + 2);
+    step(r2, r0, r1);
+  }
+  p2_wait<0>();
 }
 
 // Edge DoFs on coarse edges: sum the copies' partial rows in ascending macro
@@ -182,11 +449,19 @@ cudaError_t launch_t(const Mesh& m, const LevelDev& L, const void* x, void* y, c
   G.Se = p2_edge_slots(L.level);
   G.S2 = G.Sv + 3 * G.Se;
   StencilPtr st{L.p2_st64, L.p2_st32, L.p2_hi, L.p2_lo};
-  *what = "P2 apply kernel";
-  const dim3 grid((unsigned)((L.n + 1 + 127) / 128), (unsigned)(L.n + 1), (unsigned)m.n_cells);
-  k_p2_apply<P><<<grid, 128, 0, s>>>((const T*)x, (T*)y, G, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  *what = "P2 row kernel";
+  cudaError_t e = cudaSuccess;
+  if (L.n_p2_tiles > 0) {
+    const int64_t n_warps = (int64_t)L.n_p2_tiles * m.n_cells;
+    const int64_t blocks = (n_warps * 32 + P2THREADS - 1) / P2THREADS;
+    k_p2_rows<P><<<(unsigned)blocks, P2THREADS, 0, s>>>((const T*)x, (T*)y, L.p2_tiles, L.n_p2_tiles, n_warps, G, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  *what = "P2 boundary kernel";
+  const int nb = L.n == 1 ? 3 : 4 * L.n - 2;
+  k_p2_boundary<P><<<dim3((unsigned)((nb + 127) / 128), (unsigned)m.n_cells), 128, 0, s>>>((const T*)x, (T*)y, G, st,
+                                                                                             nb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev_mid && (e = cudaEventRecord(ev_mid, s)) != cudaSuccess) return e;
   *what = "P2 interface kernels";
   if (L.n_items > 0)
