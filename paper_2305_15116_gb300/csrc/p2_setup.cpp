@@ -182,6 +182,22 @@ std::string build_p2_level(Mesh& m, int level, LevelDev& L) {
                  .empty())
           return err;
   }
+  // For the Laplacian a vertex does not couple with the edge opposite to it in
+  // a triangle (integral of (4 lambda_i - 1) lambda_k over T is 4|T|/12 - |T|/3
+  // = 0); the quadrature leaves rounding-sized values there.  Store exact
+  // zeros: in vertex rows the edges X(-1,1), X(0,-1), Y(-1,0), Y(1,-1),
+  // XY(0,0), XY(-1,-1); in edge rows the two vertices off the edge.
+  {
+    const int vz[6] = {9, 10, 13, 14, 15, 18};
+    const int ez[2] = {2, 3};
+    for (int64_t c = 0; c < m.n_cells; ++c) {
+      double* W = &st[size_t(c) * P2W];
+      for (int cls = 0; cls < 8; ++cls)
+        for (int k : vz) W[cls * P2_NV + k] = 0.0;
+      for (int g = 0; g < 6; ++g)
+        for (int k : ez) W[P2_EOFF + g * P2_NE + k] = 0.0;
+    }
+  }
   std::vector<float> st32(st.size()), sth(st.size()), stl(st.size());
   for (size_t i = 0; i < st.size(); ++i) {
     st32[i] = float(st[i]);

@@ -147,9 +147,38 @@ def pin_listing_couplings():
         assert got == expect, tgt
 
 
+def pin_opposite_couplings_vanish():
+    """For the Laplacian a vertex does not couple with the edge opposite to it
+    in a triangle: the integral of (4 lambda_i - 1) lambda_k over T is
+    4|T|/12 - |T|/3 = 0.  In the assembled matrix the vertex row has six and
+    every edge row two rounding-sized entries, at the opposite couplings."""
+    coarse = rect_mesh(3, 2, 0.15, 4)
+    pm = p2.P2Mesh(coarse.coords, coarse.cells, 3, dirichlet=False)
+    K = pm.stiffness().tocoo()
+    scale = np.abs(K.data).max()
+    # (vertex, edge) pairs that share a triangle with the edge opposite the vertex
+    opp = set()
+    for tv, te in zip(pm.tri_vertices.tolist(), pm.tri_edges.tolist()):
+        for v, e in zip(tv, (te[1], te[2], te[0])):  # e12 opposite v0, e02 opposite v1, e01 opposite v2
+            opp.add((v, e))
+    inc = set()
+    for tv, te in zip(pm.tri_vertices.tolist(), pm.tri_edges.tolist()):
+        for v in tv:
+            for e, ends in zip(te, ((tv[0], tv[1]), (tv[1], tv[2]), (tv[0], tv[2]))):
+                if v in ends:
+                    inc.add((v, e))
+    only_opp = opp - inc
+    assert only_opp
+    vals = {(int(r), int(c)): v for r, c, v in zip(K.row, K.col, K.data)}
+    for v, e in only_opp:
+        assert abs(vals[(v, e)]) <= 1e-14 * scale
+        assert abs(vals[(e, v)]) <= 1e-14 * scale
+
+
 ALL_PINS = [("reference_element", pin_reference_element), ("quadratic_energy", pin_quadratic_energy),
             ("pde_consistency", pin_pde_consistency), ("row_structure", pin_row_structure),
-            ("counts", pin_counts), ("listing_couplings", pin_listing_couplings)]
+            ("counts", pin_counts), ("listing_couplings", pin_listing_couplings),
+            ("opposite_couplings_vanish", pin_opposite_couplings_vanish)]
 
 
 @pytest.mark.parametrize("name,check", ALL_PINS, ids=[n for n, _ in ALL_PINS])
