@@ -43,6 +43,10 @@ struct LevelDev {
   // interface work list: int4 (prim, b, a0, a1)
   int4* items = nullptr;
   int n_items = 0;
+  // 3D row-kernel work list: int4 (x0, y0, y1, z): lattice columns x0-1..x0+30
+  // (x0..x0+29 written), rows y0..y1-1 of slice z of one macro
+  int4* r3_tiles = nullptr;
+  int n_r3_tiles = 0;
   // 3D slab work list (levels with n <= 64): int4 (macro, z0, z1, 0)
   int4* slabs = nullptr;
   int n_slabs = 0;
@@ -220,11 +224,10 @@ cudaError_t mg_solve(Mesh& m, int level, int mode, const double* b, double* u, d
 // dtype: 1 = f64 (float-float arithmetic), 2 = f32, 3 = f64 native.
 cudaError_t launch_interior2d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y,
                               cudaStream_t s);
-cudaError_t launch_interior3d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y,
-                              cudaStream_t s);
 cudaError_t launch_interface(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,
                              void* y, cudaStream_t s);
 cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, cudaStream_t s);
+cudaError_t launch_row3d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y, cudaStream_t s);
 cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,
                                     void* y, cudaStream_t s);
 

@@ -217,11 +217,13 @@ cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, voi
                          cudaEvent_t ev_mid, const char** what) {
   const LevelDev& L = m.levels[level];
   cudaError_t e;
-  const bool slab = m.dim == 3 && L.n_slabs > 0;
-  *what = slab ? "3D slab kernel" : "interior kernel";
-  e = slab ? launch_slab3d(dtype, L, x, y, s)
-           : (m.dim == 2 ? launch_interior2d(dtype, L, m.n_cells, x, y, s)
-                         : launch_interior3d(dtype, L, m.n_cells, x, y, s));
+  // 3D: the slab kernel (n <= 64: whole slices in shared memory) or the row
+  // kernel (larger levels) writes every slot, partial rows at macro
+  // boundaries included; the interface step then reduces the copies
+  const bool slab = m.dim == 3;
+  *what = slab ? "3D kernel" : "interior kernel";
+  e = m.dim == 2 ? launch_interior2d(dtype, L, m.n_cells, x, y, s)
+                 : (L.n_slabs > 0 ? launch_slab3d(dtype, L, x, y, s) : launch_row3d(dtype, L, m.n_cells, x, y, s));
   if (e != cudaSuccess) return e;
   if (ev_mid) {
     *what = "cudaEventRecord";

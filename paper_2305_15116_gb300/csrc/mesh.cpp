@@ -298,6 +298,7 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.tiles);
   dev_free(m, L.items);
   dev_free(m, L.slabs);
+  dev_free(m, L.r3_tiles);
   dev_free(m, L.p2_st64);
   dev_free(m, L.p2_st32);
   dev_free(m, L.p2_hi);
@@ -399,22 +400,15 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
     stl[i] = float(st[i] - double(sth[i]));
   }
 
-  // ---- macro-interior work list: strips of columns x chunks of rows ----
-  // 2D: a warp loads 64 consecutive columns and writes the 62 inner ones;
-  // 3D (row kernel of the larger levels): 32 columns, 30 written.
-  constexpr int TW2 = 62, TW = 30, TH = 64;
+  // ---- 2D macro-interior work list: strips of columns x chunks of rows ----
+  // a warp loads 64 consecutive columns and writes the 62 inner ones
+  constexpr int TW2 = 62, TH = 64;
   std::vector<int4> tiles;
   if (d == 2) {
     for (int x0 = 1; x0 <= n - 2; x0 += TW2) {
       const int ymax = n - 1 - x0;
       for (int y0 = 1; y0 <= ymax; y0 += TH) tiles.push_back(make_int4(x0, y0, std::min(y0 + TH, ymax + 1), 0));
     }
-  } else {
-    for (int z = 1; z <= n - 3; ++z)
-      for (int x0 = 1; x0 <= n - 2 - z; x0 += TW) {
-        const int ymax = n - 1 - z - x0;
-        for (int y0 = 1; y0 <= ymax; y0 += TH) tiles.push_back(make_int4(x0, y0, std::min(y0 + TH, ymax + 1), z));
-      }
   }
   // rows of neighbouring strips run side by side, so halo rows hit in L2
   std::stable_sort(tiles.begin(), tiles.end(), [](const int4& a, const int4& b) {
@@ -469,6 +463,17 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   if (!(err = upload(m, &L.tiles, tiles)).empty()) return err;
   if (!(err = upload(m, &L.items, items)).empty()) return err;
   if (!(err = upload(m, &L.slabs, slabs)).empty()) return err;
+  if (d == 3) {
+    // row-kernel tiles: every slice z, strips of 30 columns, chunks of 64 rows
+    std::vector<int4> r3;
+    for (int z = 0; z <= n; ++z) {
+      const int M = n + 1 - z;
+      for (int x0 = 0; x0 <= M - 1; x0 += 30)
+        for (int y0 = 0; y0 <= M - 1 - x0; y0 += 64) r3.push_back(make_int4(x0, y0, std::min(y0 + 64, M - x0), z));
+    }
+    L.n_r3_tiles = int(r3.size());
+    if (!(err = upload(m, &L.r3_tiles, r3)).empty()) return err;
+  }
   if (d == 2) return build_p2_level(m, level, L);
   return "";
 }
