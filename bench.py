@@ -165,13 +165,13 @@ def setup(name, device, dtype_code, level=None):
     ys = torch.empty_like(xs)
     n = 1 << L
     interior = coarse.n_cells * ((n - 1) * (n - 2) // 2 if coarse.dim == 2 else (n - 1) * (n - 2) * (n - 3) // 6)
-    slab = coarse.dim == 3 and n <= 64  # the 3D slab kernel writes every slot
+    slab = True  # every apply kernel writes every slot (interface copies included)
     if p2:
         kernel = "k_p2_apply"
         raw = lambda l, c, xp, yp, sp: M.p2_apply_timed(l, c, xp, yp, sp, 0, 0, 0)
         timed = M.p2_apply_timed
     else:
-        kernel = "k_slab3d" if slab else ("k_interior2d" if coarse.dim == 2 else "k_interior3d")
+        kernel = "k_interior2d" if coarse.dim == 2 else ("k_slab3d" if n <= 64 else "k_row3d")
         raw, timed = M.apply_raw, M.apply_timed
     return dict(M=M, L=L, ns=ns, ng=ng, xs=xs, ys=ys, smap=smap, x_global=x, coarse=coarse,
                 interior=interior, elem=4 if dtype_code == H.F32 else 8, code=dtype_code,
@@ -215,9 +215,8 @@ def timed_applies(w, steps, warmup, stream, barrier=None):
 
 def interior_bytes(w):
     """Algorithmic bytes of one launch of the dominant kernel: every slot of
-    every macro is read once (interior points and the macro-boundary halo);
-    every interior point is written once (2D and row kernels), or every slot
-    (the 3D slab kernel and the P2 kernel, which also write the
+    every macro is read once and written once (the 2D apply writes its
+    interface points in the same launch, the 3D and P2 kernels write the
     macro-boundary partials)."""
     return w["elem"] * (w["ns"] + (w["ns"] if w["slab"] else w["interior"]))
 

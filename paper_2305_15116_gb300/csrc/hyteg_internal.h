@@ -222,10 +222,7 @@ cudaError_t mg_solve(Mesh& m, int level, int mode, const double* b, double* u, d
 
 // ---- kernels ----------------------------------------------------------------
 // dtype: 1 = f64 (float-float arithmetic), 2 = f32, 3 = f64 native.
-cudaError_t launch_interior2d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y,
-                              cudaStream_t s);
-cudaError_t launch_interface(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,
-                             void* y, cudaStream_t s);
+cudaError_t launch_apply2d(int dtype, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s);
 cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, cudaStream_t s);
 cudaError_t launch_row3d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y, cudaStream_t s);
 cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,

@@ -1,14 +1,15 @@
-// Interface step: completes the DoFs on macro vertices, edges and (3D) faces.
+// Interface step of the 3D apply: completes the DoFs on macro vertices,
+// edges and faces.
 //
-// The macro-interior kernels update only points strictly inside a macro; the
-// paper hands the points on the macro boundary to separate "interface
+// The paper hands the points on the macro boundary to separate "interface
 // primitives" (Sec. 4.1).  Here every copy of such a point in an incident
-// macro contributes its PARTIAL row: the stencil restricted to the
-// micro-elements of that macro (precomputed per macro and boundary class).
-// The partials of all incident macros are summed in ascending macro order —
-// a fixed order, so the result is deterministic — and the sum is written to
-// every copy.  In exact arithmetic the sum is the assembled matrix row.
-// Points on the domain boundary get the Dirichlet identity row: y = x.
+// macro holds its macro's PARTIAL row (the stencil restricted to the
+// micro-elements of that macro, written by the 3D kernels); the partials of
+// all incident macros are summed in ascending macro order — a fixed order,
+// so the result is deterministic — and the sum is written to every copy.  In
+// exact arithmetic the sum is the assembled matrix row.  Points on the
+// domain boundary get the Dirichlet identity row: y = x.  (2D computes its
+// interface points inside the apply launch, interior2d.cu.)
 //
 // Work list: one block per item (primitive, row b, points a0..a1-1) of at most
 // 128 points; a vertex item has one point.
@@ -19,11 +20,6 @@ namespace hyteg {
 
 namespace {
 
-__constant__ int c_off2[NW2][2] = {{0, -1}, {1, -1}, {-1, 0}, {0, 0}, {1, 0}, {-1, 1}, {0, 1}};
-__constant__ int c_off3[NW3][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
-                                   {1, -1, 0}, {-1, 1, 0}, {0, 0, 1},  {-1, 0, 1}, {0, -1, 1},
-                                   {1, -1, 1}, {0, 0, -1}, {1, 0, -1}, {0, 1, -1}, {-1, 1, -1}};
-
 __device__ __forceinline__ int64_t tri_slot(int n, int x, int y) {
   return (int64_t)y * (n + 2) - ((int64_t)y * (y + 1)) / 2 + x;
 }
@@ -31,104 +27,6 @@ __device__ __forceinline__ int64_t tet_slot(int n, int x, int y, int z) {
   const int64_t N = n + 1, b = N - z;
   const int64_t zs = N * (N + 1) * (N + 2) / 6 - b * (b + 1) * (b + 2) / 6;
   return zs + (int64_t)y * b - ((int64_t)y * (y - 1)) / 2 + x;
-}
-
-template <class T>
-__device__ __forceinline__ T wload(const StencilPtr& st, int64_t i);
-template <>
-__device__ __forceinline__ double wload<double>(const StencilPtr& st, int64_t i) { return __ldg(st.d + i); }
-template <>
-__device__ __forceinline__ float wload<float>(const StencilPtr& st, int64_t i) { return __ldg(st.f + i); }
-
-template <class T>
-__device__ __forceinline__ T tfma(T a, T b, T c);
-template <>
-__device__ __forceinline__ double tfma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
-template <>
-__device__ __forceinline__ float tfma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-
-template <class T, int DIM>
-__global__ void __launch_bounds__(128) k_interface(const T* __restrict__ x, T* __restrict__ y,
-                                                   const int4* __restrict__ items, const Prim* __restrict__ prims,
-                                                   const Inc* __restrict__ incs, int n, int64_t S,
-                                                   StencilPtr st) {
-  const int4 it = items[blockIdx.x];
-  const int a = it.z + threadIdx.x;
-  if (a >= it.w) return;
-  const Prim p = prims[it.x];
-  const int b = it.y;
-  // weights of the point on the primitive's canonical vertices
-  int wv[3] = {0, 0, 0};
-  if (p.type == 0) {
-    wv[0] = n;
-  } else if (p.type == 1) {
-    wv[0] = n - a;
-    wv[1] = a;
-  } else {
-    wv[0] = n - a - b;
-    wv[1] = a;
-    wv[2] = b;
-  }
-  const int nverts = p.type + 1;
-  constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
-  constexpr int NW = DIM == 2 ? NW2 : NW3;
-
-  T acc = T(0);
-  int64_t first_slot = -1;
-  for (int i = 0; i < p.inc_count; ++i) {
-    const Inc inc = incs[p.inc_begin + i];
-    int q[3] = {0, 0, 0};  // local index point in this cell
-    for (int j = 0; j < nverts; ++j) {
-      const int c = inc.corner[j];
-      if (c >= 1) q[c - 1] += wv[j];
-    }
-    const int64_t base = (int64_t)inc.cell * S;
-    int cls;
-    if (DIM == 2) {
-      cls = (q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[0] + q[1] == n ? 4 : 0);
-    } else {
-      cls = (q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[2] == 0 ? 4 : 0) | (q[0] + q[1] + q[2] == n ? 8 : 0);
-    }
-    if (i == 0) first_slot = base + (DIM == 2 ? tri_slot(n, q[0], q[1]) : tet_slot(n, q[0], q[1], q[2]));
-    if (p.boundary) continue;
-    const int64_t wb = ((int64_t)inc.cell * NCLS + cls) * NW;
-    T part = T(0);
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      int dx, dy, dz = 0;
-      if (DIM == 2) {
-        dx = c_off2[k][0];
-        dy = c_off2[k][1];
-      } else {
-        dx = c_off3[k][0];
-        dy = c_off3[k][1];
-        dz = c_off3[k][2];
-      }
-      bool in = !((cls & 1) && dx < 0) && !((cls & 2) && dy < 0);
-      if (DIM == 2) {
-        in = in && !((cls & 4) && dx + dy > 0);
-      } else {
-        in = in && !((cls & 4) && dz < 0) && !((cls & 8) && dx + dy + dz > 0);
-      }
-      if (!in) continue;
-      const int64_t s = base + (DIM == 2 ? tri_slot(n, q[0] + dx, q[1] + dy)
-                                         : tet_slot(n, q[0] + dx, q[1] + dy, q[2] + dz));
-      part = tfma<T>(wload<T>(st, wb + k), __ldg(x + s), part);
-    }
-    acc += part;
-  }
-  if (p.boundary) acc = __ldg(x + first_slot);
-  // write the completed value into every copy
-  for (int i = 0; i < p.inc_count; ++i) {
-    const Inc inc = incs[p.inc_begin + i];
-    int q[3] = {0, 0, 0};
-    for (int j = 0; j < nverts; ++j) {
-      const int c = inc.corner[j];
-      if (c >= 1) q[c - 1] += wv[j];
-    }
-    const int64_t base = (int64_t)inc.cell * S;
-    y[base + (DIM == 2 ? tri_slot(n, q[0], q[1]) : tet_slot(n, q[0], q[1], q[2]))] = acc;
-  }
 }
 
 // Reduce variant: the copies already hold their macro's partial row (written
@@ -177,19 +75,6 @@ __global__ void __launch_bounds__(128) k_interface_reduce(const T* __restrict__ 
 }
 
 template <class T>
-cudaError_t launch_t(int dim, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
-  if (L.n_items == 0) return cudaSuccess;
-  StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
-  if (dim == 2)
-    k_interface<T, 2><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, m.d_incs, L.n,
-                                                 L.slots_per_macro, st);
-  else
-    k_interface<T, 3><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, m.d_incs, L.n,
-                                                 L.slots_per_macro, st);
-  return cudaGetLastError();
-}
-
-template <class T>
 cudaError_t launch_reduce_t(int dim, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
   if (L.n_items == 0) return cudaSuccess;
   if (dim == 2)
@@ -217,31 +102,30 @@ cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, voi
                          cudaEvent_t ev_mid, const char** what) {
   const LevelDev& L = m.levels[level];
   cudaError_t e;
+  if (m.dim == 2) {
+    // one launch: macro-interior tiles and interface points side by side
+    *what = "2D apply kernel";
+    e = launch_apply2d(dtype, m, L, x, y, s);
+    if (e != cudaSuccess) return e;
+    if (ev_mid) {
+      *what = "cudaEventRecord";
+      e = cudaEventRecord(ev_mid, s);
+    }
+    return e;
+  }
   // 3D: the slab kernel (n <= 64: whole slices in shared memory) or the row
   // kernel (larger levels) writes every slot, partial rows at macro
   // boundaries included; the interface step then reduces the copies
-  const bool slab = m.dim == 3;
-  *what = slab ? "3D kernel" : "interior kernel";
-  e = m.dim == 2 ? launch_interior2d(dtype, L, m.n_cells, x, y, s)
-                 : (L.n_slabs > 0 ? launch_slab3d(dtype, L, x, y, s) : launch_row3d(dtype, L, m.n_cells, x, y, s));
+  *what = "3D kernel";
+  e = L.n_slabs > 0 ? launch_slab3d(dtype, L, x, y, s) : launch_row3d(dtype, L, m.n_cells, x, y, s);
   if (e != cudaSuccess) return e;
   if (ev_mid) {
     *what = "cudaEventRecord";
     e = cudaEventRecord(ev_mid, s);
     if (e != cudaSuccess) return e;
   }
-  *what = slab ? "interface reduce kernel" : "interface kernel";
-  return slab ? launch_interface_reduce(dtype, m.dim, m, L, x, y, s) : launch_interface(dtype, m.dim, m, L, x, y, s);
-}
-
-cudaError_t launch_interface(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x, void* y,
-                             cudaStream_t s) {
-  switch (dtype) {
-    case 1:
-    case 3: return launch_t<double>(dim, m, L, x, y, s);
-    case 2: return launch_t<float>(dim, m, L, x, y, s);
-    default: return cudaErrorInvalidValue;
-  }
+  *what = "interface reduce kernel";
+  return launch_interface_reduce(dtype, m.dim, m, L, x, y, s);
 }
 
 }  // namespace hyteg

@@ -8,7 +8,9 @@
 // row-major with x contiguous; row r starts at r(n+2) - r(r+1)/2 and holds
 // n+1-r points (Sec. 3).
 //
-// GPU mapping: one warp per tile of 64 consecutive columns and up to 64 rows.
+// GPU mapping: one warp per tile of 64 consecutive columns and up to 64 rows;
+// the same launch also completes the points on macro vertices and edges (the
+// interface step, stencil mode), in blocks of their own.
 // Each lane owns two adjacent columns, so it evaluates two points per row and
 // the float-float arithmetic of the pair runs on packed f32x2 instructions.
 // Each lane stages its two columns of the next RING rows in shared memory with
@@ -66,6 +68,64 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// ---- interface points (coarse vertices and edges), stencil mode ------------
+// Each macro holding a copy contributes its partial row (the class stencil of
+// the point in that macro: only the macro's own micro-triangles); the partials
+// are summed in ascending macro order and the sum is written to every copy.
+// Dirichlet points get y = x.  Arithmetic in the element type (fp64 for the
+// float-float apply).
+__constant__ int c_if_off[NW2][2] = {{0, -1}, {1, -1}, {-1, 0}, {0, 0}, {1, 0}, {-1, 1}, {0, 1}};
+
+__device__ __forceinline__ int64_t if_slot(int n, int x, int y) {
+  return (int64_t)y * (n + 2) - ((int64_t)y * (y + 1)) / 2 + x;
+}
+__device__ __forceinline__ double if_w(const StencilPtr& st, int64_t i, double) { return __ldg(st.d + i); }
+__device__ __forceinline__ float if_w(const StencilPtr& st, int64_t i, float) { return __ldg(st.f + i); }
+__device__ __forceinline__ double if_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float if_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <class T>
+__device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __restrict__ y, const int4& it, int a,
+                                              const Prim* __restrict__ prims, const Inc* __restrict__ incs, int n,
+                                              int64_t S, const StencilPtr& st) {
+  const Prim p = prims[it.x];
+  const int wv0 = p.type == 0 ? n : n - a, wv1 = p.type == 0 ? 0 : a;  // weights on the canonical vertices
+  auto local = [&](const Inc& inc, int q[2]) {
+    q[0] = q[1] = 0;
+    if (inc.corner[0] >= 1) q[inc.corner[0] - 1] += wv0;
+    if (p.type == 1 && inc.corner[1] >= 1) q[inc.corner[1] - 1] += wv1;
+  };
+  T acc = T(0);
+  if (p.boundary) {
+    int q[2];
+    local(incs[p.inc_begin], q);
+    acc = __ldg(x + (int64_t)incs[p.inc_begin].cell * S + if_slot(n, q[0], q[1]));
+  } else {
+    for (int i = 0; i < p.inc_count; ++i) {
+      const Inc inc = incs[p.inc_begin + i];
+      int q[2];
+      local(inc, q);
+      const int cls = (q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[0] + q[1] == n ? 4 : 0);
+      const int64_t base = (int64_t)inc.cell * S;
+      const int64_t wb = ((int64_t)inc.cell * NCLS2 + cls) * NW2;
+      T part = T(0);
+#pragma unroll
+      for (int k = 0; k < NW2; ++k) {
+        const int dx = c_if_off[k][0], dy = c_if_off[k][1];
+        if (((cls & 1) && dx < 0) || ((cls & 2) && dy < 0) || ((cls & 4) && dx + dy > 0)) continue;
+        part = if_fma(if_w(st, wb + k, T(0)), __ldg(x + base + if_slot(n, q[0] + dx, q[1] + dy)), part);
+      }
+      acc += part;
+    }
+  }
+  for (int i = 0; i < p.inc_count; ++i) {
+    const Inc inc = incs[p.inc_begin + i];
+    int q[2];
+    local(inc, q);
+    y[(int64_t)inc.cell * S + if_slot(n, q[0], q[1])] = acc;
+  }
+}
+
 // Rows in flight per warp: each lane stages its two columns of the next RING
 // rows in shared memory with cp.async, so a warp keeps RING rows outstanding
 // without holding them in registers.
@@ -73,14 +133,29 @@ constexpr int RING = 8;  // a power of two
 static_assert((RING & (RING - 1)) == 0, "RING must be a power of two");
 constexpr int THREADS2D = 256;
 
+// One launch does the whole apply: blocks 0 .. n_if_blocks-1 take the
+// interface items (two items of up to 128 points per block), the others the
+// macro-interior tiles.  The two parts write disjoint slots and read only x,
+// so they run side by side.
 template <class P>
 __global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* __restrict__ x,
                                                           typename P::T* __restrict__ y,
                                                           const int4* __restrict__ tiles, int n_tiles,
-                                                          int64_t n_warps, int64_t S, int n, StencilPtr st) {
+                                                          int64_t n_warps, int64_t S, int n, StencilPtr st,
+                                                          const int4* __restrict__ items, int n_items,
+                                                          const Prim* __restrict__ prims,
+                                                          const Inc* __restrict__ incs, int n_if_blocks) {
   using T = typename P::T;
   __shared__ T ring_all[THREADS2D / 32][RING][32][2];
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if ((int)blockIdx.x < n_if_blocks) {
+    const int item = 2 * (int)blockIdx.x + (int)(threadIdx.x >> 7);
+    if (item >= n_items) return;
+    const int4 it = items[item];
+    const int a = it.z + (int)(threadIdx.x & 127);
+    if (a < it.w) iface2d_point<T>(x, y, it, a, prims, incs, n, S, st);
+    return;
+  }
+  const int64_t warp = ((int64_t)(blockIdx.x - n_if_blocks) * blockDim.x + threadIdx.x) >> 5;
   if (warp >= n_warps) return;  // whole warps leave together
   const int lane = threadIdx.x & 31;
   T(*ring)[32][2] = ring_all[threadIdx.x >> 5];
@@ -159,25 +234,26 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* _
 }
 
 template <class P>
-cudaError_t launch(const LevelDev& L, int64_t n_cells, const void* x, void* y, cudaStream_t s) {
-  if (L.n_tiles == 0) return cudaSuccess;
-  const int64_t n_warps = (int64_t)L.n_tiles * n_cells;
+cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
+  const int64_t n_warps = (int64_t)L.n_tiles * m.n_cells;
   const int threads = THREADS2D;
-  const int64_t blocks = (n_warps * 32 + threads - 1) / threads;
+  const int64_t int_blocks = (n_warps * 32 + threads - 1) / threads;
+  const int if_blocks = (L.n_items + 1) / 2;
+  if (int_blocks + if_blocks == 0) return cudaSuccess;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
-  k_interior2d<P><<<(unsigned)blocks, threads, 0, s>>>((const typename P::T*)x, (typename P::T*)y, L.tiles,
-                                                       L.n_tiles, n_warps, L.slots_per_macro, L.n, st);
+  k_interior2d<P><<<(unsigned)(int_blocks + if_blocks), threads, 0, s>>>(
+      (const typename P::T*)x, (typename P::T*)y, L.tiles, L.n_tiles > 0 ? L.n_tiles : 1, n_warps,
+      L.slots_per_macro, L.n, st, L.items, L.n_items, m.d_prims, m.d_incs, if_blocks);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_interior2d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y,
-                              cudaStream_t s) {
+cudaError_t launch_apply2d(int dtype, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
   switch (dtype) {
-    case 1: return launch<ArF64FF>(L, n_cells, x, y, s);
-    case 2: return launch<ArF32>(L, n_cells, x, y, s);
-    case 3: return launch<ArF64Native>(L, n_cells, x, y, s);
+    case 1: return launch<ArF64FF>(m, L, x, y, s);
+    case 2: return launch<ArF32>(m, L, x, y, s);
+    case 3: return launch<ArF64Native>(m, L, x, y, s);
     default: return cudaErrorInvalidValue;
   }
 }
