@@ -223,6 +223,11 @@ cudaError_t mg_solve(Mesh& m, int level, int mode, const double* b, double* u, d
 // ---- kernels ----------------------------------------------------------------
 // dtype: 1 = f64 (float-float arithmetic), 2 = f32, 3 = f64 native.
 cudaError_t launch_apply2d(int dtype, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s);
+// 2D fused sweeps over u: out = u + omega dinv (b - A u) (jacobi) or
+// out = b - A u; out must not overlap u.  dtype 1 (float64, float-float
+// apply) or 2 (fp32).
+cudaError_t launch_sweep2d(int dtype, bool jacobi, const Mesh& m, const LevelDev& L, const void* u, const void* b,
+                           const void* dinv, double omega, void* out, cudaStream_t s);
 cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, cudaStream_t s);
 cudaError_t launch_row3d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y, cudaStream_t s);
 cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,

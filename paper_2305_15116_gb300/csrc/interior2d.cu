@@ -34,13 +34,18 @@ namespace {
 template <class P>
 struct Row {
   typename P::P2 v, e, w;
+  typename P::T b[2], d[2];  // b and inverse diagonal of the lane's two points (sweep modes)
 };
 
 template <class P>
 __device__ __forceinline__ Row<P> make_row(typename P::V a, typename P::V b) {
   const typename P::V right_of_b = P::down(a);  // column c + 2: A of the next lane
   const typename P::V left_of_a = P::up(b);     // column c - 1: B of the previous lane
-  return Row<P>{P::pair(a, b), P::pair(b, right_of_b), P::pair(left_of_a, a)};
+  Row<P> r;
+  r.v = P::pair(a, b);
+  r.e = P::pair(b, right_of_b);
+  r.w = P::pair(left_of_a, a);
+  return r;
 }
 
 // Row-walking cursor: offset of row r inside the macro array and its length.
@@ -68,6 +73,37 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// What a launch writes at a point with (A u) = au:
+//   MODE_APPLY:    y = A u
+//   MODE_JACOBI:   y = u + omega dinv (b - A u)   (one weighted Jacobi sweep)
+//   MODE_RESIDUAL: y = b - A u
+// (u = x at the point; b and dinv in the slot layout, copies equal).
+constexpr int MODE_APPLY = 0, MODE_JACOBI = 1, MODE_RESIDUAL = 2;
+
+struct ModeArgs {
+  const void* b;
+  const void* dinv;
+  double omega;
+};
+
+// sweep modes inside the macro: u, b and dinv of the point come from the
+// staged rows
+template <int MODE, class T>
+__device__ __forceinline__ T mode_out_staged(T au, T u, T b, T d, double omega) {
+  if (MODE == MODE_APPLY) return au;
+  if (MODE == MODE_RESIDUAL) return b - au;
+  return u + (T)omega * d * (b - au);
+}
+
+template <int MODE, class T>
+__device__ __forceinline__ T mode_out(T au, const T* __restrict__ x, const ModeArgs& md, int64_t i) {
+  if (MODE == MODE_APPLY) return au;
+  const T bi = __ldg(static_cast<const T*>(md.b) + i);
+  if (MODE == MODE_RESIDUAL) return bi - au;
+  const T ui = __ldg(x + i), di = __ldg(static_cast<const T*>(md.dinv) + i);
+  return ui + (T)md.omega * di * (bi - au);
+}
+
 // ---- interface points (coarse vertices and edges), stencil mode ------------
 // Each macro holding a copy contributes its partial row (the class stencil of
 // the point in that macro: only the macro's own micro-triangles); the partials
@@ -84,10 +120,10 @@ __device__ __forceinline__ float if_w(const StencilPtr& st, int64_t i, float) { 
 __device__ __forceinline__ double if_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float if_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-template <class T>
+template <int MODE, class T>
 __device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __restrict__ y, const int4& it, int a,
                                               const Prim* __restrict__ prims, const Inc* __restrict__ incs, int n,
-                                              int64_t S, const StencilPtr& st) {
+                                              int64_t S, const StencilPtr& st, const ModeArgs& md) {
   const Prim p = prims[it.x];
   const int wv0 = p.type == 0 ? n : n - a, wv1 = p.type == 0 ? 0 : a;  // weights on the canonical vertices
   auto local = [&](const Inc& inc, int q[2]) {
@@ -118,6 +154,11 @@ __device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __rest
       acc += part;
     }
   }
+  if (MODE != MODE_APPLY) {  // copies hold equal u, b and dinv: use the first
+    int q[2];
+    local(incs[p.inc_begin], q);
+    acc = mode_out<MODE>(acc, x, md, (int64_t)incs[p.inc_begin].cell * S + if_slot(n, q[0], q[1]));
+  }
   for (int i = 0; i < p.inc_count; ++i) {
     const Inc inc = incs[p.inc_begin + i];
     int q[2];
@@ -137,34 +178,52 @@ constexpr int THREADS2D = 256;
 // interface items (two items of up to 128 points per block), the others the
 // macro-interior tiles.  The two parts write disjoint slots and read only x,
 // so they run side by side.
-template <class P>
-__global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* __restrict__ x,
+// Threads per block: 256 for the apply; 128 for the sweep modes, whose rows of
+// b and dinv are staged beside x (the static shared-memory limit).
+template <int MODE>
+struct Thr2 {
+  static constexpr int value = MODE == MODE_APPLY ? THREADS2D : 128;
+};
+
+template <class P, int MODE>
+__global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename P::T* __restrict__ x,
                                                           typename P::T* __restrict__ y,
                                                           const int4* __restrict__ tiles, int n_tiles,
                                                           int64_t n_warps, int64_t S, int n, StencilPtr st,
                                                           const int4* __restrict__ items, int n_items,
                                                           const Prim* __restrict__ prims,
-                                                          const Inc* __restrict__ incs, int n_if_blocks) {
+                                                          const Inc* __restrict__ incs, int n_if_blocks,
+                                                          ModeArgs md) {
   using T = typename P::T;
-  __shared__ T ring_all[THREADS2D / 32][RING][32][2];
+  constexpr int THR = Thr2<MODE>::value;
+  constexpr bool SWEEP = MODE != MODE_APPLY;
+  static_assert(!SWEEP || sizeof(T) == 4, "the sweep modes are built for fp32");
+  __shared__ T ring_all[THR / 32][RING][32][2];
+  __shared__ T ringb_all[SWEEP ? THR / 32 : 1][SWEEP ? RING : 1][32][2];
+  __shared__ T ringd_all[MODE == MODE_JACOBI ? THR / 32 : 1][MODE == MODE_JACOBI ? RING : 1][32][2];
   if ((int)blockIdx.x < n_if_blocks) {
-    const int item = 2 * (int)blockIdx.x + (int)(threadIdx.x >> 7);
+    const int item = (THR / 128) * (int)blockIdx.x + (int)(threadIdx.x >> 7);
     if (item >= n_items) return;
     const int4 it = items[item];
     const int a = it.z + (int)(threadIdx.x & 127);
-    if (a < it.w) iface2d_point<T>(x, y, it, a, prims, incs, n, S, st);
+    if (a < it.w) iface2d_point<MODE, T>(x, y, it, a, prims, incs, n, S, st, md);
     return;
   }
   const int64_t warp = ((int64_t)(blockIdx.x - n_if_blocks) * blockDim.x + threadIdx.x) >> 5;
   if (warp >= n_warps) return;  // whole warps leave together
   const int lane = threadIdx.x & 31;
   T(*ring)[32][2] = ring_all[threadIdx.x >> 5];
+  T(*ringb)[32][2] = ringb_all[SWEEP ? threadIdx.x >> 5 : 0];
+  T(*ringd)[32][2] = ringd_all[MODE == MODE_JACOBI ? threadIdx.x >> 5 : 0];
+
   const int64_t m = warp / n_tiles;
   const int4 t = tiles[warp - m * n_tiles];
   const int ca = t.x - 1 + 2 * lane;  // column A; column B = ca + 1
   const int cb = ca + 1;
   const T* __restrict__ xm = x + m * S;
   T* __restrict__ ym = y + m * S;
+  const T* __restrict__ bm = SWEEP ? static_cast<const T*>(md.b) + m * S : nullptr;
+  const T* __restrict__ dm = MODE == MODE_JACOBI ? static_cast<const T*>(md.dinv) + m * S : nullptr;
 
   const int64_t wb = m * (int64_t)(NCLS2 * NW2);  // class 0: the full interior stencil
   const typename P::W wSE = P::weight(st, wb + 1), wC = P::weight(st, wb + 3), wE = P::weight(st, wb + 4),
@@ -175,8 +234,16 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* _
   Cursor is;  // next row to stage
   is.init(n, t.y - 1);
   auto stage = [&](int slot) {
-    if (ca < is.len) cp_async(&ring[slot][lane][0], xm + is.off + ca, sizeof(T));
-    if (cb < is.len) cp_async(&ring[slot][lane][1], xm + is.off + cb, sizeof(T));
+    if (ca < is.len) {
+      cp_async(&ring[slot][lane][0], xm + is.off + ca, sizeof(T));
+      if (SWEEP) cp_async(&ringb[slot][lane][0], bm + is.off + ca, sizeof(T));
+      if (MODE == MODE_JACOBI) cp_async(&ringd[slot][lane][0], dm + is.off + ca, sizeof(T));
+    }
+    if (cb < is.len) {
+      cp_async(&ring[slot][lane][1], xm + is.off + cb, sizeof(T));
+      if (SWEEP) cp_async(&ringb[slot][lane][1], bm + is.off + cb, sizeof(T));
+      if (MODE == MODE_JACOBI) cp_async(&ringd[slot][lane][1], dm + is.off + cb, sizeof(T));
+    }
     is.next();
   };
 #pragma unroll
@@ -189,7 +256,15 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* _
   auto take = [&](int k) -> Row<P> {
     cp_async_wait<RING - 1>();
     const T va = ring[k & (RING - 1)][lane][0], vb = ring[k & (RING - 1)][lane][1];
-    const Row<P> r = make_row<P>(ca < cr.len ? P::conv(va) : P::zero(), cb < cr.len ? P::conv(vb) : P::zero());
+    Row<P> r = make_row<P>(ca < cr.len ? P::conv(va) : P::zero(), cb < cr.len ? P::conv(vb) : P::zero());
+    if (SWEEP) {  // read before the slot is staged again
+      r.b[0] = ringb[k & (RING - 1)][lane][0];
+      r.b[1] = ringb[k & (RING - 1)][lane][1];
+      if (MODE == MODE_JACOBI) {
+        r.d[0] = ringd[k & (RING - 1)][lane][0];
+        r.d[1] = ringd[k & (RING - 1)][lane][1];
+      }
+    }
     // the slot of step k is free again: stage step k + RING
     if (k + RING < steps) stage(k & (RING - 1));
     cp_async_commit();
@@ -210,6 +285,15 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* _
     T outa, outb;
     P::finish(a, outa, outb);
     // point (c, r) is interior when c <= n - 1 - r, i.e. c < len - 1
+    if (SWEEP) {  // the centre values of the row are u (fp32 data)
+      float ua = 0.0f, ub = 0.0f;
+      if constexpr (SWEEP) {
+        ua = ce.v.x;
+        ub = ce.v.y;
+      }
+      outa = mode_out_staged<MODE, T>(outa, (T)ua, ce.b[0], ce.d[0], md.omega);
+      outb = mode_out_staged<MODE, T>(outb, (T)ub, ce.b[1], ce.d[1], md.omega);
+    }
     if (wa && ca < out.len - 1) ym[out.off + ca] = outa;
     if (wbb && cb < out.len - 1) ym[out.off + cb] = outb;
     out.next();
@@ -233,27 +317,39 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d(const typename P::T* _
   cp_async_wait<0>();
 }
 
-template <class P>
-cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
+template <class P, int MODE>
+cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s, const ModeArgs& md) {
   const int64_t n_warps = (int64_t)L.n_tiles * m.n_cells;
-  const int threads = THREADS2D;
+  const int threads = Thr2<MODE>::value;
   const int64_t int_blocks = (n_warps * 32 + threads - 1) / threads;
-  const int if_blocks = (L.n_items + 1) / 2;
+  const int per = threads / 128;  // interface items per block
+  const int if_blocks = (L.n_items + per - 1) / per;
   if (int_blocks + if_blocks == 0) return cudaSuccess;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
-  k_interior2d<P><<<(unsigned)(int_blocks + if_blocks), threads, 0, s>>>(
+  k_interior2d<P, MODE><<<(unsigned)(int_blocks + if_blocks), threads, 0, s>>>(
       (const typename P::T*)x, (typename P::T*)y, L.tiles, L.n_tiles > 0 ? L.n_tiles : 1, n_warps,
-      L.slots_per_macro, L.n, st, L.items, L.n_items, m.d_prims, m.d_incs, if_blocks);
+      L.slots_per_macro, L.n, st, L.items, L.n_items, m.d_prims, m.d_incs, if_blocks, md);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_apply2d(int dtype, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
+  const ModeArgs md{nullptr, nullptr, 0.0};
   switch (dtype) {
-    case 1: return launch<ArF64FF>(m, L, x, y, s);
-    case 2: return launch<ArF32>(m, L, x, y, s);
-    case 3: return launch<ArF64Native>(m, L, x, y, s);
+    case 1: return launch<ArF64FF, MODE_APPLY>(m, L, x, y, s, md);
+    case 2: return launch<ArF32, MODE_APPLY>(m, L, x, y, s, md);
+    case 3: return launch<ArF64Native, MODE_APPLY>(m, L, x, y, s, md);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_sweep2d(int dtype, bool jacobi, const Mesh& m, const LevelDev& L, const void* u, const void* b,
+                           const void* dinv, double omega, void* out, cudaStream_t s) {
+  const ModeArgs md{b, dinv, omega};
+  switch (dtype) {
+    case 2:
+      return jacobi ? launch<ArF32, MODE_JACOBI>(m, L, u, out, s, md) : launch<ArF32, MODE_RESIDUAL>(m, L, u, out, s, md);
     default: return cudaErrorInvalidValue;
   }
 }

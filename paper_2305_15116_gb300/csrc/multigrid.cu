@@ -452,14 +452,36 @@ cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s) {
   T* y = Vecs<T>::y(g);
   T* r = Vecs<T>::r(g);
   const T omega = T(sv.omega);
-  for (int it = 0; it < sv.nu1; ++it) {
+  const LevelDev& L = m.levels[l];
+  // 2D fp32 cycles: every sweep is one fused launch (apply, interface and
+  // Jacobi update together), alternating between u and y; the residual
+  // likewise.  Float64 cycles and 3D apply, then update.
+  constexpr bool fused_ok = sizeof(T) == 4;
+  auto sweeps2d = [&](int count) -> cudaError_t {
+    T* cur = u;
+    T* alt = y;
+    for (int it = 0; it < count; ++it) {
+      HY_TRY(launch_sweep2d(Vecs<T>::dtype, true, m, L, cur, b, Vecs<T>::dinv(g), sv.omega, alt, s));
+      T* t = cur;
+      cur = alt;
+      alt = t;
+    }
+    if (cur != u) HY_TRY(cudaMemcpyAsync(u, cur, sizeof(T) * ns, cudaMemcpyDeviceToDevice, s));
+    return cudaSuccess;
+  };
+  if (m.dim == 2 && fused_ok) {
+    HY_TRY(sweeps2d(sv.nu1));
+    HY_TRY(launch_sweep2d(Vecs<T>::dtype, false, m, L, u, b, Vecs<T>::dinv(g), sv.omega, r, s));
+  } else {
+    for (int it = 0; it < sv.nu1; ++it) {
+      HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
+      k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
+      HY_TRY(cudaGetLastError());
+    }
     HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
-    k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
+    k_residual<T><<<grid_for(ns), THREADS, 0, s>>>(r, b, y, ns);
     HY_TRY(cudaGetLastError());
   }
-  HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
-  k_residual<T><<<grid_for(ns), THREADS, 0, s>>>(r, b, y, ns);
-  HY_TRY(cudaGetLastError());
   MgLevel& gc = sv.lv[l - 1];
   T* bc = Vecs<T>::b(gc);
   T* uc = Vecs<T>::u(gc);
@@ -467,10 +489,14 @@ cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s) {
   HY_TRY(cudaMemsetAsync(uc, 0, sizeof(T) * m.levels[l - 1].slots_per_macro * m.n_cells, s));
   HY_TRY(vcycle_t<T>(m, l - 1, bc, uc, s));
   HY_TRY(prolong_add_t<T>(m, l, uc, u, s));
-  for (int it = 0; it < sv.nu2; ++it) {
-    HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
-    k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
-    HY_TRY(cudaGetLastError());
+  if (m.dim == 2 && fused_ok) {
+    HY_TRY(sweeps2d(sv.nu2));
+  } else {
+    for (int it = 0; it < sv.nu2; ++it) {
+      HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
+      k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
+      HY_TRY(cudaGetLastError());
+    }
   }
   return cudaSuccess;
 }
