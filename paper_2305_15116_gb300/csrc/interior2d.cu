@@ -34,7 +34,7 @@ namespace {
 template <class P>
 struct Row {
   typename P::P2 v, e, w;
-  typename P::T b[2], d[2];  // b and inverse diagonal of the lane's two points (sweep modes)
+  typename P::T b[2];  // b at the lane's two points (sweep modes)
 };
 
 template <class P>
@@ -178,11 +178,12 @@ constexpr int THREADS2D = 256;
 // interface items (two items of up to 128 points per block), the others the
 // macro-interior tiles.  The two parts write disjoint slots and read only x,
 // so they run side by side.
-// Threads per block: 256 for the apply; 128 for the sweep modes, whose rows of
-// b and dinv are staged beside x (the static shared-memory limit).
+// Threads per block (the sweep modes stage rows of b beside x; the inverse
+// diagonal of a macro-interior point is the macro's constant 1 / centre
+// weight, so it is not read).
 template <int MODE>
 struct Thr2 {
-  static constexpr int value = MODE == MODE_APPLY ? THREADS2D : 128;
+  static constexpr int value = THREADS2D;
 };
 
 template <class P, int MODE>
@@ -200,7 +201,6 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
   static_assert(!SWEEP || sizeof(T) == 4, "the sweep modes are built for fp32");
   __shared__ T ring_all[THR / 32][RING][32][2];
   __shared__ T ringb_all[SWEEP ? THR / 32 : 1][SWEEP ? RING : 1][32][2];
-  __shared__ T ringd_all[MODE == MODE_JACOBI ? THR / 32 : 1][MODE == MODE_JACOBI ? RING : 1][32][2];
   if ((int)blockIdx.x < n_if_blocks) {
     const int item = (THR / 128) * (int)blockIdx.x + (int)(threadIdx.x >> 7);
     if (item >= n_items) return;
@@ -214,7 +214,6 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
   const int lane = threadIdx.x & 31;
   T(*ring)[32][2] = ring_all[threadIdx.x >> 5];
   T(*ringb)[32][2] = ringb_all[SWEEP ? threadIdx.x >> 5 : 0];
-  T(*ringd)[32][2] = ringd_all[MODE == MODE_JACOBI ? threadIdx.x >> 5 : 0];
 
   const int64_t m = warp / n_tiles;
   const int4 t = tiles[warp - m * n_tiles];
@@ -223,7 +222,8 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
   const T* __restrict__ xm = x + m * S;
   T* __restrict__ ym = y + m * S;
   const T* __restrict__ bm = SWEEP ? static_cast<const T*>(md.b) + m * S : nullptr;
-  const T* __restrict__ dm = MODE == MODE_JACOBI ? static_cast<const T*>(md.dinv) + m * S : nullptr;
+  // inverse diagonal of the macro's interior points, rounded as the set-up's
+  const T dint = MODE == MODE_JACOBI ? (T)(1.0 / __ldg(st.d + m * (int64_t)(NCLS2 * NW2) + C2)) : T(0);
 
   const int64_t wb = m * (int64_t)(NCLS2 * NW2);  // class 0: the full interior stencil
   const typename P::W wSE = P::weight(st, wb + 1), wC = P::weight(st, wb + 3), wE = P::weight(st, wb + 4),
@@ -237,12 +237,10 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
     if (ca < is.len) {
       cp_async(&ring[slot][lane][0], xm + is.off + ca, sizeof(T));
       if (SWEEP) cp_async(&ringb[slot][lane][0], bm + is.off + ca, sizeof(T));
-      if (MODE == MODE_JACOBI) cp_async(&ringd[slot][lane][0], dm + is.off + ca, sizeof(T));
     }
     if (cb < is.len) {
       cp_async(&ring[slot][lane][1], xm + is.off + cb, sizeof(T));
       if (SWEEP) cp_async(&ringb[slot][lane][1], bm + is.off + cb, sizeof(T));
-      if (MODE == MODE_JACOBI) cp_async(&ringd[slot][lane][1], dm + is.off + cb, sizeof(T));
     }
     is.next();
   };
@@ -260,10 +258,6 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
     if (SWEEP) {  // read before the slot is staged again
       r.b[0] = ringb[k & (RING - 1)][lane][0];
       r.b[1] = ringb[k & (RING - 1)][lane][1];
-      if (MODE == MODE_JACOBI) {
-        r.d[0] = ringd[k & (RING - 1)][lane][0];
-        r.d[1] = ringd[k & (RING - 1)][lane][1];
-      }
     }
     // the slot of step k is free again: stage step k + RING
     if (k + RING < steps) stage(k & (RING - 1));
@@ -291,8 +285,8 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
         ua = ce.v.x;
         ub = ce.v.y;
       }
-      outa = mode_out_staged<MODE, T>(outa, (T)ua, ce.b[0], ce.d[0], md.omega);
-      outb = mode_out_staged<MODE, T>(outb, (T)ub, ce.b[1], ce.d[1], md.omega);
+      outa = mode_out_staged<MODE, T>(outa, (T)ua, ce.b[0], dint, md.omega);
+      outb = mode_out_staged<MODE, T>(outb, (T)ub, ce.b[1], dint, md.omega);
     }
     if (wa && ca < out.len - 1) ym[out.off + ca] = outa;
     if (wbb && cb < out.len - 1) ym[out.off + cb] = outb;
