@@ -457,21 +457,20 @@ cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s) {
   // Jacobi update together), alternating between u and y; the residual
   // likewise.  Float64 cycles and 3D apply, then update.
   constexpr bool fused_ok = sizeof(T) == 4;
+  // `cur` holds the smoothed iterate; it alternates between u and y and is
+  // copied back into u only if the sweep count is odd
+  T* cur = u;
   auto sweeps2d = [&](int count) -> cudaError_t {
-    T* cur = u;
-    T* alt = y;
     for (int it = 0; it < count; ++it) {
+      T* alt = cur == u ? y : u;
       HY_TRY(launch_sweep2d(Vecs<T>::dtype, true, m, L, cur, b, Vecs<T>::dinv(g), sv.omega, alt, s));
-      T* t = cur;
       cur = alt;
-      alt = t;
     }
-    if (cur != u) HY_TRY(cudaMemcpyAsync(u, cur, sizeof(T) * ns, cudaMemcpyDeviceToDevice, s));
     return cudaSuccess;
   };
   if (m.dim == 2 && fused_ok) {
     HY_TRY(sweeps2d(sv.nu1));
-    HY_TRY(launch_sweep2d(Vecs<T>::dtype, false, m, L, u, b, Vecs<T>::dinv(g), sv.omega, r, s));
+    HY_TRY(launch_sweep2d(Vecs<T>::dtype, false, m, L, cur, b, Vecs<T>::dinv(g), sv.omega, r, s));
   } else {
     for (int it = 0; it < sv.nu1; ++it) {
       HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
@@ -488,9 +487,10 @@ cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s) {
   HY_TRY(restrict_t<T>(m, l, r, bc, s));
   HY_TRY(cudaMemsetAsync(uc, 0, sizeof(T) * m.levels[l - 1].slots_per_macro * m.n_cells, s));
   HY_TRY(vcycle_t<T>(m, l - 1, bc, uc, s));
-  HY_TRY(prolong_add_t<T>(m, l, uc, u, s));
+  HY_TRY(prolong_add_t<T>(m, l, uc, cur, s));
   if (m.dim == 2 && fused_ok) {
     HY_TRY(sweeps2d(sv.nu2));
+    if (cur != u) HY_TRY(cudaMemcpyAsync(u, cur, sizeof(T) * ns, cudaMemcpyDeviceToDevice, s));
   } else {
     for (int it = 0; it < sv.nu2; ++it) {
       HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
