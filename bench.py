@@ -331,7 +331,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
     pending = collections.deque(reqs)
     retry = collections.deque()
     outstanding = {}
-    lat, run, queue_s, iters, rels, ngs = [], [], [], [], [], []
+    lat, run, queue_s, iters, rels, ngs, setup = [], [], [], [], [], [], []
     hits = failed = eagain = 0
     errors = collections.Counter()
     t0 = time.perf_counter()
@@ -371,6 +371,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
             t_end = max(t_end, t0 + done_at)
             lat.append(done_at - q.arrival_s)
             run.append(r.run_s)
+            setup.append(r.setup_s)
             queue_s.append(r.queue_s)
             iters.append(r.iters)
             rels.append(r.relres)
@@ -391,6 +392,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
         "solves_per_s": len(lat) / span, "gdofs_solved_per_s": float(np.sum(ngs)) / span / 1e9,
         "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
         "service_ms_p50": pct(run, 50), "service_ms_p99": pct(run, 99), "queue_ms_p50": pct(queue_s, 50),
+        "setup_ms_p50": pct(setup, 50), "setup_share": float(np.sum(setup) / np.sum(run)) if run else None,
         "span_s": span, "done": len(lat), "failed": failed, "failures": dict(errors.most_common(5)),
         "admission_retries": eagain,
         "cache_hits": hits, "evictions": st["evictions"], "iterations_mean": float(np.mean(iters)) if iters else None,

@@ -338,6 +338,7 @@ typedef struct hyteg_result {
   double queue_s;   /* seconds from submission to the start of the work */
   double run_s;     /* seconds from the start to the end of the work */
   int64_t n_global; /* DoFs of the request's problem */
+  double setup_s;   /* part of run_s spent building the refined mesh (0 on a cache hit) */
 } hyteg_result;
 
 /* Creates a server on `device` with a device arena of mem_cap bytes and

@@ -92,7 +92,7 @@ class Result(ctypes.Structure):
     """struct hyteg_result"""
     _fields_ = [("status", ctypes.c_int), ("error", ctypes.c_int), ("iters", ctypes.c_int),
                 ("cache_hit", ctypes.c_int), ("relres", ctypes.c_double), ("queue_s", ctypes.c_double),
-                ("run_s", ctypes.c_double), ("n_global", ctypes.c_int64)]
+                ("run_s", ctypes.c_double), ("n_global", ctypes.c_int64), ("setup_s", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):

@@ -233,7 +233,9 @@ void hyteg_server::release(Entry* e) {
 
 int hyteg_server::run(Req& r, cudaStream_t s, bool* hit, hyteg_result* res, std::string* msg) {
   int err = HYTEG_OK;
+  const auto t0 = Clock::now();
   Entry* e = acquire(r, s, hit, &err, msg);
+  res->setup_s = seconds_since(t0, Clock::now());
   if (!e) return err;
   hyteg::Mesh& m = e->mesh->m;
   m.mem.stream = s;
@@ -307,6 +309,7 @@ void hyteg_server::worker(int w) {
       r->res.iters = res.iters;
       r->res.relres = res.relres;
       r->res.n_global = res.n_global;
+      r->res.setup_s = res.setup_s;
       r->msg = msg;
       r->res.run_s = seconds_since(r->t_start, Clock::now());
       r->res.cache_hit = hit ? 1 : 0;

@@ -20,6 +20,7 @@ class Result:
     queue_s: float
     run_s: float
     n_global: int
+    setup_s: float = 0.0
     message: str = ""
 
     @property
@@ -29,7 +30,8 @@ class Result:
 
 def _result(r: C.Result) -> Result:
     msg = C.lib.hyteg_last_error().decode(errors="replace") if r.status == REQ_FAILED else ""
-    return Result(r.status, r.error, r.iters, bool(r.cache_hit), r.relres, r.queue_s, r.run_s, r.n_global, msg)
+    return Result(r.status, r.error, r.iters, bool(r.cache_hit), r.relres, r.queue_s, r.run_s, r.n_global,
+                  r.setup_s, msg)
 
 
 class Server:
