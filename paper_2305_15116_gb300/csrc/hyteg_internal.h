@@ -115,6 +115,11 @@ struct Solver {
   int* v_of_slot0 = nullptr;     // level-0 slot -> vertex
   int* slot_of_v0 = nullptr;     // vertex -> one level-0 slot
   double* red = nullptr;         // reduction scratch: [RED_BLOCKS partials][2 results]
+  // one V-cycle per level on the level's own vectors, captured as CUDA graphs
+  // by the solve loop from the second solve on this workspace (fp32 and
+  // float64 cycles); `solves` counts the finished solves
+  std::vector<cudaGraphExec_t> graph32, graph64;
+  int solves = 0;
 };
 
 // Device memory source of a mesh (see devmem.cpp): cudaMalloc when `arena`
@@ -229,6 +234,9 @@ cudaError_t launch_apply2d(int dtype, const Mesh& m, const LevelDev& L, const vo
 cudaError_t launch_sweep2d(int dtype, bool jacobi, const Mesh& m, const LevelDev& L, const void* u, const void* b,
                            const void* dinv, double omega, void* out, cudaStream_t s);
 cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, cudaStream_t s);
+// raises the slab kernels' shared-memory limit (once per process; before any
+// stream capture)
+cudaError_t slab3d_prepare();
 cudaError_t launch_row3d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y, cudaStream_t s);
 cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,
                                     void* y, cudaStream_t s);

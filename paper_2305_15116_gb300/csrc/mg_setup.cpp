@@ -285,6 +285,10 @@ void compute_dirichlet_mask(const Mesh& m, int level, unsigned char* mask) {
 void solver_free(Mesh& m) {
   if (!m.solver) return;
   Solver& sv = *m.solver;
+  for (cudaGraphExec_t g : sv.graph32)
+    if (g) cudaGraphExecDestroy(g);
+  for (cudaGraphExec_t g : sv.graph64)
+    if (g) cudaGraphExecDestroy(g);
   for (auto& L : sv.lv) {
     dev_free(m, L.dinv64);
     dev_free(m, L.dinv32);
@@ -317,6 +321,10 @@ std::string solver_setup(Mesh& m, int max_level, int nu1, int nu2, double omega)
   const int center = d == 2 ? C2 : C3;
   if (m.n_verts > 4096) return "the coarsest level has more than 4096 vertices (dense direct solve)";
   solver_free(m);
+  if (d == 3) {
+    const cudaError_t e = slab3d_prepare();  // before any captured cycle
+    if (e != cudaSuccess) return std::string("cuda: ") + cudaGetErrorString(e);
+  }
   m.solver = new Solver();
   Solver& sv = *m.solver;
   sv.max_level = max_level;

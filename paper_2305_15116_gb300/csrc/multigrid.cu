@@ -529,6 +529,40 @@ cudaError_t mg_prolong_add(const Mesh& m, int lf, int dtype, const void* ec, voi
                     : prolong_add_t<double>(m, lf, (const double*)ec, (double*)uf, s);
 }
 
+// One V-cycle on level l's own vectors (b, u of the level's workspace).  From
+// the second solve on the same workspace it runs as a CUDA graph, captured
+// once and replayed: the ~10 launches per level of a cycle reach the GPU as
+// one graph launch.  A first solve runs the cycle directly (instantiating a
+// graph costs more than the launches it saves when the workspace serves one
+// solve only), as do streams that cannot be captured (the legacy default
+// stream).
+template <class T>
+cudaError_t vcycle_own(Mesh& m, int l, cudaStream_t s) {
+  Solver& sv = *m.solver;
+  MgLevel& g = sv.lv[l];
+  if (sv.solves == 0 || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
+    return vcycle_t<T>(m, l, Vecs<T>::b(g), Vecs<T>::u(g), s);
+  std::vector<cudaGraphExec_t>& ge = sizeof(T) == 4 ? sv.graph32 : sv.graph64;
+  if ((int)ge.size() <= l) ge.resize(l + 1, nullptr);
+  if (!ge[l]) {
+    cudaGraph_t graph = nullptr;
+    HY_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e = vcycle_t<T>(m, l, Vecs<T>::b(g), Vecs<T>::u(g), s);
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return e != cudaSuccess ? e : e2;
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(&ge[l], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+      ge[l] = nullptr;
+      return e3;
+    }
+  }
+  return cudaGraphLaunch(ge[l], s);
+}
+
 cudaError_t mg_vcycle(Mesh& m, int l, int dtype, const void* b, void* u, cudaStream_t s) {
   return dtype == 2 ? vcycle_t<float>(m, l, (const float*)b, (float*)u, s)
                     : vcycle_t<double>(m, l, (const double*)b, (double*)u, s);
@@ -580,19 +614,20 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
       k_to_f32<<<grid_for(ns), THREADS, 0, s>>>(g.b32, g.r64, ns);
       HY_TRY(cudaGetLastError());
       HY_TRY(cudaMemsetAsync(g.u32, 0, sizeof(float) * ns, s));
-      HY_TRY(vcycle_t<float>(m, l, g.b32, g.u32, s));
+      HY_TRY(vcycle_own<float>(m, l, s));
       k_add_f32<<<grid_for(ns), THREADS, 0, s>>>(u, g.u32, ns);
       HY_TRY(cudaGetLastError());
     } else {
       HY_TRY(cudaMemcpyAsync(g.b64, g.r64, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s));
       HY_TRY(cudaMemsetAsync(g.u64, 0, sizeof(double) * ns, s));
-      HY_TRY(vcycle_t<double>(m, l, g.b64, g.u64, s));
+      HY_TRY(vcycle_own<double>(m, l, s));
       k_add_f64<<<grid_for(ns), THREADS, 0, s>>>(u, g.u64, ns);
       HY_TRY(cudaGetLastError());
     }
   }
   *iters = it;
   *relres = rel;
+  ++sv.solves;
   return cudaSuccess;
 }
 

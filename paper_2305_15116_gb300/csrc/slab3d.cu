@@ -271,6 +271,26 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
   cp_async_wait_all();
 }
 
+// The shared-memory limit is a property of the kernel shared by every thread
+// and stream of the process: raise it once, to what the largest slab level
+// (n = 64) needs, so that concurrent launches for different levels never see
+// a limit set for another level.
+template <class P>
+cudaError_t ensure_attr() {
+  using SV = typename Stage<P>::S;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    constexpr int nmax = 64;
+    const int bmax = (nmax + 1) * (nmax + 2) / 2;
+    const size_t wb = ((size_t)NCLS3 * NW3 * sizeof(typename P::W) + 15) / 16 * 16;
+    const size_t rb = ((size_t)NRING * (bmax + 2 * (nmax + 3)) * sizeof(SV) + 15) / 16 * 16;
+    const size_t xb = Stage<P>::direct ? 0 : (size_t)bmax * sizeof(typename P::T);
+    attr = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wb + rb + xb));
+  });
+  return attr;
+}
+
 template <class P>
 cudaError_t launch_t(const LevelDev& L, const void* x, void* y, cudaStream_t s) {
   if (L.n_slabs == 0) return cudaSuccess;
@@ -282,20 +302,7 @@ cudaError_t launch_t(const LevelDev& L, const void* x, void* y, cudaStream_t s) 
   const size_t ring_bytes = ((size_t)NRING * (buf + 2 * guard) * sizeof(SV) + 15) / 16 * 16;
   const size_t raw_bytes = Stage<P>::direct ? 0 : (size_t)buf * sizeof(typename P::T);
   const size_t bytes = w_bytes + ring_bytes + raw_bytes;
-  // The shared-memory limit is a property of the kernel shared by every
-  // thread and stream of the process: raise it once, to what the largest slab
-  // level needs, so that concurrent launches for different levels never see a
-  // limit set for another level.
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    constexpr int nmax = 64;
-    const int bmax = (nmax + 1) * (nmax + 2) / 2;
-    const size_t wb = ((size_t)NCLS3 * NW3 * sizeof(typename P::W) + 15) / 16 * 16;
-    const size_t rb = ((size_t)NRING * (bmax + 2 * (nmax + 3)) * sizeof(SV) + 15) / 16 * 16;
-    const size_t xb = Stage<P>::direct ? 0 : (size_t)bmax * sizeof(typename P::T);
-    attr = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wb + rb + xb));
-  });
+  const cudaError_t attr = ensure_attr<P>();
   if (attr != cudaSuccess) return attr;
   if (n > 64) return cudaErrorInvalidValue;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
@@ -305,6 +312,13 @@ cudaError_t launch_t(const LevelDev& L, const void* x, void* y, cudaStream_t s) 
 }
 
 }  // namespace
+
+cudaError_t slab3d_prepare() {
+  cudaError_t e = ensure_attr<ArF64FF>();
+  if (e == cudaSuccess) e = ensure_attr<ArF32>();
+  if (e == cudaSuccess) e = ensure_attr<ArF64Native>();
+  return e;
+}
 
 cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
   switch (dtype) {
