@@ -148,6 +148,15 @@ int hyteg_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* 
 int hyteg_apply_host(hyteg_mesh* mesh, int level, int dtype, const void* x_host, void* y_host,
                      void* stream);
 
+/* `count` products y_hosts[i] = A x_hosts[i] with HOST vectors, pipelined:
+ * the host-to-device copy of x_{i+1}, the apply of x_i and the device-to-host
+ * copy of y_{i-1} run at the same time (two staging pairs owned by the mesh,
+ * two internal copy streams; the applies run on `stream` after its earlier
+ * work).  Returns when every y_hosts[i] is written.  Page-locked host memory
+ * is needed for the copies to overlap.  Errors as hyteg_apply_host. */
+int hyteg_apply_host_batch(hyteg_mesh* mesh, int level, int dtype, const void* const* x_hosts,
+                           void* const* y_hosts, int count, void* stream);
+
 /* ---- geometry queries (host only, any level 0..15, no refine needed) ----- */
 
 /* Coordinates of every slot: xyz[n_slots * dim] (host), slot s at

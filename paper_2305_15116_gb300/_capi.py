@@ -41,6 +41,9 @@ lib.hyteg_apply_timed.restype = ctypes.c_int
 lib.hyteg_apply_host.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p]
 lib.hyteg_apply_host.restype = ctypes.c_int
+lib.hyteg_apply_host_batch.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]
+lib.hyteg_apply_host_batch.restype = ctypes.c_int
 lib.hyteg_apply_host_static.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]
 lib.hyteg_apply_host_static.restype = ctypes.c_int

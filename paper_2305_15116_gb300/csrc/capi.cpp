@@ -216,6 +216,96 @@ int hyteg_apply_host(hyteg_mesh* mesh, int level, int dtype, const void* x_host,
   return HYTEG_OK;
 }
 
+int hyteg_apply_host_batch(hyteg_mesh* mesh, int level, int dtype, const void* const* x_hosts,
+                           void* const* y_hosts, int count, void* stream) {
+  if (int r = check_level(mesh, level)) return r;
+  if (!valid_dtype(dtype)) return fail(HYTEG_EINVAL, "unknown dtype");
+  if (count < 0 || (count > 0 && (!x_hosts || !y_hosts))) return fail(HYTEG_EINVAL, "bad batch");
+  for (int i = 0; i < count; ++i)
+    if (!x_hosts[i] || !y_hosts[i]) return fail(HYTEG_EINVAL, "NULL host vector in the batch");
+  if (count == 0) return HYTEG_OK;
+  hyteg::Mesh& m = mesh->m;
+  const size_t bytes = size_t(m.n_cells) * size_t(hyteg::slots_per_macro(m.dim, level)) * elem_size(dtype);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  // two staging pairs, one allocation each for x and y
+  if (m.stage_bytes < 2 * bytes) {
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    cudaFree(m.stage_x);
+    cudaFree(m.stage_y);
+    m.stage_x = m.stage_y = nullptr;
+    m.stage_bytes = 0;
+    if (cudaMalloc(&m.stage_x, 2 * bytes) != cudaSuccess || cudaMalloc(&m.stage_y, 2 * bytes) != cudaSuccess) {
+      cudaFree(m.stage_x);
+      m.stage_x = nullptr;
+      cudaGetLastError();
+      return fail(HYTEG_ENOMEM, "device staging allocation failed");
+    }
+    m.stage_bytes = 2 * bytes;
+  }
+  char* sx[2] = {static_cast<char*>(m.stage_x), static_cast<char*>(m.stage_x) + bytes};
+  char* sy[2] = {static_cast<char*>(m.stage_y), static_cast<char*>(m.stage_y) + bytes};
+  cudaStream_t up = nullptr, down = nullptr;
+  cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_cmp[2] = {nullptr, nullptr}, ev_down[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr;
+  auto cleanup = [&]() {
+    if (up) cudaStreamSynchronize(up);
+    if (down) cudaStreamSynchronize(down);
+    cudaStreamSynchronize(cs);
+    for (int k = 0; k < 2; ++k) {
+      if (ev_up[k]) cudaEventDestroy(ev_up[k]);
+      if (ev_cmp[k]) cudaEventDestroy(ev_cmp[k]);
+      if (ev_down[k]) cudaEventDestroy(ev_down[k]);
+    }
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (up) cudaStreamDestroy(up);
+    if (down) cudaStreamDestroy(down);
+  };
+#define HB_TRY(call, what)           \
+  do {                               \
+    e = (call);                      \
+    if (e != cudaSuccess) {          \
+      cleanup();                     \
+      return cuda_fail(e, what);     \
+    }                                \
+  } while (0)
+  HB_TRY(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking), "cudaStreamCreate");
+  HB_TRY(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking), "cudaStreamCreate");
+  for (int k = 0; k < 2; ++k) {
+    HB_TRY(cudaEventCreateWithFlags(&ev_up[k], cudaEventDisableTiming), "cudaEventCreate");
+    HB_TRY(cudaEventCreateWithFlags(&ev_cmp[k], cudaEventDisableTiming), "cudaEventCreate");
+    HB_TRY(cudaEventCreateWithFlags(&ev_down[k], cudaEventDisableTiming), "cudaEventCreate");
+  }
+  // the copies start after the caller's earlier work on `stream`
+  HB_TRY(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming), "cudaEventCreate");
+  HB_TRY(cudaEventRecord(ev_start, cs), "cudaEventRecord");
+  HB_TRY(cudaStreamWaitEvent(up, ev_start, 0), "cudaStreamWaitEvent");
+  for (int i = 0; i < count; ++i) {
+    const int k = i & 1;
+    if (i >= 2) HB_TRY(cudaStreamWaitEvent(up, ev_cmp[k], 0), "cudaStreamWaitEvent");  // x slot free
+    HB_TRY(cudaMemcpyAsync(sx[k], x_hosts[i], bytes, cudaMemcpyHostToDevice, up), "cudaMemcpyAsync H2D");
+    HB_TRY(cudaEventRecord(ev_up[k], up), "cudaEventRecord");
+    HB_TRY(cudaStreamWaitEvent(cs, ev_up[k], 0), "cudaStreamWaitEvent");
+    if (i >= 2) HB_TRY(cudaStreamWaitEvent(cs, ev_down[k], 0), "cudaStreamWaitEvent");  // y slot free
+    const char* what = "";
+    e = hyteg::launch_apply(m, level, dtype, sx[k], sy[k], cs, nullptr, &what);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, what);
+    }
+    HB_TRY(cudaEventRecord(ev_cmp[k], cs), "cudaEventRecord");
+    HB_TRY(cudaStreamWaitEvent(down, ev_cmp[k], 0), "cudaStreamWaitEvent");
+    HB_TRY(cudaMemcpyAsync(y_hosts[i], sy[k], bytes, cudaMemcpyDeviceToHost, down), "cudaMemcpyAsync D2H");
+    HB_TRY(cudaEventRecord(ev_down[k], down), "cudaEventRecord");
+  }
+#undef HB_TRY
+  e = cudaStreamSynchronize(down);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  return HYTEG_OK;
+}
+
 int hyteg_slot_coords(const hyteg_mesh* mesh, int level, double* xyz) {
   if (int r = check_host_level(mesh, level)) return r;
   if (!xyz) return fail(HYTEG_EINVAL, "xyz is NULL");

@@ -129,6 +129,19 @@ class Mesh:
         return y_host
 
     # ---- geometry -------------------------------------------------------------
+    def apply_host_batch(self, level: int, xs_host, ys_host, ieee: bool = False, stream=None):
+        """ys_host[i] = A xs_host[i] for lists of host tensors (page-locked for
+        overlap), copies and applies pipelined inside the library."""
+        if len(xs_host) != len(ys_host):
+            raise ValueError("xs_host and ys_host differ in length")
+        code = self._dtype_code(xs_host[0], ieee) if xs_host else F64
+        n = len(xs_host)
+        xp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs_host])
+        yp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ys_host])
+        C.check(C.lib.hyteg_apply_host_batch(self._h, level, code, xp, yp, n, ctypes.c_void_p(_stream_ptr(stream))),
+                "hyteg_apply_host_batch")
+        return ys_host
+
     def slot_coords(self, level: int) -> np.ndarray:
         """Coordinates of every slot, float64 [n_slots, dim]."""
         ns, _ = self.num_slots(level)
