@@ -560,6 +560,14 @@ def main():
             del v
             torch.cuda.empty_cache()
         line["variants"] = variants
+        # latency of one small apply (2 macros, level 7, 16,641 DoFs, L2-resident):
+        # the mean event time over back-to-back applies
+        v = setup("square2_L7", device, H.F64)
+        rv = timed_applies(v, 200, args.warmup, stream)
+        line["latency_small"] = {"workload": describe("square2_L7", v["ng"], v["ns"]),
+                                 "us_per_apply": 1e3 * rv["total_ms"] / 200,
+                                 "dtype": "f64 data, float-float arithmetic"}
+        del v
 
     if rank == 0 and world == 1 and not args.no_variants:
         line["solve"] = solve_workload(device, stream)
