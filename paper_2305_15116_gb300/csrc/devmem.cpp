@@ -106,6 +106,15 @@ size_t arena_largest_free(Arena* a) {
 }
 
 cudaError_t dev_alloc(const Mesh& m, void** p, size_t bytes) {
+  if (m.mem.region) {
+    DevMem& mm = const_cast<DevMem&>(m.mem);
+    const size_t need = round_up(bytes ? bytes : 1);
+    if (mm.region_used + need <= mm.region_size) {
+      *p = mm.region + mm.region_used;
+      mm.region_used += need;
+      return cudaSuccess;
+    }
+  }
   if (m.mem.arena) {
     *p = arena_alloc(m.mem.arena, bytes);
     return *p ? cudaSuccess : cudaErrorMemoryAllocation;
@@ -115,6 +124,8 @@ cudaError_t dev_alloc(const Mesh& m, void** p, size_t bytes) {
 
 void dev_free(const Mesh& m, void* p) {
   if (!p) return;
+  if (m.mem.region && static_cast<char*>(p) >= m.mem.region && static_cast<char*>(p) < m.mem.region + m.mem.region_size)
+    return;  // released with the region
   if (m.mem.arena) {
     // Arena blocks are handed to the next allocation at once, possibly on
     // another stream: drain the work this mesh queued (uploads, clears,

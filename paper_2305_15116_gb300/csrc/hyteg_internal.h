@@ -123,11 +123,16 @@ struct Solver {
 };
 
 // Device memory source of a mesh (see devmem.cpp): cudaMalloc when `arena`
-// is null, else blocks of the arena; uploads and clears go to `stream`.
+// is null, else blocks of the arena; with a `region` (one arena block
+// reserved for the whole mesh) allocations are carved from it first, in
+// order, and released with it.  Uploads and clears go to `stream`.
 struct Arena;
 struct DevMem {
   Arena* arena = nullptr;
   cudaStream_t stream = nullptr;
+  char* region = nullptr;
+  size_t region_size = 0;
+  size_t region_used = 0;
 };
 
 // Level-independent tables of the Poisson model problem (problem.cu): cell

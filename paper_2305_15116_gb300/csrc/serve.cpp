@@ -121,10 +121,14 @@ struct hyteg_server {
 
 void hyteg_server::destroy_entry(Entry* e) {
   if (e->mesh) {
-    hyteg::arena_free(arena, e->b);
-    hyteg::arena_free(arena, e->u);
-    hyteg::arena_free(arena, e->glob);
-    hyteg_mesh_destroy(e->mesh);
+    hyteg::Mesh& m = e->mesh->m;
+    char* region = m.mem.region;
+    cudaStreamSynchronize(m.mem.stream);
+    hyteg::dev_free(m, e->b);
+    hyteg::dev_free(m, e->u);
+    hyteg::dev_free(m, e->glob);
+    hyteg_mesh_destroy(e->mesh);  // its blocks outside the region go back here
+    hyteg::arena_free(arena, region);
   }
   e->mesh = nullptr;
 }
@@ -156,24 +160,35 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
       }
   }
   *hit = false;
-  // make room first: drop idle cached meshes, least recently used first,
-  // until the arena's free bytes cover the request's estimate
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    while (hyteg::arena_free_bytes(arena) < r.est && evict_one()) {
-    }
-  }
-  // build a new entry; should the arena still run out (fragmentation), drop
-  // more idle entries, then wait (bounded) for requests in flight to hand
-  // theirs back
+  // One arena block (the request's estimate) holds the whole refined mesh:
+  // reserve it first, dropping idle cached meshes least recently used first
+  // and, when none is left, waiting (bounded) for requests in flight to hand
+  // theirs back.  Allocations beyond the estimate fall back to the arena.
   const auto deadline = Clock::now() + std::chrono::seconds(120);
   for (;;) {
+    char* region = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      for (;;) {
+        region = static_cast<char*>(hyteg::arena_alloc(arena, r.est));
+        if (region || !evict_one()) break;
+      }
+      if (!region) {
+        if (Clock::now() > deadline || cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+          *err = HYTEG_ENOMEM;
+          *msg = "device arena exhausted";
+          return nullptr;
+        }
+        continue;
+      }
+    }
     auto e = std::make_unique<Entry>();
     e->key = r.key;
     e->busy = true;
     int rc = hyteg_mesh_create(r.dim, int64_t(r.coords.size() / r.dim), r.coords.data(),
                                int64_t(r.cells.size() / (r.dim + 1)), r.cells.data(), HYTEG_BC_DIRICHLET, &e->mesh);
     if (rc != HYTEG_OK) {
+      hyteg::arena_free(arena, region);
       *err = rc;
       *msg = hyteg_last_error();
       return nullptr;
@@ -181,6 +196,8 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
     hyteg::Mesh& m = e->mesh->m;
     m.mem.arena = arena;
     m.mem.stream = s;
+    m.mem.region = region;
+    m.mem.region_size = r.est;
     rc = hyteg_mesh_refine(e->mesh, r.level);
     if (rc == HYTEG_OK) rc = hyteg_solver_setup(e->mesh, r.level, 3, 3, 2.0 / 3.0);
     std::string perr;
@@ -191,10 +208,10 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
     if (rc == HYTEG_OK) {
       const int64_t ns = slots_of(r.dim, r.level, m.n_cells);
       e->n_global = hyteg::n_global_dofs(m, r.level);
-      e->b = static_cast<double*>(hyteg::arena_alloc(arena, size_t(ns) * 8));
-      e->u = static_cast<double*>(hyteg::arena_alloc(arena, size_t(ns) * 8));
-      e->glob = static_cast<double*>(hyteg::arena_alloc(arena, size_t(e->n_global) * 8));
-      if (!e->b || !e->u || !e->glob) rc = HYTEG_ENOMEM;
+      if (hyteg::dev_alloc(m, (void**)&e->b, size_t(ns) * 8) != cudaSuccess ||
+          hyteg::dev_alloc(m, (void**)&e->u, size_t(ns) * 8) != cudaSuccess ||
+          hyteg::dev_alloc(m, (void**)&e->glob, size_t(e->n_global) * 8) != cudaSuccess)
+        rc = HYTEG_ENOMEM;
     }
     if (rc == HYTEG_OK) {
       Entry* raw = e.get();
@@ -210,10 +227,10 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
       *msg = why;
       return nullptr;
     }
+    // the mesh outgrew its region and the arena: drop an idle mesh and retry
     std::unique_lock<std::mutex> lk(mu);
     if (evict_one()) continue;
-    if (Clock::now() > deadline ||
-        cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+    if (Clock::now() > deadline || cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
       *err = HYTEG_ENOMEM;
       *msg = "device arena exhausted: " + why;
       return nullptr;
