@@ -43,6 +43,11 @@ struct LevelDev {
   // interface work list: int4 (prim, b, a0, a1)
   int4* items = nullptr;
   int n_items = 0;
+  // 3D: slots of every copy of every interface point (work-list order) and
+  // each item's first entry
+  int64_t* if_slots = nullptr;
+  int64_t* if_item_base = nullptr;
+  int64_t n_if_slots = 0;
   // 3D row-kernel work list: int4 (x0, y0, y1, z): lattice columns x0-1..x0+30
   // (x0..x0+29 written), rows y0..y1-1 of slice z of one macro
   int4* r3_tiles = nullptr;
@@ -243,6 +248,7 @@ cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, 
 // stream capture)
 cudaError_t slab3d_prepare();
 cudaError_t launch_row3d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y, cudaStream_t s);
+cudaError_t build_iface_slots(const Mesh& m, const LevelDev& L, cudaStream_t s);
 cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,
                                     void* y, cudaStream_t s);
 

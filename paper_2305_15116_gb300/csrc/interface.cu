@@ -29,6 +29,65 @@ __device__ __forceinline__ int64_t tet_slot(int n, int x, int y, int z) {
   return zs + (int64_t)y * b - ((int64_t)y * (y - 1)) / 2 + x;
 }
 
+// Slots of every copy of every interface point, in work-list order: item i
+// owns the entries from item_base[i], (a - a0) * inc_count + copy for its
+// point a.  Built once per level; the reduction then reads the slots instead
+// of recomputing them from the incidence tables.
+template <int DIM>
+__global__ void __launch_bounds__(128) k_build_iface_slots(int64_t* __restrict__ out,
+                                                           const int64_t* __restrict__ item_base,
+                                                           const int4* __restrict__ items,
+                                                           const Prim* __restrict__ prims,
+                                                           const Inc* __restrict__ incs, int n, int64_t S) {
+  const int4 it = items[blockIdx.x];
+  const int a = it.z + threadIdx.x;
+  if (a >= it.w) return;
+  const Prim p = prims[it.x];
+  const int b = it.y;
+  int wv[3] = {0, 0, 0};
+  if (p.type == 0) {
+    wv[0] = n;
+  } else if (p.type == 1) {
+    wv[0] = n - a;
+    wv[1] = a;
+  } else {
+    wv[0] = n - a - b;
+    wv[1] = a;
+    wv[2] = b;
+  }
+  int64_t* o = out + item_base[blockIdx.x] + (int64_t)(a - it.z) * p.inc_count;
+  for (int i = 0; i < p.inc_count; ++i) {
+    const Inc inc = incs[p.inc_begin + i];
+    int q[3] = {0, 0, 0};
+    for (int j = 0; j <= p.type; ++j)
+      if (inc.corner[j] >= 1) q[inc.corner[j] - 1] += wv[j];
+    o[i] = (int64_t)inc.cell * S + (DIM == 2 ? tri_slot(n, q[0], q[1]) : tet_slot(n, q[0], q[1], q[2]));
+  }
+}
+
+// Reduce with the slot table: sum the copies' partial rows in ascending
+// macro order (the table's order) and write the sum into every copy.
+template <class T>
+__global__ void __launch_bounds__(128) k_interface_reduce_tab(const T* __restrict__ x, T* __restrict__ y,
+                                                              const int4* __restrict__ items,
+                                                              const Prim* __restrict__ prims,
+                                                              const int64_t* __restrict__ item_base,
+                                                              const int64_t* __restrict__ slots) {
+  const int4 it = items[blockIdx.x];
+  const int a = it.z + threadIdx.x;
+  if (a >= it.w) return;
+  const Prim p = prims[it.x];
+  if (!p.boundary && p.inc_count == 1) return;
+  const int64_t* sl = slots + item_base[blockIdx.x] + (int64_t)(a - it.z) * p.inc_count;
+  T acc = T(0);
+  if (p.boundary) {
+    acc = __ldg(x + __ldg(sl));
+  } else {
+    for (int i = 0; i < p.inc_count; ++i) acc += y[__ldg(sl + i)];
+  }
+  for (int i = 0; i < p.inc_count; ++i) y[__ldg(sl + i)] = acc;
+}
+
 // Reduce variant: the copies already hold their macro's partial row (written
 // by the 3D slab kernel); sum them in ascending macro order and write the sum
 // into every copy.  A point with a single copy is already complete.
@@ -77,6 +136,11 @@ __global__ void __launch_bounds__(128) k_interface_reduce(const T* __restrict__ 
 template <class T>
 cudaError_t launch_reduce_t(int dim, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
   if (L.n_items == 0) return cudaSuccess;
+  if (L.if_slots) {
+    k_interface_reduce_tab<T><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, L.if_item_base,
+                                                         L.if_slots);
+    return cudaGetLastError();
+  }
   if (dim == 2)
     k_interface_reduce<T, 2><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, m.d_incs, L.n,
                                                         L.slots_per_macro);
@@ -87,6 +151,17 @@ cudaError_t launch_reduce_t(int dim, const Mesh& m, const LevelDev& L, const voi
 }
 
 }  // namespace
+
+cudaError_t build_iface_slots(const Mesh& m, const LevelDev& L, cudaStream_t s) {
+  if (L.n_items == 0 || !L.if_slots) return cudaSuccess;
+  if (m.dim == 2)
+    k_build_iface_slots<2><<<L.n_items, 128, 0, s>>>(L.if_slots, L.if_item_base, L.items, m.d_prims, m.d_incs, L.n,
+                                                      L.slots_per_macro);
+  else
+    k_build_iface_slots<3><<<L.n_items, 128, 0, s>>>(L.if_slots, L.if_item_base, L.items, m.d_prims, m.d_incs, L.n,
+                                                      L.slots_per_macro);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x, void* y,
                                     cudaStream_t s) {

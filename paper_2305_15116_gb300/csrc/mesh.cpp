@@ -299,6 +299,8 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.items);
   dev_free(m, L.slabs);
   dev_free(m, L.r3_tiles);
+  dev_free(m, L.if_slots);
+  dev_free(m, L.if_item_base);
   dev_free(m, L.p2_st64);
   dev_free(m, L.p2_st32);
   dev_free(m, L.p2_hi);
@@ -463,6 +465,21 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   if (!(err = upload(m, &L.tiles, tiles)).empty()) return err;
   if (!(err = upload(m, &L.items, items)).empty()) return err;
   if (!(err = upload(m, &L.slabs, slabs)).empty()) return err;
+  if (d == 3 && !items.empty()) {
+    // the slot table of the interface reduction (built on the device)
+    std::vector<int64_t> base(items.size() + 1, 0);
+    for (size_t i = 0; i < items.size(); ++i)
+      base[i + 1] = base[i] + int64_t(items[i].w - items[i].z) * m.prims[items[i].x].inc_count;
+    L.n_if_slots = base.back();
+    if (!(err = upload(m, &L.if_item_base, base)).empty()) return err;
+    const cudaError_t e = dev_alloc(m, (void**)&L.if_slots, size_t(L.n_if_slots) * sizeof(int64_t));
+    if (e != cudaSuccess) {
+      L.if_slots = nullptr;
+      return "device allocation: interface slot table";
+    }
+    const cudaError_t e2 = build_iface_slots(m, L, m.mem.stream);
+    if (e2 != cudaSuccess) return std::string("cuda: ") + cudaGetErrorString(e2);
+  }
   if (d == 3) {
     // row-kernel tiles: every slice z, strips of 30 columns, chunks of 64 rows
     std::vector<int4> r3;

@@ -64,13 +64,14 @@ int64_t slots_of(int dim, int level, int64_t n_cells) { return hyteg::slots_per_
 
 // Device bytes of a request: per level the solver workspace (2 inverse
 // diagonals, owner flags, 4 float64 and 4 fp32 vectors: 61 B per slot) and
-// its tables, plus b, u (slot layout) and the global-order buffer on the
+// its tables (3D: the interface slot table), plus b, u (slot layout) and the global-order buffer on the
 // finest level, with a margin for tables and allocation rounding.
 size_t estimate_bytes(int dim, int level, int64_t n_cells, int64_t n_verts) {
   size_t b = 0;
   for (int l = 0; l <= level; ++l) {
     const int64_t S = hyteg::slots_per_macro(dim, l);
-    b += size_t(61) * size_t(S * n_cells) + size_t(4) * size_t(S) + (size_t(64) << 10);
+    // 3D: + the slot table of the interface copies (about 4 B per slot)
+    b += size_t(dim == 3 ? 65 : 61) * size_t(S * n_cells) + size_t(4) * size_t(S) + (size_t(64) << 10);
   }
   const int64_t ns = slots_of(dim, level, n_cells);
   b += size_t(24) * size_t(ns);
