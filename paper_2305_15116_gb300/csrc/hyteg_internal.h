@@ -48,6 +48,15 @@ struct LevelDev {
   int64_t* if_slots = nullptr;
   int64_t* if_item_base = nullptr;
   int64_t n_if_slots = 0;
+  // points with two copies (inside the domain) or one (Dirichlet), reduced
+  // by a flat kernel: (slot, slot) or (slot, -2); each item's first entry
+  // (-1: the item's points are not in the table); the items left to the
+  // general reduction
+  longlong2* if_pairs = nullptr;
+  int64_t n_if_pairs = 0;
+  int64_t* if_flat_base = nullptr;
+  int* if_rest = nullptr;
+  int n_if_rest = 0;
   // 3D row-kernel work list: int4 (x0, y0, y1, z): lattice columns x0-1..x0+30
   // (x0..x0+29 written), rows y0..y1-1 of slice z of one macro
   int4* r3_tiles = nullptr;

@@ -13,6 +13,8 @@
 //
 // Work list: one block per item (primitive, row b, points a0..a1-1) of at most
 // 128 points; a vertex item has one point.
+#include <algorithm>
+
 #include "arith.cuh"
 #include "hyteg_internal.h"
 
@@ -36,6 +38,8 @@ __device__ __forceinline__ int64_t tet_slot(int n, int x, int y, int z) {
 template <int DIM>
 __global__ void __launch_bounds__(128) k_build_iface_slots(int64_t* __restrict__ out,
                                                            const int64_t* __restrict__ item_base,
+                                                           const int64_t* __restrict__ flat_base,
+                                                           longlong2* __restrict__ pairs,
                                                            const int4* __restrict__ items,
                                                            const Prim* __restrict__ prims,
                                                            const Inc* __restrict__ incs, int n, int64_t S) {
@@ -56,12 +60,38 @@ __global__ void __launch_bounds__(128) k_build_iface_slots(int64_t* __restrict__
     wv[2] = b;
   }
   int64_t* o = out + item_base[blockIdx.x] + (int64_t)(a - it.z) * p.inc_count;
+  int64_t s01[2] = {-1, -2};
   for (int i = 0; i < p.inc_count; ++i) {
     const Inc inc = incs[p.inc_begin + i];
     int q[3] = {0, 0, 0};
     for (int j = 0; j <= p.type; ++j)
       if (inc.corner[j] >= 1) q[inc.corner[j] - 1] += wv[j];
     o[i] = (int64_t)inc.cell * S + (DIM == 2 ? tri_slot(n, q[0], q[1]) : tet_slot(n, q[0], q[1], q[2]));
+    if (i < 2) s01[i] = o[i];
+  }
+  // points of two copies (inside the domain) or one (Dirichlet) also go to
+  // the flat pair table: (slot, slot) or (slot, -2)
+  const int64_t fb = flat_base[blockIdx.x];
+  if (fb >= 0) pairs[fb + (a - it.z)] = make_longlong2(s01[0], p.boundary ? -2 : s01[1]);
+}
+
+// Flat reduction of the points of the pair table, one thread each: two copies
+// are summed (lower macro first) and the sum written to both; a Dirichlet
+// point of one copy gets y = x.
+// One thread per point and blocks in table order, so that the points in
+// flight at any time lie close together in the vectors (cache locality).
+template <class T>
+__global__ void __launch_bounds__(256) k_interface_reduce_pairs(const T* __restrict__ x, T* __restrict__ y,
+                                                                const longlong2* __restrict__ pairs, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const longlong2 pr = pairs[i];
+  if (pr.y == -2) {
+    y[pr.x] = __ldg(x + pr.x);
+  } else {
+    const T v = y[pr.x] + y[pr.y];
+    y[pr.x] = v;
+    y[pr.y] = v;
   }
 }
 
@@ -72,13 +102,15 @@ __global__ void __launch_bounds__(128) k_interface_reduce_tab(const T* __restric
                                                               const int4* __restrict__ items,
                                                               const Prim* __restrict__ prims,
                                                               const int64_t* __restrict__ item_base,
-                                                              const int64_t* __restrict__ slots) {
-  const int4 it = items[blockIdx.x];
+                                                              const int64_t* __restrict__ slots,
+                                                              const int* __restrict__ list) {
+  const int item = list[blockIdx.x];
+  const int4 it = items[item];
   const int a = it.z + threadIdx.x;
   if (a >= it.w) return;
   const Prim p = prims[it.x];
   if (!p.boundary && p.inc_count == 1) return;
-  const int64_t* sl = slots + item_base[blockIdx.x] + (int64_t)(a - it.z) * p.inc_count;
+  const int64_t* sl = slots + item_base[item] + (int64_t)(a - it.z) * p.inc_count;
   T acc = T(0);
   if (p.boundary) {
     acc = __ldg(x + __ldg(sl));
@@ -137,8 +169,13 @@ template <class T>
 cudaError_t launch_reduce_t(int dim, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
   if (L.n_items == 0) return cudaSuccess;
   if (L.if_slots) {
-    k_interface_reduce_tab<T><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, L.if_item_base,
-                                                         L.if_slots);
+    if (L.n_if_pairs > 0) {
+      const int64_t blocks = (L.n_if_pairs + 255) / 256;
+      k_interface_reduce_pairs<T><<<(unsigned)blocks, 256, 0, s>>>((const T*)x, (T*)y, L.if_pairs, L.n_if_pairs);
+    }
+    if (L.n_if_rest > 0)
+      k_interface_reduce_tab<T><<<L.n_if_rest, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, L.if_item_base,
+                                                             L.if_slots, L.if_rest);
     return cudaGetLastError();
   }
   if (dim == 2)
@@ -155,11 +192,11 @@ cudaError_t launch_reduce_t(int dim, const Mesh& m, const LevelDev& L, const voi
 cudaError_t build_iface_slots(const Mesh& m, const LevelDev& L, cudaStream_t s) {
   if (L.n_items == 0 || !L.if_slots) return cudaSuccess;
   if (m.dim == 2)
-    k_build_iface_slots<2><<<L.n_items, 128, 0, s>>>(L.if_slots, L.if_item_base, L.items, m.d_prims, m.d_incs, L.n,
-                                                      L.slots_per_macro);
+    k_build_iface_slots<2><<<L.n_items, 128, 0, s>>>(L.if_slots, L.if_item_base, L.if_flat_base, L.if_pairs,
+                                                      L.items, m.d_prims, m.d_incs, L.n, L.slots_per_macro);
   else
-    k_build_iface_slots<3><<<L.n_items, 128, 0, s>>>(L.if_slots, L.if_item_base, L.items, m.d_prims, m.d_incs, L.n,
-                                                      L.slots_per_macro);
+    k_build_iface_slots<3><<<L.n_items, 128, 0, s>>>(L.if_slots, L.if_item_base, L.if_flat_base, L.if_pairs,
+                                                      L.items, m.d_prims, m.d_incs, L.n, L.slots_per_macro);
   return cudaGetLastError();
 }
 

@@ -301,6 +301,9 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.r3_tiles);
   dev_free(m, L.if_slots);
   dev_free(m, L.if_item_base);
+  dev_free(m, L.if_pairs);
+  dev_free(m, L.if_flat_base);
+  dev_free(m, L.if_rest);
   dev_free(m, L.p2_st64);
   dev_free(m, L.p2_st32);
   dev_free(m, L.p2_hi);
@@ -472,6 +475,29 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
       base[i + 1] = base[i] + int64_t(items[i].w - items[i].z) * m.prims[items[i].x].inc_count;
     L.n_if_slots = base.back();
     if (!(err = upload(m, &L.if_item_base, base)).empty()) return err;
+    std::vector<int64_t> fbase(items.size(), -1);
+    std::vector<int> rest;
+    int64_t nflat = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+      const Prim& pr = m.prims[items[i].x];
+      if ((!pr.boundary && pr.inc_count == 2) || (pr.boundary && pr.inc_count == 1)) {
+        fbase[i] = nflat;
+        nflat += items[i].w - items[i].z;
+      } else if (pr.boundary || pr.inc_count > 1) {
+        rest.push_back(int(i));
+      }
+    }
+    L.n_if_pairs = nflat;
+    L.n_if_rest = int(rest.size());
+    if (!(err = upload(m, &L.if_flat_base, fbase)).empty()) return err;
+    if (!(err = upload(m, &L.if_rest, rest)).empty()) return err;
+    if (nflat > 0) {
+      const cudaError_t ep = dev_alloc(m, (void**)&L.if_pairs, size_t(nflat) * sizeof(longlong2));
+      if (ep != cudaSuccess) {
+        L.if_pairs = nullptr;
+        return "device allocation: interface pair table";
+      }
+    }
     const cudaError_t e = dev_alloc(m, (void**)&L.if_slots, size_t(L.n_if_slots) * sizeof(int64_t));
     if (e != cudaSuccess) {
       L.if_slots = nullptr;

@@ -70,8 +70,8 @@ size_t estimate_bytes(int dim, int level, int64_t n_cells, int64_t n_verts) {
   size_t b = 0;
   for (int l = 0; l <= level; ++l) {
     const int64_t S = hyteg::slots_per_macro(dim, l);
-    // 3D: + the slot table of the interface copies (about 4 B per slot)
-    b += size_t(dim == 3 ? 65 : 61) * size_t(S * n_cells) + size_t(4) * size_t(S) + (size_t(64) << 10);
+    // 3D: + the slot and pair tables of the interface copies (about 8 B per slot)
+    b += size_t(dim == 3 ? 69 : 61) * size_t(S * n_cells) + size_t(4) * size_t(S) + (size_t(64) << 10);
   }
   const int64_t ns = slots_of(dim, level, n_cells);
   b += size_t(24) * size_t(ns);
