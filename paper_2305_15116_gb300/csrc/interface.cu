@@ -75,16 +75,45 @@ __global__ void __launch_bounds__(128) k_build_iface_slots(int64_t* __restrict__
   if (fb >= 0) pairs[fb + (a - it.z)] = make_longlong2(s01[0], p.boundary ? -2 : s01[1]);
 }
 
-// Flat reduction of the points of the pair table, one thread each: two copies
-// are summed (lower macro first) and the sum written to both; a Dirichlet
-// point of one copy gets y = x.
-// One thread per point and blocks in table order, so that the points in
-// flight at any time lie close together in the vectors (cache locality).
+// Reduction with the precomputed tables, one launch.  Blocks [0, rest_blocks)
+// take the points with three or more copies (edges and vertices), two items of
+// the rest list per block: the copies' partial rows are summed in ascending
+// macro order (the slot table's order) and the sum written into every copy; a
+// Dirichlet point gets y = x.  The other blocks take the pair table, one
+// thread per point: two copies are summed (lower macro first) and the sum
+// written to both, or a Dirichlet point of one copy gets y = x.  Pair blocks
+// run in table order, so that the points in flight at any time lie close
+// together in the vectors.  The two sets of points are disjoint.
 template <class T>
-__global__ void __launch_bounds__(256) k_interface_reduce_pairs(const T* __restrict__ x, T* __restrict__ y,
-                                                                const longlong2* __restrict__ pairs, int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__global__ void __launch_bounds__(256) k_interface_reduce_flat(const T* __restrict__ x, T* __restrict__ y,
+                                                               const longlong2* __restrict__ pairs, int64_t n_pairs,
+                                                               const int4* __restrict__ items,
+                                                               const Prim* __restrict__ prims,
+                                                               const int64_t* __restrict__ item_base,
+                                                               const int64_t* __restrict__ slots,
+                                                               const int* __restrict__ list, int n_rest,
+                                                               int rest_blocks) {
+  if ((int)blockIdx.x < rest_blocks) {
+    const int k = 2 * (int)blockIdx.x + (int)(threadIdx.x >> 7);
+    if (k >= n_rest) return;
+    const int item = list[k];
+    const int4 it = items[item];
+    const int a = it.z + (int)(threadIdx.x & 127);
+    if (a >= it.w) return;
+    const Prim p = prims[it.x];
+    if (!p.boundary && p.inc_count == 1) return;
+    const int64_t* sl = slots + item_base[item] + (int64_t)(a - it.z) * p.inc_count;
+    T acc = T(0);
+    if (p.boundary) {
+      acc = __ldg(x + __ldg(sl));
+    } else {
+      for (int i = 0; i < p.inc_count; ++i) acc += y[__ldg(sl + i)];
+    }
+    for (int i = 0; i < p.inc_count; ++i) y[__ldg(sl + i)] = acc;
+    return;
+  }
+  const int64_t i = (int64_t)(blockIdx.x - rest_blocks) * blockDim.x + threadIdx.x;
+  if (i >= n_pairs) return;
   const longlong2 pr = pairs[i];
   if (pr.y == -2) {
     y[pr.x] = __ldg(x + pr.x);
@@ -93,31 +122,6 @@ __global__ void __launch_bounds__(256) k_interface_reduce_pairs(const T* __restr
     y[pr.x] = v;
     y[pr.y] = v;
   }
-}
-
-// Reduce with the slot table: sum the copies' partial rows in ascending
-// macro order (the table's order) and write the sum into every copy.
-template <class T>
-__global__ void __launch_bounds__(128) k_interface_reduce_tab(const T* __restrict__ x, T* __restrict__ y,
-                                                              const int4* __restrict__ items,
-                                                              const Prim* __restrict__ prims,
-                                                              const int64_t* __restrict__ item_base,
-                                                              const int64_t* __restrict__ slots,
-                                                              const int* __restrict__ list) {
-  const int item = list[blockIdx.x];
-  const int4 it = items[item];
-  const int a = it.z + threadIdx.x;
-  if (a >= it.w) return;
-  const Prim p = prims[it.x];
-  if (!p.boundary && p.inc_count == 1) return;
-  const int64_t* sl = slots + item_base[item] + (int64_t)(a - it.z) * p.inc_count;
-  T acc = T(0);
-  if (p.boundary) {
-    acc = __ldg(x + __ldg(sl));
-  } else {
-    for (int i = 0; i < p.inc_count; ++i) acc += y[__ldg(sl + i)];
-  }
-  for (int i = 0; i < p.inc_count; ++i) y[__ldg(sl + i)] = acc;
 }
 
 // Reduce variant: the copies already hold their macro's partial row (written
@@ -169,13 +173,12 @@ template <class T>
 cudaError_t launch_reduce_t(int dim, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
   if (L.n_items == 0) return cudaSuccess;
   if (L.if_slots) {
-    if (L.n_if_pairs > 0) {
-      const int64_t blocks = (L.n_if_pairs + 255) / 256;
-      k_interface_reduce_pairs<T><<<(unsigned)blocks, 256, 0, s>>>((const T*)x, (T*)y, L.if_pairs, L.n_if_pairs);
-    }
-    if (L.n_if_rest > 0)
-      k_interface_reduce_tab<T><<<L.n_if_rest, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, L.if_item_base,
-                                                             L.if_slots, L.if_rest);
+    const int rest_blocks = (L.n_if_rest + 1) / 2;
+    const int64_t blocks = rest_blocks + (L.n_if_pairs + 255) / 256;
+    if (blocks > 0)
+      k_interface_reduce_flat<T><<<(unsigned)blocks, 256, 0, s>>>((const T*)x, (T*)y, L.if_pairs, L.n_if_pairs,
+                                                                  L.items, m.d_prims, L.if_item_base, L.if_slots,
+                                                                  L.if_rest, L.n_if_rest, rest_blocks);
     return cudaGetLastError();
   }
   if (dim == 2)

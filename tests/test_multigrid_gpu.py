@@ -62,7 +62,7 @@ def _rhs(H, L, seed=2):
 
 
 @pytest.mark.parametrize("kind", ["f64", "f32"])
-@pytest.mark.parametrize("dim,L", [(2, 2), (2, 5), (3, 3)])
+@pytest.mark.parametrize("dim,L", [(2, 2), (2, 5), (3, 3), (3, 4)])
 def test_one_vcycle_matches_oracle(cuda, dim, L, kind):
     import torch
     dt = torch.float64 if kind == "f64" else torch.float32
