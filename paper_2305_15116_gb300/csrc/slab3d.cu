@@ -95,18 +95,6 @@ __device__ __forceinline__ int tri_row(int q, int K) {
   return y;
 }
 
-// tri_row with a fast reciprocal square root; the integer fix-ups make the
-// result exact whenever the estimate is within one row.
-__device__ __forceinline__ int tri_row_fast(int q, int K) {
-  const float b = 2.0f * K + 1.0f;
-  const float d = fmaxf(b * b - 8.0f * q, 1.0f);
-  int y = (int)((b - d * rsqrtf(d)) * 0.5f);
-  y = max(y, 0);
-  if (y * K - (y * (y - 1)) / 2 > q) --y;
-  if ((y + 1) * K - ((y + 1) * y) / 2 <= q) ++y;
-  return y;
-}
-
 constexpr int NRING = 4;  // slices z-1, z, z+1 being read, z+2 being filled
 
 template <class P>
@@ -172,41 +160,43 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
     const int bz = roff(z), bu = roff(z + 1), bd = roff(z - 1);
 
     // ---- interior points: x, y >= 1, x + y <= K = M - 2 (z >= 1) ---------
-    // The cnt = (K-1)K/2 interior points of the slice are enumerated row by
-    // row; every thread evaluates two of them together (q and q + 256).
+    // Work unit: two adjacent points (x, y), (x + 1, y) of one row, x odd.
+    // Rows are taken in pairs (y, y + 1), y = 1 + 2r, which together hold
+    // K - 1 - 2r units; r(K - r) units precede pair r, K/2 (K - K/2) in all.
+    // The second point of a unit at the end of an odd row lies on the
+    // macro's diagonal face: it is evaluated (its neighbours are valid ring
+    // cells) but not written.
     if (z >= 1 && M >= 4) {
       const int K = M - 2;
-      const int cnt = (K - 1) * K / 2;
-      for (int q0 = tid; q0 < cnt; q0 += 2 * SLAB_THREADS) {
-        const int q1 = min(q0 + SLAB_THREADS, cnt - 1);  // past the end: repeat a valid point
-        int p[2], yy[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int q = h ? q1 : q0;
-          const int j = tri_row_fast(q, K - 1);  // row y = j + 1 holds K - 1 - j points
-          yy[h] = j + 1;
-          const int xx = q - (j * (K - 1) - (j * (j - 1)) / 2) + 1;
-          p[h] = yy[h] * M - (yy[h] * (yy[h] - 1)) / 2 + xx;
-        }
-        // ring offsets of the point in slices z, z+1, z-1 and the row gap A = M - y
-        const int qz0 = bz + p[0], qz1 = bz + p[1];
-        const int qu0 = bu + p[0] - yy[0], qu1 = bu + p[1] - yy[1];
-        const int qd0 = bd + p[0] + yy[0], qd1 = bd + p[1] + yy[1];
-        const int A0 = M - yy[0], A1 = M - yy[1];
-        auto at = [&](int i0, int i1) { return P::pair(SS::get(ring[i0]), SS::get(ring[i1])); };
+      const int units = (K / 2) * (K - K / 2);
+      const float Kf = (float)K;
+      for (int u = tid; u < units; u += SLAB_THREADS) {
+        // row pair r: the largest r with r (K - r) <= u
+        const float d = fmaxf(Kf * Kf - 4.0f * (float)u, 1.0f);
+        int r = max((int)((Kf - d * rsqrtf(d)) * 0.5f), 0);
+        if (r * (K - r) > u) --r;
+        if ((r + 1) * (K - r - 1) <= u) ++r;
+        const int j = u - r * (K - r);
+        const int h = (K - 2 * r) >> 1;  // units in row 1 + 2r: ceil((K - 1 - 2r) / 2)
+        const int yy = j < h ? 1 + 2 * r : 2 + 2 * r;
+        const int xx = 1 + 2 * (j < h ? j : j - h);
+        const int p = yy * M - (yy * (yy - 1)) / 2 + xx;
+        // ring offsets of the first point in slices z, z+1, z-1; row gap A = M - y
+        const int qz = bz + p, qu = bu + p - yy, qd = bd + p + yy, A = M - yy;
+        auto at = [&](int i) { return P::pair(SS::get(ring[i]), SS::get(ring[i + 1])); };
         typename P::Acc a;
-        P::first(a, w[0], at(qz0, qz1));
-        P::add_sym(a, w[1], at(qz0 + 1, qz1 + 1), at(qz0 - 1, qz1 - 1));                  // (±1,0,0)
-        P::add_sym(a, w[3], at(qz0 + A0, qz1 + A1), at(qz0 - A0 - 1, qz1 - A1 - 1));      // (0,±1,0)
-        P::add_sym(a, w[5], at(qz0 - A0, qz1 - A1), at(qz0 + A0 - 1, qz1 + A1 - 1));      // ±(1,-1,0)
-        P::add_sym(a, w[7], at(qu0, qu1), at(qd0, qd1));                                  // (0,0,±1)
-        P::add_sym(a, w[8], at(qu0 - 1, qu1 - 1), at(qd0 + 1, qd1 + 1));                  // ±(-1,0,1)
-        P::add_sym(a, w[9], at(qu0 - A0, qu1 - A1), at(qd0 + A0 + 1, qd1 + A1 + 1));      // ±(0,-1,1)
-        P::add_sym(a, w[10], at(qu0 - A0 + 1, qu1 - A1 + 1), at(qd0 + A0, qd1 + A1));     // ±(1,-1,1)
+        P::first(a, w[0], at(qz));
+        P::add_sym(a, w[1], at(qz + 1), at(qz - 1));           // (±1,0,0)
+        P::add_sym(a, w[3], at(qz + A), at(qz - A - 1));       // (0,±1,0)
+        P::add_sym(a, w[5], at(qz - A), at(qz + A - 1));       // ±(1,-1,0)
+        P::add_sym(a, w[7], at(qu), at(qd));                   // (0,0,±1)
+        P::add_sym(a, w[8], at(qu - 1), at(qd + 1));           // ±(-1,0,1)
+        P::add_sym(a, w[9], at(qu - A), at(qd + A + 1));       // ±(0,-1,1)
+        P::add_sym(a, w[10], at(qu - A + 1), at(qd + A));      // ±(1,-1,1)
         T r0, r1;
         P::finish(a, r0, r1);
-        ym[zoff + p[0]] = r0;
-        if (q0 + SLAB_THREADS < cnt) ym[zoff + p[1]] = r1;
+        ym[zoff + p] = r0;
+        if (xx < K - yy) ym[zoff + p + 1] = r1;
       }
     }
     // ---- macro-boundary points of the slice: partial rows ---------------------
