@@ -78,6 +78,47 @@ struct Stage<ArF64FF> {
   static __device__ __forceinline__ S zero() { return make_float2(0.0f, 0.0f); }
 };
 
+// Class weights as kept in shared memory, and the policy's weight type built
+// from them (float-float: the two parts only; the packed forms are rebuilt in
+// registers).
+template <class P>
+struct WStore;
+template <>
+struct WStore<ArF32> {
+  using S = float;
+  static __device__ __forceinline__ S load(const StencilPtr& st, int64_t i) { return __ldg(st.f + i); }
+  static __device__ __forceinline__ ArF32::W w(S s) { return s; }
+};
+template <>
+struct WStore<ArF64Native> {
+  using S = double;
+  static __device__ __forceinline__ S load(const StencilPtr& st, int64_t i) { return __ldg(st.d + i); }
+  static __device__ __forceinline__ ArF64Native::W w(S s) { return s; }
+};
+template <>
+struct WStore<ArF64FF> {
+  using S = float2;
+  static __device__ __forceinline__ S load(const StencilPtr& st, int64_t i) {
+    return make_float2(__ldg(st.hi + i), __ldg(st.lo + i));
+  }
+  static __device__ __forceinline__ ArF64FF::W w(S s) {
+    return ArF64FF::W{f2_pack(s.x, s.x), f2_pack(s.y, s.y), s.x, s.y};
+  }
+};
+
+// Blocks per SM each kernel is built for (its register budget): 8-byte ring
+// elements as shared memory allows at n = 64 (the float-float weights are kept
+// as two floats and the next slice is staged in place, so that three blocks
+// fit); fp32 without a bound (0: the compiler's own choice, 40 registers).
+template <class P>
+struct SlabOcc {
+  static constexpr int value = 3;
+};
+template <>
+struct SlabOcc<ArF32> {
+  static constexpr int value = 0;
+};
+
 __device__ __forceinline__ int t3i(int k) { return k * (k + 1) * (k + 2) / 6; }
 __device__ __forceinline__ int slice_count(int n, int z) {
   const int M = n + 1 - z;
@@ -98,20 +139,24 @@ __device__ __forceinline__ int tri_row(int q, int K) {
 constexpr int NRING = 4;  // slices z-1, z, z+1 being read, z+2 being filled
 
 template <class P>
-__global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __restrict__ x,
+__global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(const typename P::T* __restrict__ x,
                                                          typename P::T* __restrict__ y,
                                                          const int4* __restrict__ items, int n, int64_t S,
-                                                         int buf_elems, int guard, int raw_bytes, StencilPtr st) {
+                                                         int buf_elems, int guard, StencilPtr st) {
   using SS = Stage<P>;
   using SV = typename SS::S;
   using T = typename P::T;
   using W = typename P::W;
-  // layout: [class weights: NCLS3*NW3 W] [ring: NRING x (guard + buf + guard) SV] [raw staging: buf T]
+  using WS = WStore<P>;
+  using WSV = typename WS::S;
+  // layout: [class weights: NCLS3*NW3 WSV] [ring: NRING x (guard + buf + guard) SV]
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  W* wcls = reinterpret_cast<W*>(smem_raw);
-  SV* ring = reinterpret_cast<SV*>(smem_raw + (NCLS3 * NW3 * sizeof(W) + 15) / 16 * 16);
+  WSV* wcls = reinterpret_cast<WSV*>(smem_raw);
+  SV* ring = reinterpret_cast<SV*>(smem_raw + (NCLS3 * NW3 * sizeof(WSV) + 15) / 16 * 16);
   const int stride = buf_elems + 2 * guard;
-  T* raw = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(ring) + ((size_t)NRING * stride * sizeof(SV) + 15) / 16 * 16);
+  // a slice staged raw (float-float) lands in its own ring buffer as T and
+  // is converted in place by the thread that staged each element
+  static_assert(SS::direct || sizeof(SV) == sizeof(T), "in-place staging needs equal element sizes");
   // offset of element 0 of slice z's buffer inside `ring`
   auto roff = [&](int z) -> int { return (z & (NRING - 1)) * stride + guard; };
 
@@ -124,7 +169,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
 
   // zero the ring (guards and stale tails must hold finite values), class weights
   for (int i = tid; i < NRING * stride; i += SLAB_THREADS) ring[i] = SS::zero();
-  for (int i = tid; i < NCLS3 * NW3; i += SLAB_THREADS) wcls[i] = P::weight(st, (int64_t)m * (NCLS3 * NW3) + i);
+  for (int i = tid; i < NCLS3 * NW3; i += SLAB_THREADS) wcls[i] = WS::load(st, (int64_t)m * (NCLS3 * NW3) + i);
   __syncthreads();
   // slices z0-1 .. z0+1 directly
   for (int z = max(z0 - 1, 0); z <= min(z0 + 1, n); ++z) {
@@ -142,6 +187,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
         const int rb = roff(zs);
         for (int i = tid; i < cnt; i += SLAB_THREADS) cp_async(&ring[rb + i], xm + off + i, sizeof(T));
       } else {
+        T* raw = reinterpret_cast<T*>(ring + roff(zs));
         for (int i = tid; i < cnt; i += SLAB_THREADS) cp_async(raw + i, xm + off + i, sizeof(T));
       }
     }
@@ -152,7 +198,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
 
   W w[NW3];  // interior weights (class 0) in registers
 #pragma unroll
-  for (int k = 0; k < NW3; ++k) w[k] = wcls[k];
+  for (int k = 0; k < NW3; ++k) w[k] = WS::w(wcls[k]);
 
   for (int z = z0; z < z1; ++z) {
     const int M = N - z;
@@ -225,24 +271,25 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
         }
         const int cls = (xx == 0 ? 1 : 0) | (yv == 0 ? 2 : 0) | (z == 0 ? 4 : 0) | (xx + yv == M - 1 ? 8 : 0);
         const int p = yv * M - (yv * (yv - 1)) / 2 + xx;
-        const W* cw = wcls + cls * NW3;
+        const WSV* cwv = wcls + cls * NW3;
+        auto cw = [&](int k) { return WS::w(cwv[k]); };
         const int qz = bz + p, qu = bu + p - yv, qd = bd + p + yv, A = M - yv;
         typename P::Acc1 a;
-        P::first1(a, cw[0], SS::get(ring[qz]));
-        P::add1(a, cw[1], SS::get(ring[qz + 1]));
-        P::add1(a, cw[2], SS::get(ring[qz - 1]));
-        P::add1(a, cw[3], SS::get(ring[qz + A]));
-        P::add1(a, cw[4], SS::get(ring[qz - A - 1]));
-        P::add1(a, cw[5], SS::get(ring[qz - A]));
-        P::add1(a, cw[6], SS::get(ring[qz + A - 1]));
-        P::add1(a, cw[7], SS::get(ring[qu]));
-        P::add1(a, cw[8], SS::get(ring[qu - 1]));
-        P::add1(a, cw[9], SS::get(ring[qu - A]));
-        P::add1(a, cw[10], SS::get(ring[qu - A + 1]));
-        P::add1(a, cw[11], SS::get(ring[qd]));
-        P::add1(a, cw[12], SS::get(ring[qd + 1]));
-        P::add1(a, cw[13], SS::get(ring[qd + A + 1]));
-        P::add1(a, cw[14], SS::get(ring[qd + A]));
+        P::first1(a, cw(0), SS::get(ring[qz]));
+        P::add1(a, cw(1), SS::get(ring[qz + 1]));
+        P::add1(a, cw(2), SS::get(ring[qz - 1]));
+        P::add1(a, cw(3), SS::get(ring[qz + A]));
+        P::add1(a, cw(4), SS::get(ring[qz - A - 1]));
+        P::add1(a, cw(5), SS::get(ring[qz - A]));
+        P::add1(a, cw(6), SS::get(ring[qz + A - 1]));
+        P::add1(a, cw(7), SS::get(ring[qu]));
+        P::add1(a, cw(8), SS::get(ring[qu - 1]));
+        P::add1(a, cw(9), SS::get(ring[qu - A]));
+        P::add1(a, cw(10), SS::get(ring[qu - A + 1]));
+        P::add1(a, cw(11), SS::get(ring[qd]));
+        P::add1(a, cw(12), SS::get(ring[qd + 1]));
+        P::add1(a, cw(13), SS::get(ring[qd + A + 1]));
+        P::add1(a, cw(14), SS::get(ring[qd + A]));
         ym[zoff + p] = P::finish1(a);
       }
     }
@@ -253,6 +300,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab3d(const typename P::T* __
     if (!SS::direct && z + 2 < z1 + 1 && z + 2 <= n) {
       const int cnt = slice_count(n, z + 2);
       const int rb = roff(z + 2);
+      const T* raw = reinterpret_cast<const T*>(ring + rb);
       for (int i = tid; i < cnt; i += SLAB_THREADS) ring[rb + i] = SS::from(raw[i]);
     }
     __syncthreads();
@@ -273,10 +321,9 @@ cudaError_t ensure_attr() {
   std::call_once(once, [] {
     constexpr int nmax = 64;
     const int bmax = (nmax + 1) * (nmax + 2) / 2;
-    const size_t wb = ((size_t)NCLS3 * NW3 * sizeof(typename P::W) + 15) / 16 * 16;
+    const size_t wb = ((size_t)NCLS3 * NW3 * sizeof(typename WStore<P>::S) + 15) / 16 * 16;
     const size_t rb = ((size_t)NRING * (bmax + 2 * (nmax + 3)) * sizeof(SV) + 15) / 16 * 16;
-    const size_t xb = Stage<P>::direct ? 0 : (size_t)bmax * sizeof(typename P::T);
-    attr = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wb + rb + xb));
+    attr = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wb + rb));
   });
   return attr;
 }
@@ -288,16 +335,15 @@ cudaError_t launch_t(const LevelDev& L, const void* x, void* y, cudaStream_t s) 
   const int n = L.n;
   const int buf = (n + 1) * (n + 2) / 2;
   const int guard = n + 3;
-  const size_t w_bytes = ((size_t)NCLS3 * NW3 * sizeof(typename P::W) + 15) / 16 * 16;
+  const size_t w_bytes = ((size_t)NCLS3 * NW3 * sizeof(typename WStore<P>::S) + 15) / 16 * 16;
   const size_t ring_bytes = ((size_t)NRING * (buf + 2 * guard) * sizeof(SV) + 15) / 16 * 16;
-  const size_t raw_bytes = Stage<P>::direct ? 0 : (size_t)buf * sizeof(typename P::T);
-  const size_t bytes = w_bytes + ring_bytes + raw_bytes;
+  const size_t bytes = w_bytes + ring_bytes;
   const cudaError_t attr = ensure_attr<P>();
   if (attr != cudaSuccess) return attr;
   if (n > 64) return cudaErrorInvalidValue;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
   k_slab3d<P><<<L.n_slabs, SLAB_THREADS, bytes, s>>>((const typename P::T*)x, (typename P::T*)y, L.slabs, n,
-                                                    L.slots_per_macro, buf, guard, (int)raw_bytes, st);
+                                                    L.slots_per_macro, buf, guard, st);
   return cudaGetLastError();
 }
 
