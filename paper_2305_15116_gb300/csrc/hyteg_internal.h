@@ -91,6 +91,22 @@ int64_t p2_edge_slots(int level);  // n(n+1)/2 edges of one group per macro
 int64_t p2_slots_per_macro(int level);
 
 // Interface primitive (coarse vertex, edge or face) and its incident cells.
+#ifdef __CUDACC__
+// Macro index of a slot index i (slots per macro S >= 2) without a 64-bit
+// division per element: for i, S < 2^32 the quotient is the high 64 bits of
+// i * (floor((2^64 - 1) / S) + 1) (Lemire, Kaser, Kurz, "Faster remainder by
+// direct computation", 2019).  The multiplier is formed once per thread.
+struct SlotDiv {
+  int64_t S;
+  unsigned long long m;  // 0: the plain division (vectors of 2^32 slots or more)
+  __device__ __forceinline__ SlotDiv(int64_t S_, int64_t total)
+      : S(S_), m(total <= 0xFFFFFFFFll ? ~0ull / (unsigned long long)S_ + 1 : 0ull) {}
+  __device__ __forceinline__ int64_t operator()(int64_t i) const {
+    return m ? (int64_t)__umul64hi((unsigned long long)i, m) : i / S;
+  }
+};
+#endif
+
 struct Prim {
   int type;        // 0 vertex, 1 edge, 2 face
   int boundary;    // 1 if all its refined points are Dirichlet DoFs

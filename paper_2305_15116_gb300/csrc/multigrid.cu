@@ -117,8 +117,9 @@ __global__ void k_partial_diff(const double* __restrict__ u, double* __restrict_
   constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
   constexpr int NW = DIM == 2 ? NW2 : NW3;
   constexpr int CEN = DIM == 2 ? C2 : C3;
+  const SlotDiv divS(S, total);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = i / S;
+    const int64_t cell = divS(i);
     int q[3];
     unpack<DIM>(lpts[i - cell * S], q);
     const int cls = pclass<DIM>(n, q);
@@ -155,8 +156,9 @@ __global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ bc, const u
   constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
   constexpr int ND = DIM == 2 ? 3 : 7;
   const int nf = 2 * nc;
+  const SlotDiv divSc(Sc, total);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = i / Sc;
+    const int64_t cell = divSc(i);
     int q[3];
     unpack<DIM>(lpts_c[i - cell * Sc], q);
     const int f[3] = {2 * q[0], 2 * q[1], 2 * q[2]};
@@ -233,8 +235,9 @@ __global__ void k_diag_part(double* __restrict__ diag, unsigned char* __restrict
   constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
   constexpr int NW = DIM == 2 ? NW2 : NW3;
   constexpr int CEN = DIM == 2 ? C2 : C3;
+  const SlotDiv divS(S, total);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = i / S;
+    const int64_t cell = divS(i);
     int q[3];
     unpack<DIM>(lpts[i - cell * S], q);
     diag[i] = st[(cell * NCLS + pclass<DIM>(n, q)) * NW + CEN];
@@ -292,8 +295,9 @@ __global__ void k_diag_invert(double* __restrict__ d64, float* __restrict__ d32,
 template <class T, int DIM>
 __global__ void k_prolong_add(T* __restrict__ uf, const T* __restrict__ ec, const unsigned* __restrict__ lpts_f,
                               int nc, int64_t Sc, int64_t Sf, int64_t total) {
+  const SlotDiv divSf(Sf, total);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = i / Sf;
+    const int64_t cell = divSf(i);
     int q[3];
     unpack<DIM>(lpts_f[i - cell * Sf], q);
     const T* __restrict__ e = ec + cell * Sc;

@@ -165,8 +165,9 @@ __global__ void k_rhs_interior(double* __restrict__ b, const unsigned* __restric
                                int64_t S, int64_t total, Counts k, double cnt0, uint64_t seed, double noise) {
   const double inv_n = 1.0 / n;
   const double nd = DIM == 2 ? double(n) * n : double(n) * n * n;
+  const SlotDiv divS(S, total);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = i / S;
+    const int64_t cell = divS(i);
     int q[3];
     unpack<DIM>(lpts[i - cell * S], q);
     if (!macro_interior<DIM>(n, q)) continue;
@@ -216,8 +217,9 @@ __global__ void __launch_bounds__(128) k_rhs_iface(double* __restrict__ b, const
 template <int DIM>
 __global__ void k_global_interior(double* __restrict__ out, const double* __restrict__ v,
                                   const unsigned* __restrict__ lpts, int n, int64_t S, int64_t total, Counts k) {
+  const SlotDiv divS(S, total);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = i / S;
+    const int64_t cell = divS(i);
     int q[3];
     unpack<DIM>(lpts[i - cell * S], q);
     if (!macro_interior<DIM>(n, q)) continue;
