@@ -86,11 +86,6 @@ __global__ void k_residual(T* __restrict__ r, const T* __restrict__ b, const T* 
     r[i] = b[i] - y[i];
 }
 
-__global__ void k_to_f32(float* __restrict__ o, const double* __restrict__ v, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = __double2float_rn(v[i]);
-}
-
 __global__ void k_add_f64(double* __restrict__ u, const double* __restrict__ e, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     u[i] = u[i] + e[i];
@@ -367,6 +362,28 @@ __global__ void k_dot_final(const double* __restrict__ partial, int nb, double* 
   if (threadIdx.x == 0) *out = sm[0];
 }
 
+// r = b - y at every slot, stored as TO (the correction cycle's right-hand
+// side), and per-block partial sums of r^2 over one copy of every
+// non-Dirichlet DoF (fixed grid and order: deterministic).
+template <class TO>
+__global__ void k_residual_norm(TO* __restrict__ out, const double* __restrict__ b, const double* __restrict__ y,
+                                const unsigned char* __restrict__ owner, int64_t n, double* __restrict__ partial) {
+  __shared__ double sm[THREADS];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = b[i] - y[i];
+    out[i] = (TO)r;
+    if (owner[i]) acc += r * r;
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
 int grid_for(int64_t n) {
   const int64_t g = (n + THREADS - 1) / THREADS;
   return int(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
@@ -572,9 +589,8 @@ cudaError_t mg_vcycle(Mesh& m, int l, int dtype, const void* b, void* u, cudaStr
                     : vcycle_t<double>(m, l, (const double*)b, (double*)u, s);
 }
 
-// r = b - A u in float64, difference form; Dirichlet rows: r = b - u.
-cudaError_t accurate_residual(const Mesh& m, int l, const double* b, const double* u, double* y, double* r,
-                              cudaStream_t s) {
+// y = A u in float64, difference form; Dirichlet rows: y = u.
+cudaError_t accurate_apply(const Mesh& m, int l, const double* u, double* y, cudaStream_t s) {
   const Solver& sv = *m.solver;
   const LevelDev& L = m.levels[l];
   const int64_t ns = L.slots_per_macro * m.n_cells;
@@ -583,9 +599,7 @@ cudaError_t accurate_residual(const Mesh& m, int l, const double* b, const doubl
   else
     k_partial_diff<3><<<grid_for(ns), THREADS, 0, s>>>(u, y, sv.lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns);
   HY_TRY(cudaGetLastError());
-  HY_TRY(launch_interface_reduce(3, m.dim, m, L, u, y, s));  // sum the copies; Dirichlet rows: y = u
-  k_residual<double><<<grid_for(ns), THREADS, 0, s>>>(r, b, y, ns);
-  return cudaGetLastError();
+  return launch_interface_reduce(3, m.dim, m, L, u, y, s);  // sum the copies; Dirichlet rows: y = u
 }
 
 cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, double rtol, int max_iter,
@@ -608,18 +622,26 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
   // form; from there on, and for every stopping decision, the difference form.
   constexpr double kFastUntil = 1e-6;
   bool fast = true;
+  // r = b - A u goes straight into the correction cycle's right-hand side
+  // (fp32 for HYTEG_SOLVE_MIXED), its norm from the same pass
   auto residual = [&](bool ff, double* out) -> cudaError_t {
     if (ff) {
       const char* what = "";
       HY_TRY(launch_apply(m, l, 1, u, g.y64, s, nullptr, &what));
-      k_residual<double><<<grid_for(ns), THREADS, 0, s>>>(g.r64, b, g.y64, ns);
-      HY_TRY(cudaGetLastError());
     } else {
-      HY_TRY(accurate_residual(m, l, b, u, g.y64, g.r64, s));
+      HY_TRY(accurate_apply(m, l, u, g.y64, s));
     }
-    double nr = 0.0;
-    HY_TRY(norm2<double>(m, l, g.r64, &nr, s));
-    *out = nr / nb;
+    if (mode == 2)
+      k_residual_norm<float><<<RED_BLOCKS, THREADS, 0, s>>>(g.b32, b, g.y64, g.owner, ns, sv.red);
+    else
+      k_residual_norm<double><<<RED_BLOCKS, THREADS, 0, s>>>(g.b64, b, g.y64, g.owner, ns, sv.red);
+    HY_TRY(cudaGetLastError());
+    k_dot_final<<<1, THREADS, 0, s>>>(sv.red, RED_BLOCKS, sv.red + RED_BLOCKS);
+    HY_TRY(cudaGetLastError());
+    double h = 0.0;
+    HY_TRY(cudaMemcpyAsync(&h, sv.red + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HY_TRY(cudaStreamSynchronize(s));
+    *out = sqrt(h) / nb;
     return cudaSuccess;
   };
   for (;; ++it) {
@@ -645,14 +667,11 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
     }
     prev = rel;
     if (mode == 2) {
-      k_to_f32<<<grid_for(ns), THREADS, 0, s>>>(g.b32, g.r64, ns);
-      HY_TRY(cudaGetLastError());
       HY_TRY(cudaMemsetAsync(g.u32, 0, sizeof(float) * ns, s));
       HY_TRY(vcycle_own<float>(m, l, s));
       k_add_f32<<<grid_for(ns), THREADS, 0, s>>>(u, g.u32, ns);
       HY_TRY(cudaGetLastError());
     } else {
-      HY_TRY(cudaMemcpyAsync(g.b64, g.r64, sizeof(double) * ns, cudaMemcpyDeviceToDevice, s));
       HY_TRY(cudaMemsetAsync(g.u64, 0, sizeof(double) * ns, s));
       HY_TRY(vcycle_own<double>(m, l, s));
       k_add_f64<<<grid_for(ns), THREADS, 0, s>>>(u, g.u64, ns);
