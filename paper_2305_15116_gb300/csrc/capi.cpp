@@ -107,6 +107,10 @@ int hyteg_mesh_refine(hyteg_mesh* mesh, int max_level) {
       }
       m.levels.push_back(L);
       m.max_level = l;
+      if (m.dim == 3) {  // pick the 3D slab kernel's work split for this level
+        e = hyteg::slab3d_autotune(m, m.levels.back());
+        if (e != cudaSuccess) return cuda_fail(e, "slab work-split autotuning");
+      }
     }
     e = hyteg::dev_sync(m);
     if (e != cudaSuccess) return cuda_fail(e, "refine");
@@ -137,6 +141,14 @@ void hyteg_mesh_destroy(hyteg_mesh* mesh) {
     cudaSetDevice(cur);
   }
   delete mesh;
+}
+
+int hyteg_autotune_choice(const hyteg_mesh* mesh, int level, int dtype, int* value) {
+  if (int r = check_level(mesh, level)) return r;
+  if (!value) return fail(HYTEG_EINVAL, "value is NULL");
+  if (dtype != HYTEG_F64 && dtype != HYTEG_F32 && dtype != HYTEG_F64_IEEE) return fail(HYTEG_EINVAL, "bad dtype");
+  *value = mesh->m.levels[level].slab_chunks[dtype];
+  return HYTEG_OK;
 }
 
 int hyteg_num_slots(const hyteg_mesh* mesh, int level, int64_t* n_slots, int64_t* n_global) {

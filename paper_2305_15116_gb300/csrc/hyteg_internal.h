@@ -64,6 +64,11 @@ struct LevelDev {
   // 3D slab work list (levels with n <= 64): int4 (macro, z0, z1, 0)
   int4* slabs = nullptr;
   int n_slabs = 0;
+  // per element type (1 float-float, 2 fp32, 3 native fp64): the slab work
+  // list the autotuner picked (nullptr: `slabs`), and its z-ranges per macro
+  int4* slabs_dt[4] = {nullptr, nullptr, nullptr, nullptr};
+  int n_slabs_dt[4] = {0, 0, 0, 0};
+  int slab_chunks[4] = {0, 0, 0, 0};
   // host copy of the class stencils (multigrid set-up)
   std::vector<double> st_host;
   // P2 (2D): class stencils [cell][P2W] and the edge interface work list
@@ -211,6 +216,13 @@ void set_last_error(const std::string& msg);
 // Returns an error message, empty on success.
 std::string build_topology(Mesh& m);
 std::string build_level(Mesh& m, int level, LevelDev& out);
+// 3D slab work items (macro, z0, z1): every macro cut into `chunks` z-ranges
+// of about equal point counts
+std::vector<int4> slab_work_list(int n, int64_t n_cells, int chunks);
+// Time the slab kernel on this level for several z-range counts per element
+// type and keep the fastest list (levels of at least 2^18 slots; results are
+// cached per (macro count, level size) for the process).  Synchronous.
+cudaError_t slab3d_autotune(Mesh& m, LevelDev& L);
 void free_level(const Mesh& m, LevelDev& L);
 
 // ---- P2 (p2_setup.cpp, p2.cu) ------------------------------------------------

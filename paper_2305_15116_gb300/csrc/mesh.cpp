@@ -290,6 +290,25 @@ std::string build_topology(Mesh& m) {
   return "";
 }
 
+std::vector<int4> slab_work_list(int n, int64_t n_cells, int chunks) {
+  // cuts at z where the cumulative slice point count passes c/chunks of the
+  // macro's slots; items ordered by z-range, then macro
+  const int64_t S = (int64_t(n) + 1) * (n + 2) * (n + 3) / 6;
+  std::vector<int> cuts = {0};
+  int64_t acc = 0;
+  for (int z = 0; z <= n; ++z) {
+    const int64_t M = n + 1 - z;
+    acc += M * (M + 1) / 2;
+    if (int(cuts.size()) < chunks && acc * chunks >= S * int64_t(cuts.size()) && z < n) cuts.push_back(z + 1);
+  }
+  cuts.push_back(n + 1);
+  std::vector<int4> items;
+  for (size_t c = 0; c + 1 < cuts.size(); ++c)
+    for (int64_t mm = 0; mm < n_cells; ++mm)
+      if (cuts[c] < cuts[c + 1]) items.push_back(make_int4(int(mm), cuts[c], cuts[c + 1], 0));
+  return items;
+}
+
 void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.st64);
   dev_free(m, L.st32);
@@ -298,6 +317,7 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.tiles);
   dev_free(m, L.items);
   dev_free(m, L.slabs);
+  for (int t = 0; t < 4; ++t) dev_free(m, L.slabs_dt[t]);
   dev_free(m, L.r3_tiles);
   dev_free(m, L.if_slots);
   dev_free(m, L.if_item_base);
@@ -440,24 +460,11 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   }
   L.n_items = int(items.size());
 
-  // ---- 3D slab work list: every macro cut into z-ranges of about equal
-  // point counts (n <= 64, where three slices fit in shared memory) ----------
+  // ---- 3D slab work list: every macro cut into two z-ranges of about equal
+  // point counts (n <= 64, where three slices fit in shared memory); the
+  // autotuner may replace it per element type after refinement -------------
   std::vector<int4> slabs;
-  if (d == 3 && n <= 64) {
-    constexpr int CHUNKS = 2;
-    const int64_t S = L.slots_per_macro;
-    std::vector<int> cuts = {0};
-    int64_t acc = 0;
-    for (int z = 0; z <= n; ++z) {
-      const int64_t M = n + 1 - z;
-      acc += M * (M + 1) / 2;
-      if (int(cuts.size()) < CHUNKS && acc * CHUNKS >= S * int64_t(cuts.size()) && z < n) cuts.push_back(z + 1);
-    }
-    cuts.push_back(n + 1);
-    for (size_t c = 0; c + 1 < cuts.size(); ++c)
-      for (int64_t mm = 0; mm < m.n_cells; ++mm)
-        if (cuts[c] < cuts[c + 1]) slabs.push_back(make_int4(int(mm), cuts[c], cuts[c + 1], 0));
-  }
+  if (d == 3 && n <= 64) slabs = slab_work_list(n, m.n_cells, 2);
   L.n_slabs = int(slabs.size());
 
   std::string err;

@@ -75,6 +75,9 @@ size_t estimate_bytes(int dim, int level, int64_t n_cells, int64_t n_verts) {
   }
   const int64_t ns = slots_of(dim, level, n_cells);
   b += size_t(24) * size_t(ns);
+  // 3D: scratch vectors of the slab work-split autotuner (two float64
+  // vectors on the levels it times, all levels together below 20 B per slot)
+  if (dim == 3) b += size_t(20) * size_t(ns);
   b += size_t(8) * size_t(n_verts) * size_t(n_verts) * 2;  // dense level-0 inverse (fp64 + fp32 copy)
   b += size_t(1) << 20;
   return b;

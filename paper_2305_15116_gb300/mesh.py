@@ -62,6 +62,12 @@ class Mesh:
         self.max_level = max(self.max_level, max_level)
         return self
 
+    def autotune_choice(self, level: int, dtype: int = F64) -> int:
+        """z-ranges per macro-tet the 3D slab autotuner picked (0: not tuned)."""
+        v = ctypes.c_int()
+        C.check(C.lib.hyteg_autotune_choice(self._h, level, dtype, ctypes.byref(v)), "hyteg_autotune_choice")
+        return v.value
+
     def num_slots(self, level: int):
         """(slots in the library layout, distinct refined vertices)."""
         ns, ng = ctypes.c_int64(), ctypes.c_int64()

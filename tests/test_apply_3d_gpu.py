@@ -94,3 +94,32 @@ def test_level7_row_kernel_sampled(cuda, kind):
     yref = oracle.row_apply(rm, gids, x)
     absrow = np.array([_absrow(rm, g, x) for g in gids])
     check_close(yg[slots], yref, absrow, kind, "3D L7 sampled")
+
+
+def test_slab_autotune_choices_and_parity(cuda):
+    """Refinement autotunes the slab kernel's work split on 3D levels of at
+    least 2^18 slots; every element type's chosen list must still cover every
+    slot (outputs start as NaN) and match the oracle on sampled rows."""
+    H = _lib()
+    coarse = unit_cube_kuhn_mesh(2, 0.1, 3)  # 48 macro-tets
+    M = H.Mesh(coarse.coords, coarse.cells).refine(6)
+    for L, tuned in ((4, False), (5, True), (6, True)):
+        for dt in (H.F64, H.F32, H.F64_IEEE):
+            c = M.autotune_choice(L, dt)
+            assert (c in (2, 3, 4, 5, 6, 8)) if tuned else c == 0, (L, dt, c)
+    L = 6
+    ns, ng = M.num_slots(L)
+    smap = M.dof_map(L)
+    rm = oracle.RefinedMesh(coarse.coords, coarse.cells, L)
+    rng = np.random.default_rng(31)
+    slots = rng.integers(0, ns, 200)
+    gids = smap[slots]
+    for kind in KINDS:
+        x = random_vector(ng, 8)
+        if kind == "f32":
+            x = x.astype(np.float32).astype(np.float64)
+        yg = gpu_apply(M, L, x[smap], kind)
+        assert np.all(np.isfinite(yg)), kind
+        yref = oracle.row_apply(rm, gids, x)
+        absrow = np.array([_absrow(rm, g, x) for g in gids])
+        check_close(yg[slots], yref, absrow, kind, f"autotuned 3D L6 {kind}")
