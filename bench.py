@@ -557,6 +557,8 @@ def main():
                 "interior_GBps": vb / (rv["interior_ms"] * 1e-3) / 1e9,
                 "interior_frac": vb / (rv["interior_ms"] * 1e-3) / 1e9 / peak,
                 "interior_ms": rv["interior_ms"], "interface_ms": rv["iface_ms"]})
+            if v["kernel"] == "k_slab3d":  # the work split the refinement's autotuner picked
+                variants[-1]["slab_z_ranges_per_macro"] = v["M"].autotune_choice(v["L"], vcode)
             del v
             torch.cuda.empty_cache()
         line["variants"] = variants
