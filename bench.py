@@ -296,16 +296,21 @@ def solve_workload(device, stream, reps=3, rtol=1e-10):
 
 
 # ---------------------------------------------------------------- solve server
-def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
+def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=None):
     """The solve server under the synthetic request stream of inputs.serving:
     Poisson arrivals at 2000/s, half 2D (4..64 macro-triangles, levels 5..10),
     half 3D (6..384 macro-tets, levels 3..6), each request a lumped-mass
     right-hand side with its own noise seed, solved to rtol with fp32 V(3,3)
-    cycles in float64 refinement; the solution of every request is copied
-    back to host memory.  Requests refused by the memory cap are retried in
-    order.  Latency runs from a request's arrival to the end of its work."""
+    cycles in float64 refinement (mode None) or float64 cycles; the solution
+    of every request is copied back to host memory.  Requests refused by the
+    memory cap are retried in order.  Latency runs from a request's arrival
+    to the end of its work.  A solve whose residual stops falling above rtol
+    (the float64 floor of 2D level 10 is about 1.8e-10) ends there; the line
+    counts those apart."""
     import collections
     import paper_2305_15116_gb300 as H
+    if mode is None:
+        mode = H.SOLVE_MIXED
     from inputs.serving import request_stream, coarse_mesh
     reqs = request_stream(n_requests)
     ng_of = {}
@@ -325,7 +330,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
     # warm-up: one small request per dimension (module load, first launches)
     for dim, shape, lev in ((2, (2, 1), 5), (3, (1, 1, 1), 3)):
         c = coarse_mesh(dim, shape)
-        t = sv.submit(c.coords, c.cells, lev, 1, 0.1, rtol=rtol)
+        t = sv.submit(c.coords, c.cells, lev, 1, 0.1, rtol=rtol, mode=mode)
         sv.wait(t, 600)
         sv.release(t)
     pending = collections.deque(reqs)
@@ -345,7 +350,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
             n = ng_of[(q.dim, q.shape, q.level)]
             u = buf(n)
             ts = time.perf_counter() - t0
-            t = sv.submit(c.coords, c.cells, q.level, q.rhs_seed, 0.1, rtol=rtol, max_iter=100, u_out=u)
+            t = sv.submit(c.coords, c.cells, q.level, q.rhs_seed, 0.1, mode=mode, rtol=rtol, max_iter=100, u_out=u)
             if t is None:
                 pool[n].append(u)
                 if not retry:
@@ -387,7 +392,8 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
         "workload": (f"solve server, {n_requests} requests of the synthetic stream (Poisson arrivals 2000/s, seed 3; "
                      "half 2D: 4..64 jittered macro-triangles, levels 5..10; half 3D: 6..384 jittered macro-tets, "
                      f"levels 3..6; lumped-mass RHS with 0.1 N(0,1) Philox noise per request seed); rtol {rtol}, "
-                     "fp32 V(3,3) cycles in float64 refinement; every solution copied to host memory; "
+                     + ("fp32 V(3,3) cycles in float64 refinement" if mode == H.SOLVE_MIXED else
+                        "float64 V(3,3) cycles") + "; every solution copied to host memory; "
                      f"{workers} worker streams, {cap_bytes >> 30} GiB device arena"),
         "solves_per_s": len(lat) / span, "gdofs_solved_per_s": float(np.sum(ngs)) / span / 1e9,
         "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
@@ -398,6 +404,8 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-8):
         "cache_hits": hits, "evictions": st["evictions"], "iterations_mean": float(np.mean(iters)) if iters else None,
         "relres_max": float(np.max(rels)) if rels else None,
         "reached_rtol": bool(rels and max(rels) <= rtol),
+        "reached_rtol_share": float(np.mean(np.asarray(rels) <= rtol)) if rels else None,
+        "stopped_at_float64_floor": int(np.sum(np.asarray(rels) > rtol)) if rels else 0,
     }
 
 
@@ -577,6 +585,10 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_variants and args.serve_requests > 0:
         line["serving"] = serve_workload(args.serve_requests, args.serve_workers)
+        # the same stream with float64 V-cycles: the plain float64 multigrid
+        # the mixed-precision server is compared with
+        line["serving_fp64_cycles"] = serve_workload(args.serve_requests, args.serve_workers,
+                                                     mode=H.SOLVE_F64)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         ng, ts, sample = cpu_oracle_run(5, 1)

@@ -97,18 +97,20 @@ int hyteg_mesh_create(int dim, int64_t n_verts, const double* coords, int64_t n_
  * interface tables and the kernels' work lists.  Allocates a few small device
  * tables with cudaMalloc (size O(cells * levels + interface primitives)),
  * owned by the mesh.  Synchronous.  May be called again with a larger level.
- * 3D levels of at least 2^18 slots with n <= 64 are autotuned here: the slab
+ * 3D levels of at least 2^20 slots with n <= 64 are autotuned here: the slab
  * kernel is timed on two scratch float64 vectors of the level's size (freed
- * before returning) for several work splits per element type, and the
- * fastest split is kept (choices cached per macro count and level for the
- * process; see hyteg_autotune_choice).
+ * before returning) for several work splits (float-float and fp32; native
+ * fp64 takes the float-float choice), and the fastest split is kept (choices
+ * cached per macro count and level for the process; see
+ * hyteg_autotune_choice).  Meshes built by the solve server only take cached
+ * choices: their timings would run among other requests' kernels.
  * Errors: HYTEG_EINVAL (max_level < 0 or > 15), HYTEG_ECUDA, HYTEG_ENOMEM. */
 int hyteg_mesh_refine(hyteg_mesh* mesh, int max_level);
 
 /* The work split the autotuner picked for the 3D slab kernel on `level` and
  * element type `dtype` (HYTEG_F64, HYTEG_F32, HYTEG_F64_IEEE): the number of
  * z-ranges every macro-tetrahedron is cut into, one thread block each; 0 when
- * the level was not autotuned (2D, n > 64, or fewer than 2^18 slots: two
+ * the level was not autotuned (2D, n > 64, or fewer than 2^20 slots: two
  * z-ranges).  Errors: HYTEG_EINVAL (null, dtype), HYTEG_ESTATE (level not
  * refined). */
 int hyteg_autotune_choice(const hyteg_mesh* mesh, int level, int dtype, int* value);

@@ -207,6 +207,10 @@ struct Mesh {
   Solver* solver = nullptr;
   ProblemDev problem;
   DevMem mem;
+  // slab work-split autotuning at refinement: 2 time the candidates on a
+  // cache miss, 1 only take cached choices (meshes built by the solve server,
+  // whose timings would run among other requests' kernels), 0 off
+  int autotune = 2;
 };
 
 // Records the message returned by hyteg_last_error() on this thread.
@@ -220,7 +224,7 @@ std::string build_level(Mesh& m, int level, LevelDev& out);
 // of about equal point counts
 std::vector<int4> slab_work_list(int n, int64_t n_cells, int chunks);
 // Time the slab kernel on this level for several z-range counts per element
-// type and keep the fastest list (levels of at least 2^18 slots; results are
+// type and keep the fastest list (levels of at least 2^20 slots; results are
 // cached per (macro count, level size) for the process).  Synchronous.
 cudaError_t slab3d_autotune(Mesh& m, LevelDev& L);
 void free_level(const Mesh& m, LevelDev& L);
@@ -284,6 +288,9 @@ cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, 
 // raises the slab kernels' shared-memory limit (once per process; before any
 // stream capture)
 cudaError_t slab3d_prepare();
+// the slab kernel over an explicit work list (the autotuner's candidates)
+cudaError_t launch_slab3d_items(int dtype, const LevelDev& L, const int4* items, int n_items, const void* x,
+                                void* y, cudaStream_t s);
 cudaError_t launch_row3d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y, cudaStream_t s);
 cudaError_t build_iface_slots(const Mesh& m, const LevelDev& L, cudaStream_t s);
 cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,

@@ -202,6 +202,7 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
     m.mem.stream = s;
     m.mem.region = region;
     m.mem.region_size = r.est;
+    m.autotune = 1;  // cached work splits only: no timing among other requests' kernels
     rc = hyteg_mesh_refine(e->mesh, r.level);
     if (rc == HYTEG_OK) rc = hyteg_solver_setup(e->mesh, r.level, 3, 3, 2.0 / 3.0);
     std::string perr;

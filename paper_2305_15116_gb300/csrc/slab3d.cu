@@ -24,10 +24,7 @@
 //   z  : p±1, p+M-y (0,1,0), p+M-y-1 (-1,1,0), p-M+y-1 (0,-1,0), p-M+y (1,-1,0)
 //   z+1: p-y (0,0,1), p-y-1 (-1,0,1), p-M (0,-1,1), p-M+1 (1,-1,1)
 //   z-1: p+y (0,0,-1), p+y+1 (1,0,-1), p+M+1 (0,1,-1), p+M (-1,1,-1)
-#include <array>
-#include <map>
 #include <mutex>
-#include <vector>
 
 #include "arith.cuh"
 #include "hyteg_internal.h"
@@ -358,15 +355,6 @@ cudaError_t launch_t(const LevelDev& L, int dt, const void* x, void* y, cudaStre
                         : launch_items<P>(L, L.slabs, L.n_slabs, x, y, s);
 }
 
-cudaError_t launch_list(int dt, const LevelDev& L, const int4* items, int n_items, const void* x, void* y,
-                        cudaStream_t s) {
-  switch (dt) {
-    case 1: return launch_items<ArF64FF>(L, items, n_items, x, y, s);
-    case 2: return launch_items<ArF32>(L, items, n_items, x, y, s);
-    default: return launch_items<ArF64Native>(L, items, n_items, x, y, s);
-  }
-}
-
 }  // namespace
 
 cudaError_t slab3d_prepare() {
@@ -376,95 +364,14 @@ cudaError_t slab3d_prepare() {
   return e;
 }
 
-// ---- autotuner of the slab work split -------------------------------------------
-// How many z-ranges a macro is cut into trades the waves of CTAs over the SMs
-// (which depend on the blocks per SM of each element type) against the
-// per-item cost of loading the first three slices.  On first use of a level
-// size the kernel is timed for each candidate on scratch vectors (the best
-// of three launches each, so that a concurrent workload inflates no
-// candidate in particular) and the fastest list is kept; the choice is
-// cached per (macro count, level, element type) for the process.
-cudaError_t slab3d_autotune(Mesh& m, LevelDev& L) {
-  if (L.n_slabs == 0) return cudaSuccess;
-  const int64_t total = L.slots_per_macro * m.n_cells;
-  if (total < (int64_t(1) << 18)) return cudaSuccess;
-  static std::mutex mu;
-  static std::map<std::array<int64_t, 3>, int> cache;
-  constexpr int kCand[] = {2, 3, 4, 5, 6, 8};
-  void* x = nullptr;
-  void* y = nullptr;
-  cudaStream_t s = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t err = cudaSuccess;
-  auto cleanup = [&] {
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (s) {  // nothing of the timing may still run when the scratch is released
-      cudaStreamSynchronize(s);
-      cudaStreamDestroy(s);
-    }
-    dev_free(m, x);
-    dev_free(m, y);
-  };
-  for (int dt = 1; dt <= 3 && err == cudaSuccess; ++dt) {
-    const std::array<int64_t, 3> key{m.n_cells, L.n, dt};
-    int best = 0;
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      auto it = cache.find(key);
-      if (it != cache.end()) best = it->second;
-    }
-    if (best == 0) {
-      if (!x) {
-        if ((err = dev_alloc(m, &x, sizeof(double) * total)) != cudaSuccess) break;
-        if ((err = dev_alloc(m, &y, sizeof(double) * total)) != cudaSuccess) break;
-        if ((err = dev_zero(m, x, sizeof(double) * total)) != cudaSuccess) break;
-        if ((err = dev_sync(m)) != cudaSuccess) break;
-        if ((err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) break;
-        if ((err = cudaEventCreate(&e0)) != cudaSuccess) break;
-        if ((err = cudaEventCreate(&e1)) != cudaSuccess) break;
-      }
-      float best_ms = 0.0f;
-      for (int c : kCand) {
-        const std::vector<int4> items = slab_work_list(L.n, m.n_cells, c);
-        int4* d_items = nullptr;
-        if ((err = dev_alloc(m, (void**)&d_items, items.size() * sizeof(int4))) != cudaSuccess) break;
-        err = dev_upload(m, d_items, items.data(), items.size() * sizeof(int4));
-        if (err == cudaSuccess) err = dev_sync(m);
-        float ms = 0.0f;
-        for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {  // the first launch warms up
-          if ((err = cudaEventRecord(e0, s)) != cudaSuccess) break;
-          if ((err = launch_list(dt, L, d_items, int(items.size()), x, y, s)) != cudaSuccess) break;
-          if ((err = cudaEventRecord(e1, s)) != cudaSuccess) break;
-          if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
-          float t = 0.0f;
-          if ((err = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
-          if (rep == 1 || (rep > 1 && t < ms)) ms = t;
-        }
-        const cudaError_t ef = cudaStreamSynchronize(s);
-        dev_free(m, d_items);
-        if (err == cudaSuccess) err = ef;
-        if (err != cudaSuccess) break;
-        if (best == 0 || ms < best_ms) {
-          best = c;
-          best_ms = ms;
-        }
-      }
-      if (err != cudaSuccess) break;
-      std::lock_guard<std::mutex> lk(mu);
-      cache[key] = best;
-    }
-    if (best != 2) {  // the default list holds two z-ranges per macro
-      const std::vector<int4> items = slab_work_list(L.n, m.n_cells, best);
-      if ((err = dev_alloc(m, (void**)&L.slabs_dt[dt], items.size() * sizeof(int4))) != cudaSuccess) break;
-      if ((err = dev_upload(m, L.slabs_dt[dt], items.data(), items.size() * sizeof(int4))) != cudaSuccess) break;
-      L.n_slabs_dt[dt] = int(items.size());
-    }
-    L.slab_chunks[dt] = best;
+cudaError_t launch_slab3d_items(int dtype, const LevelDev& L, const int4* items, int n_items, const void* x,
+                                void* y, cudaStream_t s) {
+  switch (dtype) {
+    case 1: return launch_items<ArF64FF>(L, items, n_items, x, y, s);
+    case 2: return launch_items<ArF32>(L, items, n_items, x, y, s);
+    case 3: return launch_items<ArF64Native>(L, items, n_items, x, y, s);
+    default: return cudaErrorInvalidValue;
   }
-  if (err == cudaSuccess) err = dev_sync(m);
-  cleanup();
-  return err;
 }
 
 cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
