@@ -144,77 +144,106 @@ __global__ void k_partial_diff(const double* __restrict__ u, double* __restrict_
 
 // ---- transfers --------------------------------------------------------------
 
-// Per-macro partial of (P^T r) at every coarse slot.
+// One macro's partial of (P^T r) at its coarse point q: the fine value at the
+// coincident point plus half the values at the midpoints of the coarse
+// micro-edges around it (6 in 2D, 14 in 3D), each divided by the number of
+// macros holding a copy of it (a per-macro table by boundary class).
 template <class T, int DIM>
-__global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ bc, const unsigned* __restrict__ lpts_c,
-                           const T* __restrict__ multinv, int nc, int64_t Sc, int64_t Sf, int64_t total) {
+__device__ __forceinline__ T restrict_partial(const T* __restrict__ rf, const T* __restrict__ multinv, int64_t cell,
+                                              const int q[3], int nc, int64_t Sf) {
   constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
   constexpr int ND = DIM == 2 ? 3 : 7;
   const int nf = 2 * nc;
+  const int f[3] = {2 * q[0], 2 * q[1], 2 * q[2]};
+  const T* __restrict__ r = rf + cell * Sf;
+  const T* __restrict__ mi = multinv + cell * NCLS;
+  T acc = r[slotq<DIM>(nf, f)] * mi[pclass<DIM>(nf, f)];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+#pragma unroll
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      int j[3];
+      if (DIM == 2) {
+        j[0] = f[0] + sgn * c_dir2[k][0];
+        j[1] = f[1] + sgn * c_dir2[k][1];
+        j[2] = 0;
+      } else {
+        j[0] = f[0] + sgn * c_dir3[k][0];
+        j[1] = f[1] + sgn * c_dir3[k][1];
+        j[2] = f[2] + sgn * c_dir3[k][2];
+      }
+      if (inside<DIM>(nf, j)) acc += T(0.5) * r[slotq<DIM>(nf, j)] * mi[pclass<DIM>(nf, j)];
+    }
+  }
+  return acc;
+}
+
+// b_c = P^T r_f in one launch: blocks [0, n_if_blocks) take the coarse
+// interface items (each point sums the partials of its copies in ascending
+// macro order and writes every copy; Dirichlet points get 0), the others the
+// macro-interior coarse points (one copy each).  With u_c non-null the launch
+// also performs the coarse level's first weighted-Jacobi sweep from u_c = 0,
+// u_c = omega D^-1 b_c, at every slot.
+template <class T, int DIM>
+__global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ bc,
+                                                        T* __restrict__ uc, const T* __restrict__ dinv, T omega,
+                                                        const unsigned* __restrict__ lpts_c,
+                                                        const T* __restrict__ multinv, const int4* __restrict__ items,
+                                                        const Prim* __restrict__ prims, const Inc* __restrict__ incs,
+                                                        int nc, int64_t Sc, int64_t Sf, int64_t total,
+                                                        int n_if_blocks) {
+  if ((int)blockIdx.x < n_if_blocks) {
+    const int4 it = items[blockIdx.x];
+    const int a = it.z + threadIdx.x;
+    if (a >= it.w) return;
+    const Prim p = prims[it.x];
+    const int b = it.y;
+    int wv[3] = {0, 0, 0};
+    if (p.type == 0) {
+      wv[0] = nc;
+    } else if (p.type == 1) {
+      wv[0] = nc - a;
+      wv[1] = a;
+    } else {
+      wv[0] = nc - a - b;
+      wv[1] = a;
+      wv[2] = b;
+    }
+    auto local = [&](const Inc& inc, int q[3]) {
+      q[0] = q[1] = q[2] = 0;
+      for (int j = 0; j <= p.type; ++j)
+        if (inc.corner[j] >= 1) q[inc.corner[j] - 1] += wv[j];
+    };
+    T acc = T(0);
+    if (!p.boundary) {
+      for (int i = 0; i < p.inc_count; ++i) {
+        const Inc inc = incs[p.inc_begin + i];
+        int q[3];
+        local(inc, q);
+        acc += restrict_partial<T, DIM>(rf, multinv, inc.cell, q, nc, Sf);
+      }
+    }
+    for (int i = 0; i < p.inc_count; ++i) {
+      const Inc inc = incs[p.inc_begin + i];
+      int q[3];
+      local(inc, q);
+      const int64_t sl = (int64_t)inc.cell * Sc + slotq<DIM>(nc, q);
+      bc[sl] = acc;
+      if (uc) uc[sl] = omega * dinv[sl] * acc;
+    }
+    return;
+  }
   const SlotDiv divSc(Sc, total);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)(gridDim.x - n_if_blocks) * blockDim.x;
+  for (int64_t i = (int64_t)(blockIdx.x - n_if_blocks) * blockDim.x + threadIdx.x; i < total; i += stride) {
     const int64_t cell = divSc(i);
     int q[3];
     unpack<DIM>(lpts_c[i - cell * Sc], q);
-    const int f[3] = {2 * q[0], 2 * q[1], 2 * q[2]};
-    const T* __restrict__ r = rf + cell * Sf;
-    const T* __restrict__ mi = multinv + cell * NCLS;
-    T acc = r[slotq<DIM>(nf, f)] * mi[pclass<DIM>(nf, f)];
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-#pragma unroll
-      for (int sgn = -1; sgn <= 1; sgn += 2) {
-        int j[3];
-        if (DIM == 2) {
-          j[0] = f[0] + sgn * c_dir2[k][0];
-          j[1] = f[1] + sgn * c_dir2[k][1];
-          j[2] = 0;
-        } else {
-          j[0] = f[0] + sgn * c_dir3[k][0];
-          j[1] = f[1] + sgn * c_dir3[k][1];
-          j[2] = f[2] + sgn * c_dir3[k][2];
-        }
-        if (inside<DIM>(nf, j)) acc += T(0.5) * r[slotq<DIM>(nf, j)] * mi[pclass<DIM>(nf, j)];
-      }
-    }
+    if (pclass<DIM>(nc, q) != 0) continue;  // macro-boundary point: an interface item's
+    const T acc = restrict_partial<T, DIM>(rf, multinv, cell, q, nc, Sf);
     bc[i] = acc;
+    if (uc) uc[i] = omega * dinv[i] * acc;
   }
-}
-
-// Sum the copies' partials of every interface point in ascending macro order
-// and write the sum to all copies; Dirichlet points get zero.
-template <class T, int DIM>
-__global__ void __launch_bounds__(128) k_iface_sum_zero(T* __restrict__ v, const int4* __restrict__ items,
-                                                        const Prim* __restrict__ prims,
-                                                        const Inc* __restrict__ incs, int n, int64_t S) {
-  const int4 it = items[blockIdx.x];
-  const int a = it.z + threadIdx.x;
-  if (a >= it.w) return;
-  const Prim p = prims[it.x];
-  if (!p.boundary && p.inc_count == 1) return;
-  const int b = it.y;
-  int wv[3] = {0, 0, 0};
-  if (p.type == 0) {
-    wv[0] = n;
-  } else if (p.type == 1) {
-    wv[0] = n - a;
-    wv[1] = a;
-  } else {
-    wv[0] = n - a - b;
-    wv[1] = a;
-    wv[2] = b;
-  }
-  auto slot_of = [&](int i) -> int64_t {
-    const Inc inc = incs[p.inc_begin + i];
-    int q[3] = {0, 0, 0};
-    for (int j = 0; j <= p.type; ++j)
-      if (inc.corner[j] >= 1) q[inc.corner[j] - 1] += wv[j];
-    return (int64_t)inc.cell * S + slotq<DIM>(n, q);
-  };
-  T acc = T(0);
-  if (!p.boundary)
-    for (int i = 0; i < p.inc_count; ++i) acc += v[slot_of(i)];
-  for (int i = 0; i < p.inc_count; ++i) v[slot_of(i)] = acc;
 }
 
 // ---- set-up: inverse diagonals and owner flags ----------------------------------
@@ -365,14 +394,19 @@ __global__ void k_dot_final(const double* __restrict__ partial, int nb, double* 
 // r = b - y at every slot, stored as TO (the correction cycle's right-hand
 // side), and per-block partial sums of r^2 over one copy of every
 // non-Dirichlet DoF (fixed grid and order: deterministic).
+// With u_out non-null it also performs the correction cycle's first sweep
+// from a zero guess: u_out = omega D^-1 (TO)r.
 template <class TO>
-__global__ void k_residual_norm(TO* __restrict__ out, const double* __restrict__ b, const double* __restrict__ y,
+__global__ void k_residual_norm(TO* __restrict__ out, TO* __restrict__ u_out, const TO* __restrict__ dinv, TO omega,
+                                const double* __restrict__ b, const double* __restrict__ y,
                                 const unsigned char* __restrict__ owner, int64_t n, double* __restrict__ partial) {
   __shared__ double sm[THREADS];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double r = b[i] - y[i];
-    out[i] = (TO)r;
+    const TO rt = (TO)r;
+    out[i] = rt;
+    if (u_out) u_out[i] = omega * dinv[i] * rt;
     if (owner[i]) acc += r * r;
   }
   sm[threadIdx.x] = acc;
@@ -420,26 +454,29 @@ struct Vecs<double> {
     if (e_ != cudaSuccess) return e_;      \
   } while (0)
 
+// b_c = P^T r_f on level lf - 1; with u_c non-null also u_c = omega D^-1 b_c
+// (the coarse level's first sweep from a zero guess).
 template <class T>
-cudaError_t restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t s) {
+cudaError_t restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t s, T* uc = nullptr) {
   const Solver& sv = *m.solver;
   const LevelDev& Lc = m.levels[lf - 1];
   const LevelDev& Lf = m.levels[lf];
   const int64_t total = Lc.slots_per_macro * m.n_cells;
   const MgLevel& gc = sv.lv[lf - 1];
+  const int if_blocks = Lc.n_items;
+  const int64_t want = (total + 127) / 128;
+  const int int_blocks = int(want < 152 * 32 ? (want > 0 ? want : 1) : 152 * 32);
+  const T omega = T(sv.omega);
   if (m.dim == 2)
-    k_restrict<T, 2><<<grid_for(total), THREADS, 0, s>>>(rf, bc, gc.lpts, Vecs<T>::multinv(gc), Lc.n,
-                                                          Lc.slots_per_macro, Lf.slots_per_macro, total);
+    k_restrict_fused<T, 2><<<if_blocks + int_blocks, 128, 0, s>>>(rf, bc, uc, Vecs<T>::dinv(gc), omega, gc.lpts,
+                                                                   Vecs<T>::multinv(gc), Lc.items, m.d_prims,
+                                                                   m.d_incs, Lc.n, Lc.slots_per_macro,
+                                                                   Lf.slots_per_macro, total, if_blocks);
   else
-    k_restrict<T, 3><<<grid_for(total), THREADS, 0, s>>>(rf, bc, gc.lpts, Vecs<T>::multinv(gc), Lc.n,
-                                                          Lc.slots_per_macro, Lf.slots_per_macro, total);
-  HY_TRY(cudaGetLastError());
-  if (Lc.n_items > 0) {
-    if (m.dim == 2)
-      k_iface_sum_zero<T, 2><<<Lc.n_items, 128, 0, s>>>(bc, Lc.items, m.d_prims, m.d_incs, Lc.n, Lc.slots_per_macro);
-    else
-      k_iface_sum_zero<T, 3><<<Lc.n_items, 128, 0, s>>>(bc, Lc.items, m.d_prims, m.d_incs, Lc.n, Lc.slots_per_macro);
-  }
+    k_restrict_fused<T, 3><<<if_blocks + int_blocks, 128, 0, s>>>(rf, bc, uc, Vecs<T>::dinv(gc), omega, gc.lpts,
+                                                                   Vecs<T>::multinv(gc), Lc.items, m.d_prims,
+                                                                   m.d_incs, Lc.n, Lc.slots_per_macro,
+                                                                   Lf.slots_per_macro, total, if_blocks);
   return cudaGetLastError();
 }
 
@@ -460,7 +497,10 @@ cudaError_t prolong_add_t(const Mesh& m, int lf, const T* ec, T* uf, cudaStream_
 
 // One V(nu1, nu2) cycle on level l for A u = b (u updated in place).
 template <class T>
-cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s) {
+// first_done: u already holds the first pre-smoothing sweep from a zero guess
+// (u = omega D^-1 b, written by the launch that produced b), so one sweep
+// fewer is run here.
+cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s, bool first_done = false) {
   Solver& sv = *m.solver;
   MgLevel& g = sv.lv[l];
   const int64_t ns = m.levels[l].slots_per_macro * m.n_cells;
@@ -489,11 +529,12 @@ cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s) {
     }
     return cudaSuccess;
   };
+  const int pre = sv.nu1 - (first_done ? 1 : 0);
   if (m.dim == 2 && fused_ok) {
-    HY_TRY(sweeps2d(sv.nu1));
+    HY_TRY(sweeps2d(pre));
     HY_TRY(launch_sweep2d(Vecs<T>::dtype, false, m, L, cur, b, Vecs<T>::dinv(g), sv.omega, r, s));
   } else {
-    for (int it = 0; it < sv.nu1; ++it) {
+    for (int it = 0; it < pre; ++it) {
       HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
       k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
       HY_TRY(cudaGetLastError());
@@ -505,9 +546,13 @@ cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s) {
   MgLevel& gc = sv.lv[l - 1];
   T* bc = Vecs<T>::b(gc);
   T* uc = Vecs<T>::u(gc);
-  HY_TRY(restrict_t<T>(m, l, r, bc, s));
-  HY_TRY(cudaMemsetAsync(uc, 0, sizeof(T) * m.levels[l - 1].slots_per_macro * m.n_cells, s));
-  HY_TRY(vcycle_t<T>(m, l - 1, bc, uc, s));
+  // the restriction also performs the coarse level's first sweep from zero;
+  // level 0 is solved directly and overwrites all of uc
+  const bool first = sv.nu1 >= 1 && l - 1 > 0;
+  HY_TRY(restrict_t<T>(m, l, r, bc, s, first ? uc : nullptr));
+  if (!first && l - 1 > 0)
+    HY_TRY(cudaMemsetAsync(uc, 0, sizeof(T) * m.levels[l - 1].slots_per_macro * m.n_cells, s));
+  HY_TRY(vcycle_t<T>(m, l - 1, bc, uc, s, first));
   HY_TRY(prolong_add_t<T>(m, l, uc, cur, s));
   if (m.dim == 2 && fused_ok) {
     HY_TRY(sweeps2d(sv.nu2));
@@ -558,17 +603,17 @@ cudaError_t mg_prolong_add(const Mesh& m, int lf, int dtype, const void* ec, voi
 // solve only), as do streams that cannot be captured (the legacy default
 // stream).
 template <class T>
-cudaError_t vcycle_own(Mesh& m, int l, cudaStream_t s) {
+cudaError_t vcycle_own(Mesh& m, int l, cudaStream_t s, bool first_done) {
   Solver& sv = *m.solver;
   MgLevel& g = sv.lv[l];
   if (sv.solves == 0 || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
-    return vcycle_t<T>(m, l, Vecs<T>::b(g), Vecs<T>::u(g), s);
+    return vcycle_t<T>(m, l, Vecs<T>::b(g), Vecs<T>::u(g), s, first_done);
   std::vector<cudaGraphExec_t>& ge = sizeof(T) == 4 ? sv.graph32 : sv.graph64;
   if ((int)ge.size() <= l) ge.resize(l + 1, nullptr);
   if (!ge[l]) {
     cudaGraph_t graph = nullptr;
     HY_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const cudaError_t e = vcycle_t<T>(m, l, Vecs<T>::b(g), Vecs<T>::u(g), s);
+    const cudaError_t e = vcycle_t<T>(m, l, Vecs<T>::b(g), Vecs<T>::u(g), s, first_done);
     const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -623,7 +668,9 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
   constexpr double kFastUntil = 1e-6;
   bool fast = true;
   // r = b - A u goes straight into the correction cycle's right-hand side
-  // (fp32 for HYTEG_SOLVE_MIXED), its norm from the same pass
+  // (fp32 for HYTEG_SOLVE_MIXED), its norm from the same pass, and the
+  // cycle's first sweep from a zero correction with it
+  const bool first = sv.nu1 >= 1 && l > 0;
   auto residual = [&](bool ff, double* out) -> cudaError_t {
     if (ff) {
       const char* what = "";
@@ -632,9 +679,11 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
       HY_TRY(accurate_apply(m, l, u, g.y64, s));
     }
     if (mode == 2)
-      k_residual_norm<float><<<RED_BLOCKS, THREADS, 0, s>>>(g.b32, b, g.y64, g.owner, ns, sv.red);
+      k_residual_norm<float><<<RED_BLOCKS, THREADS, 0, s>>>(g.b32, first ? g.u32 : nullptr, g.dinv32,
+                                                             (float)sv.omega, b, g.y64, g.owner, ns, sv.red);
     else
-      k_residual_norm<double><<<RED_BLOCKS, THREADS, 0, s>>>(g.b64, b, g.y64, g.owner, ns, sv.red);
+      k_residual_norm<double><<<RED_BLOCKS, THREADS, 0, s>>>(g.b64, first ? g.u64 : nullptr, g.dinv64, sv.omega, b,
+                                                              g.y64, g.owner, ns, sv.red);
     HY_TRY(cudaGetLastError());
     k_dot_final<<<1, THREADS, 0, s>>>(sv.red, RED_BLOCKS, sv.red + RED_BLOCKS);
     HY_TRY(cudaGetLastError());
@@ -667,13 +716,13 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
     }
     prev = rel;
     if (mode == 2) {
-      HY_TRY(cudaMemsetAsync(g.u32, 0, sizeof(float) * ns, s));
-      HY_TRY(vcycle_own<float>(m, l, s));
+      if (!first) HY_TRY(cudaMemsetAsync(g.u32, 0, sizeof(float) * ns, s));
+      HY_TRY(vcycle_own<float>(m, l, s, first));
       k_add_f32<<<grid_for(ns), THREADS, 0, s>>>(u, g.u32, ns);
       HY_TRY(cudaGetLastError());
     } else {
-      HY_TRY(cudaMemsetAsync(g.u64, 0, sizeof(double) * ns, s));
-      HY_TRY(vcycle_own<double>(m, l, s));
+      if (!first) HY_TRY(cudaMemsetAsync(g.u64, 0, sizeof(double) * ns, s));
+      HY_TRY(vcycle_own<double>(m, l, s, first));
       k_add_f64<<<grid_for(ns), THREADS, 0, s>>>(u, g.u64, ns);
       HY_TRY(cudaGetLastError());
     }
