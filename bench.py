@@ -213,6 +213,47 @@ def timed_applies(w, steps, warmup, stream, barrier=None):
                 t0=t0, t1=t1)
 
 
+def batched_small(w, count, stream, reps=50):
+    """`count` products of the small mesh (distinct vector pairs, as from as
+    many requests): one hyteg_apply each against one hyteg_apply_batch for
+    all of them, timed with CUDA events on the launching stream."""
+    import torch
+    import paper_2305_15116_gb300 as H
+    M, L = w["M"], w["L"]
+    g = torch.Generator(device="cpu").manual_seed(7)
+    xs = [torch.rand(w["ns"], generator=g, dtype=torch.float64).to(w["xs"].device) for _ in range(count)]
+    ys = [torch.empty_like(x) for x in xs]
+    out = {}
+    with torch.cuda.stream(stream):
+        for mode in ("one launch per product", "hyteg_apply_batch"):
+            def run():
+                if mode == "hyteg_apply_batch":
+                    H.apply_batch([M] * count, [L] * count, xs, ys, stream=stream)
+                else:
+                    for x, y in zip(xs, ys):
+                        M.apply_raw(L, H.F64, x.data_ptr(), y.data_ptr(), stream.cuda_stream)
+            for _ in range(3):
+                run()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            us = 1e3 * e0.elapsed_time(e1) / reps
+            out[mode] = {"us_per_batch": us, "GDoF_per_s": count * w["ng"] / (us * 1e-6) / 1e9}
+    # the two agree bit for bit
+    ref = [torch.empty_like(x) for x in xs]
+    for x, r in zip(xs, ref):
+        M.apply(L, x, r, stream=stream)
+    H.apply_batch([M] * count, [L] * count, xs, ys, stream=stream)
+    torch.cuda.synchronize()
+    out["bitwise_equal"] = all(torch.equal(a, b) for a, b in zip(ys, ref))
+    out["workload"] = f"{count} products on the 2-macro level-7 mesh (16,641 DoFs each), float64 data"
+    return out
+
+
 def interior_bytes(w):
     """Algorithmic bytes of one launch of the dominant kernel: every slot of
     every macro is read once and written once (the 2D apply writes its
@@ -577,6 +618,7 @@ def main():
         line["latency_small"] = {"workload": describe("square2_L7", v["ng"], v["ns"]),
                                  "us_per_apply": 1e3 * rv["total_ms"] / 200,
                                  "dtype": "f64 data, float-float arithmetic"}
+        line["batched_small"] = batched_small(v, 64, stream)
         del v
 
     if rank == 0 and world == 1 and not args.no_variants:

@@ -146,7 +146,21 @@ int hyteg_dof_map(const hyteg_mesh* mesh, int level, int64_t* global_id);
 int hyteg_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y,
                 void* stream);
 
-/* hyteg_apply with CUDA events (cudaEvent_t as void*, each may be NULL)
+/* y_i = A_i x_i for `count` independent products (meshes[i] on level
+ * levels[i], device vectors xs[i] -> ys[i], all of element type `dtype`):
+ * the 2D products run together, up to 64 meshes per launch of one kernel
+ * whose blocks walk the combined work list of every mesh's tiles and
+ * interface items (one launch for many small requests instead of one each);
+ * 3D products are launched one after another.  Every y_i is bitwise the
+ * result of hyteg_apply on that product.  The meshes may repeat (several
+ * vectors on one mesh).  Asynchronous on `stream`, allocation-free.
+ * Errors: HYTEG_EINVAL (count < 0, NULL arrays or vectors, x_i overlapping
+ * y_i, dtype), HYTEG_ESTATE (a level not refined), HYTEG_ECUDA; every entry
+ * is validated before the first launch. */
+int hyteg_apply_batch(const hyteg_mesh* const* meshes, const int* levels, int dtype, const void* const* xs,
+                      void* const* ys, int count, void* stream);
+
+/* hyteg_apply with CUDA events/* hyteg_apply with CUDA events (cudaEvent_t as void*, each may be NULL)
  * recorded on `stream` before the macro-interior kernel (ev_begin), between
  * it and the interface kernel (ev_mid) and after the interface kernel
  * (ev_end), so a caller can time each kernel on the launching stream.  The

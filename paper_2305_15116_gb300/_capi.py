@@ -30,6 +30,10 @@ lib.hyteg_mesh_destroy.argtypes = [ctypes.c_void_p]
 lib.hyteg_mesh_destroy.restype = None
 lib.hyteg_autotune_choice.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
 lib.hyteg_autotune_choice.restype = ctypes.c_int
+lib.hyteg_apply_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                  ctypes.c_void_p]
+lib.hyteg_apply_batch.restype = ctypes.c_int
 lib.hyteg_num_slots.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p, c_i64p]
 lib.hyteg_num_slots.restype = ctypes.c_int
 lib.hyteg_dof_map.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p]

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/hyteg.h"
 #include "hyteg_internal.h"
@@ -193,6 +194,49 @@ int hyteg_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* 
 
 int hyteg_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream) {
   return hyteg_apply_timed(mesh, level, dtype, x, y, stream, nullptr, nullptr, nullptr);
+}
+
+int hyteg_apply_batch(const hyteg_mesh* const* meshes, const int* levels, int dtype, const void* const* xs,
+                      void* const* ys, int count, void* stream) {
+  if (count < 0) return fail(HYTEG_EINVAL, "count < 0");
+  if (count == 0) return HYTEG_OK;
+  if (!meshes || !levels || !xs || !ys) return fail(HYTEG_EINVAL, "NULL array");
+  if (!valid_dtype(dtype)) return fail(HYTEG_EINVAL, "unknown dtype");
+  // validate everything before the first launch
+  for (int i = 0; i < count; ++i) {
+    if (int r = check_level(meshes[i], levels[i])) return r;
+    if (!xs[i] || !ys[i]) return fail(HYTEG_EINVAL, "x or y is NULL (entry " + std::to_string(i) + ")");
+    const hyteg::Mesh& m = meshes[i]->m;
+    const size_t bytes = size_t(m.n_cells) * size_t(hyteg::slots_per_macro(m.dim, levels[i])) * elem_size(dtype);
+    const char* xb = static_cast<const char*>(xs[i]);
+    const char* yb = static_cast<const char*>(ys[i]);
+    if (xb < yb + bytes && yb < xb + bytes)
+      return fail(HYTEG_EINVAL, "x and y overlap (entry " + std::to_string(i) + ")");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<const hyteg::Mesh*> m2;
+  std::vector<int> l2;
+  std::vector<const void*> x2;
+  std::vector<void*> y2;
+  for (int i = 0; i < count; ++i) {
+    const hyteg::Mesh& m = meshes[i]->m;
+    if (m.dim == 2) {
+      m2.push_back(&m);
+      l2.push_back(levels[i]);
+      x2.push_back(xs[i]);
+      y2.push_back(ys[i]);
+    } else {  // 3D meshes: their own launches, in order
+      const char* what = "";
+      const cudaError_t e = hyteg::launch_apply(m, levels[i], dtype, xs[i], ys[i], s, nullptr, &what);
+      if (e != cudaSuccess) return cuda_fail(e, what);
+    }
+  }
+  if (!m2.empty()) {
+    const cudaError_t e = hyteg::launch_apply2d_batch(dtype, m2.data(), l2.data(), x2.data(), y2.data(),
+                                                      int(m2.size()), s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched 2D apply kernel");
+  }
+  return HYTEG_OK;
 }
 
 int hyteg_apply_host(hyteg_mesh* mesh, int level, int dtype, const void* x_host, void* y_host, void* stream) {

@@ -279,6 +279,9 @@ cudaError_t mg_solve(Mesh& m, int level, int mode, const double* b, double* u, d
 // ---- kernels ----------------------------------------------------------------
 // dtype: 1 = f64 (float-float arithmetic), 2 = f32, 3 = f64 native.
 cudaError_t launch_apply2d(int dtype, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s);
+// 2D applies of several meshes (levels[i], xs[i] -> ys[i]), up to 64 meshes per launch
+cudaError_t launch_apply2d_batch(int dtype, const Mesh* const* meshes, const int* levels, const void* const* xs,
+                                 void* const* ys, int count, cudaStream_t s);
 // 2D fused sweeps over u: out = u + omega dinv (b - A u) (jacobi) or
 // out = b - A u; out must not overlap u.  dtype 1 (float64, float-float
 // apply) or 2 (fp32).

@@ -186,30 +186,30 @@ struct Thr2 {
   static constexpr int value = THREADS2D;
 };
 
+// The work of one block of an apply / sweep launch over one mesh (block =
+// the block's index within that mesh's part of the launch).
 template <class P, int MODE>
-__global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename P::T* __restrict__ x,
-                                                          typename P::T* __restrict__ y,
-                                                          const int4* __restrict__ tiles, int n_tiles,
-                                                          int64_t n_warps, int64_t S, int n, StencilPtr st,
-                                                          const int4* __restrict__ items, int n_items,
-                                                          const Prim* __restrict__ prims,
-                                                          const Inc* __restrict__ incs, int n_if_blocks,
-                                                          ModeArgs md) {
+__device__ __forceinline__ void apply2d_block(int block, const typename P::T* __restrict__ x,
+                                              typename P::T* __restrict__ y, const int4* __restrict__ tiles,
+                                              int n_tiles, int64_t n_warps, int64_t S, int n, const StencilPtr& st,
+                                              const int4* __restrict__ items, int n_items,
+                                              const Prim* __restrict__ prims, const Inc* __restrict__ incs,
+                                              int n_if_blocks, const ModeArgs& md,
+                                              typename P::T (*ring_all)[RING][32][2],
+                                              typename P::T (*ringb_all)[RING][32][2]) {
   using T = typename P::T;
   constexpr int THR = Thr2<MODE>::value;
   constexpr bool SWEEP = MODE != MODE_APPLY;
   static_assert(!SWEEP || sizeof(T) == 4, "the sweep modes are built for fp32");
-  __shared__ T ring_all[THR / 32][RING][32][2];
-  __shared__ T ringb_all[SWEEP ? THR / 32 : 1][SWEEP ? RING : 1][32][2];
-  if ((int)blockIdx.x < n_if_blocks) {
-    const int item = (THR / 128) * (int)blockIdx.x + (int)(threadIdx.x >> 7);
+  if (block < n_if_blocks) {
+    const int item = (THR / 128) * block + (int)(threadIdx.x >> 7);
     if (item >= n_items) return;
     const int4 it = items[item];
     const int a = it.z + (int)(threadIdx.x & 127);
     if (a < it.w) iface2d_point<MODE, T>(x, y, it, a, prims, incs, n, S, st, md);
     return;
   }
-  const int64_t warp = ((int64_t)(blockIdx.x - n_if_blocks) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warp = ((int64_t)(block - n_if_blocks) * blockDim.x + threadIdx.x) >> 5;
   if (warp >= n_warps) return;  // whole warps leave together
   const int lane = threadIdx.x & 31;
   T(*ring)[32][2] = ring_all[threadIdx.x >> 5];
@@ -312,6 +312,67 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
 }
 
 template <class P, int MODE>
+__global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename P::T* __restrict__ x,
+                                                          typename P::T* __restrict__ y,
+                                                          const int4* __restrict__ tiles, int n_tiles,
+                                                          int64_t n_warps, int64_t S, int n, StencilPtr st,
+                                                          const int4* __restrict__ items, int n_items,
+                                                          const Prim* __restrict__ prims,
+                                                          const Inc* __restrict__ incs, int n_if_blocks,
+                                                          ModeArgs md) {
+  using T = typename P::T;
+  constexpr int THR = Thr2<MODE>::value;
+  constexpr bool SWEEP = MODE != MODE_APPLY;
+  __shared__ T ring_all[THR / 32][RING][32][2];
+  __shared__ T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
+  apply2d_block<P, MODE>((int)blockIdx.x, x, y, tiles, n_tiles, n_warps, S, n, st, items, n_items, prims, incs,
+                         n_if_blocks, md, ring_all, ringb_all);
+}
+
+// ---- batched apply: many meshes in one launch ------------------------------------
+// Each mesh of the batch owns a consecutive range of the launch's blocks (its
+// interface blocks, then its tile blocks, exactly as in its own launch); a
+// block finds its mesh by binary search over the ranges.  The descriptors
+// travel as a kernel parameter, so the launch allocates nothing.
+struct Apply2dDesc {
+  const void* x;
+  void* y;
+  const int4* tiles;
+  const int4* items;
+  const Prim* prims;
+  const Inc* incs;
+  StencilPtr st;
+  int64_t n_warps;
+  int64_t S;
+  int n_tiles, n, n_items, n_if_blocks;
+  int block_begin;  // first block of this mesh in the launch
+};
+constexpr int BATCH2D = 64;  // meshes per launch (the parameter block stays below 8 KB)
+struct Apply2dBatch {
+  Apply2dDesc d[BATCH2D];
+  int count;
+};
+
+template <class P>
+__global__ void __launch_bounds__(THREADS2D) k_interior2d_batch(const __grid_constant__ Apply2dBatch b) {
+  using T = typename P::T;
+  __shared__ T ring_all[THREADS2D / 32][RING][32][2];
+  int lo = 0, hi = b.count - 1;  // the last mesh whose range starts at or before this block
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.d[mid].block_begin <= (int)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const Apply2dDesc& d = b.d[lo];
+  const ModeArgs md{nullptr, nullptr, 0.0};
+  apply2d_block<P, MODE_APPLY>((int)blockIdx.x - d.block_begin, static_cast<const T*>(d.x), static_cast<T*>(d.y),
+                               d.tiles, d.n_tiles > 0 ? d.n_tiles : 1, d.n_warps, d.S, d.n, d.st, d.items,
+                               d.n_items, d.prims, d.incs, d.n_if_blocks, md, ring_all, ring_all);
+}
+
+template <class P, int MODE>
 cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s, const ModeArgs& md) {
   const int64_t n_warps = (int64_t)L.n_tiles * m.n_cells;
   const int threads = Thr2<MODE>::value;
@@ -324,6 +385,46 @@ cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cud
       (const typename P::T*)x, (typename P::T*)y, L.tiles, L.n_tiles > 0 ? L.n_tiles : 1, n_warps,
       L.slots_per_macro, L.n, st, L.items, L.n_items, m.d_prims, m.d_incs, if_blocks, md);
   return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const void* const* xs, void* const* ys,
+                           int count, cudaStream_t s) {
+  Apply2dBatch b;
+  for (int i0 = 0; i0 < count; i0 += BATCH2D) {
+    b.count = 0;
+    int blocks = 0;
+    for (int i = i0; i < count && i < i0 + BATCH2D; ++i) {
+      const Mesh& m = *meshes[i];
+      const LevelDev& L = m.levels[levels[i]];
+      const int64_t n_warps = (int64_t)L.n_tiles * m.n_cells;
+      const int64_t int_blocks = (n_warps * 32 + THREADS2D - 1) / THREADS2D;
+      const int if_blocks = (L.n_items + THREADS2D / 128 - 1) / (THREADS2D / 128);
+      if (int_blocks + if_blocks == 0) continue;
+      if ((int64_t)blocks + int_blocks + if_blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
+      Apply2dDesc& d = b.d[b.count++];
+      d.x = xs[i];
+      d.y = ys[i];
+      d.tiles = L.tiles;
+      d.items = L.items;
+      d.prims = m.d_prims;
+      d.incs = m.d_incs;
+      d.st = StencilPtr{L.st64, L.st32, L.st_hi, L.st_lo};
+      d.n_warps = n_warps;
+      d.S = L.slots_per_macro;
+      d.n_tiles = L.n_tiles;
+      d.n = L.n;
+      d.n_items = L.n_items;
+      d.n_if_blocks = if_blocks;
+      d.block_begin = blocks;
+      blocks += int(int_blocks + if_blocks);
+    }
+    if (b.count == 0) continue;
+    k_interior2d_batch<P><<<blocks, THREADS2D, 0, s>>>(b);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -344,6 +445,16 @@ cudaError_t launch_sweep2d(int dtype, bool jacobi, const Mesh& m, const LevelDev
   switch (dtype) {
     case 2:
       return jacobi ? launch<ArF32, MODE_JACOBI>(m, L, u, out, s, md) : launch<ArF32, MODE_RESIDUAL>(m, L, u, out, s, md);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_apply2d_batch(int dtype, const Mesh* const* meshes, const int* levels, const void* const* xs,
+                                 void* const* ys, int count, cudaStream_t s) {
+  switch (dtype) {
+    case 1: return launch_batch_t<ArF64FF>(meshes, levels, xs, ys, count, s);
+    case 2: return launch_batch_t<ArF32>(meshes, levels, xs, ys, count, s);
+    case 3: return launch_batch_t<ArF64Native>(meshes, levels, xs, ys, count, s);
     default: return cudaErrorInvalidValue;
   }
 }

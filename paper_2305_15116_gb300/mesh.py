@@ -248,3 +248,32 @@ class Mesh:
         C.check(C.lib.hyteg_p2_apply_timed(self._h, level, dtype, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
                                            ctypes.c_void_p(stream_ptr), ctypes.c_void_p(ev_begin),
                                            ctypes.c_void_p(ev_mid), ctypes.c_void_p(ev_end)), "hyteg_p2_apply_timed")
+
+
+def apply_batch(meshes, levels, xs, ys, ieee: bool = False, stream=None):
+    """ys[i] = A_i xs[i] for several (mesh, level) products in as few launches
+    as possible: the 2D ones share one kernel launch per 64 meshes.  All
+    vectors are contiguous CUDA tensors of one dtype; returns ys."""
+    n = len(meshes)
+    if not (len(levels) == len(xs) == len(ys) == n):
+        raise ValueError("meshes, levels, xs and ys must have the same length")
+    if n == 0:
+        return ys
+    dt = xs[0].dtype
+    for M, lev, x, y in zip(meshes, levels, xs, ys):
+        if not (x.is_cuda and y.is_cuda) or x.dtype != dt or y.dtype != dt:
+            raise ValueError("all vectors must be CUDA tensors of one dtype")
+        if not (x.is_contiguous() and y.is_contiguous()):
+            raise ValueError("vectors must be contiguous")
+        ns, _ = M.num_slots(lev)
+        if x.numel() != ns or y.numel() != ns:
+            raise ValueError(f"vectors of level {lev} must have {ns} elements")
+    code = Mesh._dtype_code(xs[0], ieee)
+    hs = (ctypes.c_void_p * n)(*[M._h.value if isinstance(M._h, ctypes.c_void_p) else M._h for M in meshes])
+    ls = (ctypes.c_int * n)(*levels)
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+    C.check(C.lib.hyteg_apply_batch(hs, ls, code, xp, yp, n, ctypes.c_void_p(_stream_ptr(stream))),
+            "hyteg_apply_batch")
+    return ys
+

@@ -188,3 +188,63 @@ def test_apply_host_batch_matches_single_applies(cuda):
             M.apply(L, xd, yd)
             torch.cuda.synchronize()
             assert torch.equal(yd.cpu(), ys[i])
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_apply_batch_is_bitwise_the_single_applies(cuda, kind):
+    """hyteg_apply_batch: 70 products (two launches of the batched 2D kernel)
+    on meshes of 2, 8 and 32 macros at levels 0..7, vectors repeating a mesh,
+    and 3D products in between; every output equals that product's own
+    hyteg_apply bit for bit (outputs start as NaN)."""
+    import torch
+    from inputs import unit_cube_kuhn_mesh
+    H = _lib()
+    dt = torch.float32 if kind == "f32" else torch.float64
+    ieee = kind == "f64_ieee"
+    c2 = [unit_square_mesh(1, 0.0, 0), unit_square_mesh(2, 0.15, 1), unit_square_mesh(4, 0.15, 0)]
+    m2 = [H.Mesh(c.coords, c.cells).refine(7) for c in c2]
+    c3 = unit_cube_kuhn_mesh(1, 0.1, 0)
+    m3 = H.Mesh(c3.coords, c3.cells).refine(3)
+    rng = np.random.default_rng(5)
+    meshes, levels = [], []
+    for i in range(70):
+        if i % 23 == 11:
+            meshes.append(m3)
+            levels.append(int(rng.integers(0, 4)))
+        else:
+            meshes.append(m2[int(rng.integers(0, 3))])
+            levels.append(int(rng.integers(0, 8)))
+    xs, ys, refs = [], [], []
+    for i, (M, lev) in enumerate(zip(meshes, levels)):
+        ns, _ = M.num_slots(lev)
+        x = torch.from_numpy(random_vector(ns, 100 + i)).to("cuda", dt)
+        xs.append(x)
+        ys.append(torch.full_like(x, float("nan")))
+        r = torch.full_like(x, float("nan"))
+        M.apply(lev, x, r, ieee=ieee)
+        refs.append(r)
+    H.apply_batch(meshes, levels, xs, ys, ieee=ieee)
+    torch.cuda.synchronize()
+    for i in range(70):
+        assert torch.equal(ys[i], refs[i]), (i, levels[i])
+
+
+def test_apply_batch_errors(cuda):
+    import torch
+    H = _lib()
+    coarse = unit_square_mesh(2, 0.1, 0)
+    M = H.Mesh(coarse.coords, coarse.cells).refine(3)
+    ns, _ = M.num_slots(3)
+    x = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(H.HytegError) as e:
+        H.apply_batch([M, M], [3, 3], [x, x], [y, x])
+    assert e.value.code == -1  # x and y overlap in the second entry
+    ns4, _ = M.num_slots(4)
+    x4 = torch.zeros(ns4, dtype=torch.float64, device="cuda")
+    with pytest.raises(H.HytegError) as e:
+        H.apply_batch([M], [4], [x4], [torch.zeros_like(x4)])
+    assert e.value.code == -5  # level not refined
+    with pytest.raises(ValueError):
+        H.apply_batch([M], [3, 3], [x], [y])
+    assert H.apply_batch([], [], [], []) == []
