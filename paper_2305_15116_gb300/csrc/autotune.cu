@@ -54,8 +54,19 @@ cudaError_t slab3d_autotune(Mesh& m, LevelDev& L) {
     if (best == 0 && m.autotune < 2) continue;  // lookup only: the default split
     if (best == 0) {
       if (!x) {
-        if ((err = dev_alloc(m, &x, sizeof(double) * total)) != cudaSuccess) break;
-        if ((err = dev_alloc(m, &y, sizeof(double) * total)) != cudaSuccess) break;
+        // no room for the scratch vectors: keep the default split
+        void* p = nullptr;
+        if (dev_alloc(m, &p, sizeof(double) * total) != cudaSuccess) {
+          cudaGetLastError();
+          break;
+        }
+        x = p;
+        p = nullptr;
+        if (dev_alloc(m, &p, sizeof(double) * total) != cudaSuccess) {
+          cudaGetLastError();
+          break;  // x is released below
+        }
+        y = p;
         if ((err = dev_zero(m, x, sizeof(double) * total)) != cudaSuccess) break;
         if ((err = dev_sync(m)) != cudaSuccess) break;
         if ((err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) break;
