@@ -213,6 +213,31 @@ def timed_applies(w, steps, warmup, stream, barrier=None):
                 t0=t0, t1=t1)
 
 
+def graph_replay_us(w, reps, stream):
+    """Mean device time of one apply when it is replayed from a CUDA graph
+    (the library's apply allocates nothing and never synchronises, so it can
+    be captured)."""
+    import torch
+    M, L, code = w["M"], w["L"], w["code"]
+    xp, yp = w["xs"].data_ptr(), w["ys"].data_ptr()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        M.apply_raw(L, code, xp, yp, stream.cuda_stream)  # warm-up outside the capture
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            M.apply_raw(L, code, xp, yp, torch.cuda.current_stream().cuda_stream)
+        for _ in range(5):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+    return 1e3 * e0.elapsed_time(e1) / reps
+
+
 def batched_small(w, count, stream, reps=50):
     """`count` products of the small mesh (distinct vector pairs, as from as
     many requests): one hyteg_apply each against one hyteg_apply_batch for
@@ -617,7 +642,11 @@ def main():
         rv = timed_applies(v, 200, args.warmup, stream)
         line["latency_small"] = {"workload": describe("square2_L7", v["ng"], v["ns"]),
                                  "us_per_apply": 1e3 * rv["total_ms"] / 200,
-                                 "dtype": "f64 data, float-float arithmetic"}
+                                 "us_per_apply_graph_replay": graph_replay_us(v, 200, stream),
+                                 "dtype": "f64 data, float-float arithmetic",
+                                 "note": "us_per_apply: back-to-back hyteg_apply_timed calls from Python (the host "
+                                         "loop bounds it); graph replay: one apply captured in a CUDA graph and "
+                                         "replayed, the device-side time per apply"}
         line["batched_small"] = batched_small(v, 64, stream)
         del v
 

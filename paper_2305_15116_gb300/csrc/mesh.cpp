@@ -426,8 +426,27 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   }
 
   // ---- 2D macro-interior work list: strips of columns x chunks of rows ----
-  // a warp loads 64 consecutive columns and writes the 62 inner ones
-  constexpr int TW2 = 62, TH = 64;
+  // a warp loads 64 consecutive columns and writes the 62 inner ones.  A warp
+  // walks its rows one after another, so a level with few tiles would run
+  // few long serial walks: the row chunk shrinks from 64 rows (8 at least)
+  // until the level has four warps per SM, which keeps small applies and the
+  // multigrid's coarse sweeps short.
+  constexpr int TW2 = 62;
+  int TH = 64;
+  if (d == 2) {
+    auto n_warps = [&](int th) {
+      int64_t w = 0;
+      for (int x0 = 1; x0 <= n - 2; x0 += TW2) w += (n - 1 - x0 + th - 1) / th;
+      return w * m.n_cells;
+    };
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m.device >= 0 ? m.device : 0) != cudaSuccess ||
+        sms <= 0) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    while (TH > 8 && n_warps(TH) < 4 * int64_t(sms)) TH /= 2;
+  }
   std::vector<int4> tiles;
   if (d == 2) {
     for (int x0 = 1; x0 <= n - 2; x0 += TW2) {
