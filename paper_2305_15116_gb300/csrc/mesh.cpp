@@ -429,7 +429,7 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   // a warp loads 64 consecutive columns and writes the 62 inner ones.  A warp
   // walks its rows one after another, so a level with few tiles would run
   // few long serial walks: the row chunk shrinks from 64 rows (8 at least)
-  // until the level has four warps per SM, which keeps small applies and the
+  // until the level has 16 warps per SM, which keeps small applies and the
   // multigrid's coarse sweeps short.
   constexpr int TW2 = 62;
   int TH = 64;
@@ -445,7 +445,7 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
       cudaGetLastError();
       sms = 152;
     }
-    while (TH > 8 && n_warps(TH) < 4 * int64_t(sms)) TH /= 2;
+    while (TH > 8 && n_warps(TH) < 16 * int64_t(sms)) TH /= 2;
   }
   std::vector<int4> tiles;
   if (d == 2) {
