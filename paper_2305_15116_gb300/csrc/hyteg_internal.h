@@ -40,6 +40,8 @@ struct LevelDev {
   // macro-interior work list: int4 (x0, y0, y1, z)
   int4* tiles = nullptr;
   int n_tiles = 0;                 // per macro
+  int4* tiles32 = nullptr;         // the fp32 kernels' list (shorter row chunks)
+  int n_tiles32 = 0;               // per macro
   // interface work list: int4 (prim, b, a0, a1)
   int4* items = nullptr;
   int n_items = 0;

@@ -374,7 +374,10 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d_batch(const __grid_con
 
 template <class P, int MODE>
 cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s, const ModeArgs& md) {
-  const int64_t n_warps = (int64_t)L.n_tiles * m.n_cells;
+  const bool f32 = sizeof(typename P::T) == 4;
+  const int4* tiles = f32 ? L.tiles32 : L.tiles;
+  const int n_tiles = f32 ? L.n_tiles32 : L.n_tiles;
+  const int64_t n_warps = (int64_t)n_tiles * m.n_cells;
   const int threads = Thr2<MODE>::value;
   const int64_t int_blocks = (n_warps * 32 + threads - 1) / threads;
   const int per = threads / 128;  // interface items per block
@@ -382,7 +385,7 @@ cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cud
   if (int_blocks + if_blocks == 0) return cudaSuccess;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
   k_interior2d<P, MODE><<<(unsigned)(int_blocks + if_blocks), threads, 0, s>>>(
-      (const typename P::T*)x, (typename P::T*)y, L.tiles, L.n_tiles > 0 ? L.n_tiles : 1, n_warps,
+      (const typename P::T*)x, (typename P::T*)y, tiles, n_tiles > 0 ? n_tiles : 1, n_warps,
       L.slots_per_macro, L.n, st, L.items, L.n_items, m.d_prims, m.d_incs, if_blocks, md);
   return cudaGetLastError();
 }
@@ -397,7 +400,9 @@ cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const v
     for (int i = i0; i < count && i < i0 + BATCH2D; ++i) {
       const Mesh& m = *meshes[i];
       const LevelDev& L = m.levels[levels[i]];
-      const int64_t n_warps = (int64_t)L.n_tiles * m.n_cells;
+      const bool f32 = sizeof(typename P::T) == 4;
+      const int n_tiles = f32 ? L.n_tiles32 : L.n_tiles;
+      const int64_t n_warps = (int64_t)n_tiles * m.n_cells;
       const int64_t int_blocks = (n_warps * 32 + THREADS2D - 1) / THREADS2D;
       const int if_blocks = (L.n_items + THREADS2D / 128 - 1) / (THREADS2D / 128);
       if (int_blocks + if_blocks == 0) continue;
@@ -405,14 +410,14 @@ cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const v
       Apply2dDesc& d = b.d[b.count++];
       d.x = xs[i];
       d.y = ys[i];
-      d.tiles = L.tiles;
+      d.tiles = f32 ? L.tiles32 : L.tiles;
       d.items = L.items;
       d.prims = m.d_prims;
       d.incs = m.d_incs;
       d.st = StencilPtr{L.st64, L.st32, L.st_hi, L.st_lo};
       d.n_warps = n_warps;
       d.S = L.slots_per_macro;
-      d.n_tiles = L.n_tiles;
+      d.n_tiles = n_tiles;
       d.n = L.n;
       d.n_items = L.n_items;
       d.n_if_blocks = if_blocks;

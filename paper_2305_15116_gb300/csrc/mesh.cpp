@@ -315,6 +315,7 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.st_hi);
   dev_free(m, L.st_lo);
   dev_free(m, L.tiles);
+  dev_free(m, L.tiles32);
   dev_free(m, L.items);
   dev_free(m, L.slabs);
   for (int t = 0; t < 4; ++t) dev_free(m, L.slabs_dt[t]);
@@ -425,41 +426,46 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
     stl[i] = float(st[i] - double(sth[i]));
   }
 
-  // ---- 2D macro-interior work list: strips of columns x chunks of rows ----
+  // ---- 2D macro-interior work lists: strips of columns x chunks of rows ----
   // a warp loads 64 consecutive columns and writes the 62 inner ones.  A warp
   // walks its rows one after another, so a level with few tiles would run
-  // few long serial walks: the row chunk shrinks from 64 rows (8 at least)
-  // until the level has 16 warps per SM, which keeps small applies and the
-  // multigrid's coarse sweeps short.
+  // few long serial walks: the row chunk shrinks from its maximum (8 rows at
+  // least) until the level has 16 warps per SM, which keeps small applies
+  // and the multigrid's coarse sweeps short.  Maximum chunk: 64 rows for the
+  // float64 kernels, 16 for fp32 (measured at level 11, 32 macros: float-
+  // float flat within 1 % from 16 to 64 rows, fp32 0.117 ms at 64 rows, 0.109
+  // at 16 — more, shorter walks balance its 40 resident warps per SM better).
   constexpr int TW2 = 62;
-  int TH = 64;
-  if (d == 2) {
+  int sms = 0;
+  if (d == 2 &&
+      (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m.device >= 0 ? m.device : 0) != cudaSuccess ||
+       sms <= 0)) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  auto strips = [&](int th_max) {
+    std::vector<int4> tl;
+    if (d != 2) return tl;
     auto n_warps = [&](int th) {
       int64_t w = 0;
       for (int x0 = 1; x0 <= n - 2; x0 += TW2) w += (n - 1 - x0 + th - 1) / th;
       return w * m.n_cells;
     };
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m.device >= 0 ? m.device : 0) != cudaSuccess ||
-        sms <= 0) {
-      cudaGetLastError();
-      sms = 152;
-    }
-    while (TH > 8 && n_warps(TH) < 16 * int64_t(sms)) TH /= 2;
-  }
-  std::vector<int4> tiles;
-  if (d == 2) {
+    int th = th_max;
+    while (th > 8 && n_warps(th) < 16 * int64_t(sms)) th /= 2;
     for (int x0 = 1; x0 <= n - 2; x0 += TW2) {
       const int ymax = n - 1 - x0;
-      for (int y0 = 1; y0 <= ymax; y0 += TH) tiles.push_back(make_int4(x0, y0, std::min(y0 + TH, ymax + 1), 0));
+      for (int y0 = 1; y0 <= ymax; y0 += th) tl.push_back(make_int4(x0, y0, std::min(y0 + th, ymax + 1), 0));
     }
-  }
-  // rows of neighbouring strips run side by side, so halo rows hit in L2
-  std::stable_sort(tiles.begin(), tiles.end(), [](const int4& a, const int4& b) {
-    if (a.w != b.w) return a.w < b.w;
-    if (a.y != b.y) return a.y < b.y;
-    return a.x < b.x;
-  });
+    // rows of neighbouring strips run side by side, so halo rows hit in L2
+    std::stable_sort(tl.begin(), tl.end(), [](const int4& p, const int4& q) {
+      if (p.y != q.y) return p.y < q.y;
+      return p.x < q.x;
+    });
+    return tl;
+  };
+  std::vector<int4> tiles = strips(64), tiles32 = strips(16);
+  L.n_tiles32 = int(tiles32.size());
   L.n_tiles = int(tiles.size());
 
   // ---- interface work list: (prim, b, a0, a1), at most 128 points each ----
@@ -492,6 +498,7 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   if (!(err = upload(m, &L.st_hi, sth)).empty()) return err;
   if (!(err = upload(m, &L.st_lo, stl)).empty()) return err;
   if (!(err = upload(m, &L.tiles, tiles)).empty()) return err;
+  if (!(err = upload(m, &L.tiles32, tiles32)).empty()) return err;
   if (!(err = upload(m, &L.items, items)).empty()) return err;
   if (!(err = upload(m, &L.slabs, slabs)).empty()) return err;
   if (d == 3 && !items.empty()) {
