@@ -210,12 +210,15 @@ std::string build_p2_level(Mesh& m, int level, LevelDev& L) {
     if (m.prims[p].type == 1)
       for (int t0 = 0; t0 < n; t0 += 128) items.push_back(make_int4(int(p), t0, std::min(t0 + 128, n), 0));
   L.n_p2_items = int(items.size());
-  // row-kernel tiles: 30 lattice columns x 64 rows; a DoF of column x has an
-  // interior class only on rows y <= n-1-x
+  // row-kernel tiles: 30 lattice columns x 16 rows; a DoF of column x has an
+  // interior class only on rows y <= n-1-x.  A warp walks its rows serially:
+  // at level 10 (32 macros) 16-row chunks beat 64-row ones by 3 % (float-
+  // float) and 7 % (fp32), more, shorter walks balancing the SMs better.
+  constexpr int TH = 16;
   std::vector<int4> tiles;
   for (int x0 = 0; x0 <= n - 1; x0 += 30) {
     const int ymax = n - 1 - x0;
-    for (int y0 = 0; y0 <= ymax; y0 += 64) tiles.push_back(make_int4(x0, y0, std::min(y0 + 64, ymax + 1), 0));
+    for (int y0 = 0; y0 <= ymax; y0 += TH) tiles.push_back(make_int4(x0, y0, std::min(y0 + TH, ymax + 1), 0));
   }
   std::stable_sort(tiles.begin(), tiles.end(), [](const int4& a, const int4& b) {
     if (a.y != b.y) return a.y < b.y;
