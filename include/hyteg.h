@@ -160,7 +160,7 @@ int hyteg_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, voi
 int hyteg_apply_batch(const hyteg_mesh* const* meshes, const int* levels, int dtype, const void* const* xs,
                       void* const* ys, int count, void* stream);
 
-/* hyteg_apply with CUDA events/* hyteg_apply with CUDA events (cudaEvent_t as void*, each may be NULL)
+/* hyteg_apply with CUDA events (cudaEvent_t as void*, each may be NULL)
  * recorded on `stream` before the macro-interior kernel (ev_begin), between
  * it and the interface kernel (ev_mid) and after the interface kernel
  * (ev_end), so a caller can time each kernel on the launching stream.  The

@@ -318,7 +318,6 @@ std::string solver_setup(Mesh& m, int max_level, int nu1, int nu2, double omega)
   const int d = m.dim;
   const int ncls = d == 2 ? NCLS2 : NCLS3;
   const int nw = d == 2 ? NW2 : NW3;
-  const int center = d == 2 ? C2 : C3;
   if (m.n_verts > 4096) return "the coarsest level has more than 4096 vertices (dense direct solve)";
   solver_free(m);
   if (d == 3) {
