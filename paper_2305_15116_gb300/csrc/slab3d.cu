@@ -205,92 +205,96 @@ __global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(cons
     const int zoff = t3i(N) - t3i(N - z);
     const int bz = roff(z), bu = roff(z + 1), bd = roff(z - 1);
 
-    // ---- interior points: x, y >= 1, x + y <= K = M - 2 (z >= 1) ---------
-    // Work unit: two adjacent points (x, y), (x + 1, y) of one row, x odd.
-    // Rows are taken in pairs (y, y + 1), y = 1 + 2r, which together hold
-    // K - 1 - 2r units; r(K - r) units precede pair r, K/2 (K - K/2) in all.
-    // The second point of a unit at the end of an odd row lies on the
-    // macro's diagonal face: it is evaluated (its neighbours are valid ring
-    // cells) but not written.
-    if (z >= 1 && M >= 4) {
-      const int K = M - 2;
-      const int units = (K / 2) * (K - K / 2);
-      const float Kf = (float)K;
-      for (int u = tid; u < units; u += SLAB_THREADS) {
-        // row pair r: the largest r with r (K - r) <= u
-        const float d = fmaxf(Kf * Kf - 4.0f * (float)u, 1.0f);
-        int r = max((int)((Kf - d * rsqrtf(d)) * 0.5f), 0);
-        if (r * (K - r) > u) --r;
-        if ((r + 1) * (K - r - 1) <= u) ++r;
-        const int j = u - r * (K - r);
-        const int h = (K - 2 * r) >> 1;  // units in row 1 + 2r: ceil((K - 1 - 2r) / 2)
-        const int yy = j < h ? 1 + 2 * r : 2 + 2 * r;
-        const int xx = 1 + 2 * (j < h ? j : j - h);
-        const int p = yy * M - (yy * (yy - 1)) / 2 + xx;
-        // ring offsets of the first point in slices z, z+1, z-1; row gap A = M - y
-        const int qz = bz + p, qu = bu + p - yy, qd = bd + p + yy, A = M - yy;
-        auto at = [&](int i) { return P::pair(SS::get(ring[i]), SS::get(ring[i + 1])); };
-        typename P::Acc a;
-        P::first(a, w[0], at(qz));
-        P::add_sym(a, w[1], at(qz + 1), at(qz - 1));           // (±1,0,0)
-        P::add_sym(a, w[3], at(qz + A), at(qz - A - 1));       // (0,±1,0)
-        P::add_sym(a, w[5], at(qz - A), at(qz + A - 1));       // ±(1,-1,0)
-        P::add_sym(a, w[7], at(qu), at(qd));                   // (0,0,±1)
-        P::add_sym(a, w[8], at(qu - 1), at(qd + 1));           // ±(-1,0,1)
-        P::add_sym(a, w[9], at(qu - A), at(qd + A + 1));       // ±(0,-1,1)
-        P::add_sym(a, w[10], at(qu - A + 1), at(qd + A));      // ±(1,-1,1)
-        T r0, r1;
-        P::finish(a, r0, r1);
-        ym[zoff + p] = r0;
-        if (xx < K - yy) ym[zoff + p + 1] = r1;
-      }
-    }
-    // ---- macro-boundary points of the slice: partial rows ---------------------
-    // z = 0: the whole slice lies on the face z = 0; otherwise the rows y = 0,
-    // the column x = 0 and the diagonal x + y = M - 1.  Invalid neighbours
-    // carry weight 0 and read guard cells or stale (finite) values.
+    // ---- the slice's work: interior units, then macro-boundary points -----
+    // Interior points (x, y >= 1, x + y <= K = M - 2, z >= 1) come in units of
+    // two adjacent points (x, y), (x + 1, y) of one row, x odd.  Rows are taken
+    // in pairs (y, y + 1), y = 1 + 2r, which together hold K - 1 - 2r units;
+    // r(K - r) units precede pair r, K/2 (K - K/2) in all.  The second point
+    // of a unit at the end of an odd row lies on the macro's diagonal face: it
+    // is evaluated (its neighbours are valid ring cells) but not written.
+    // Macro-boundary points (z = 0: the whole slice, the face z = 0;
+    // otherwise the rows y = 0, the column x = 0 and the diagonal x + y =
+    // M - 1) get their partial rows; invalid neighbours carry weight 0 and
+    // read guard cells or stale (finite) values.  Units and boundary points
+    // cost about the same (a packed pair against one scalar float-float row)
+    // and share one list, so that the threads reach the slice's barrier
+    // together.
     {
+      const int K = M - 2;
+      const int units = (z >= 1 && M >= 4) ? (K / 2) * (K - K / 2) : 0;
       const int nb = (z == 0) ? M * (M + 1) / 2 : (M >= 2 ? 3 * (M - 1) : 1);
-      for (int q = tid; q < nb; q += SLAB_THREADS) {
-        int xx, yv;
-        if (z == 0) {
-          yv = tri_row(q, M);
-          xx = q - (yv * M - (yv * (yv - 1)) / 2);
-        } else if (M == 1) {
-          xx = 0;
-          yv = 0;
-        } else if (q < M) {  // y = 0
-          xx = q;
-          yv = 0;
-        } else if (q < 2 * M - 1) {  // x = 0, y = 1 .. M-1
-          xx = 0;
-          yv = q - M + 1;
-        } else {  // diagonal, y = 1 .. M-2
-          yv = q - (2 * M - 1) + 1;
-          xx = M - 1 - yv;
+      const float Kf = (float)K;
+      for (int wi = tid; wi < units + nb; wi += SLAB_THREADS) {
+        if (wi < units) {
+          const int u = wi;
+          // row pair r: the largest r with r (K - r) <= u
+          const float d = fmaxf(Kf * Kf - 4.0f * (float)u, 1.0f);
+          int r = max((int)((Kf - d * rsqrtf(d)) * 0.5f), 0);
+          if (r * (K - r) > u) --r;
+          if ((r + 1) * (K - r - 1) <= u) ++r;
+          const int j = u - r * (K - r);
+          const int h = (K - 2 * r) >> 1;  // units in row 1 + 2r: ceil((K - 1 - 2r) / 2)
+          const int yy = j < h ? 1 + 2 * r : 2 + 2 * r;
+          const int xx = 1 + 2 * (j < h ? j : j - h);
+          const int p = yy * M - (yy * (yy - 1)) / 2 + xx;
+          // ring offsets of the first point in slices z, z+1, z-1; row gap A = M - y
+          const int qz = bz + p, qu = bu + p - yy, qd = bd + p + yy, A = M - yy;
+          auto at = [&](int i) { return P::pair(SS::get(ring[i]), SS::get(ring[i + 1])); };
+          typename P::Acc a;
+          P::first(a, w[0], at(qz));
+          P::add_sym(a, w[1], at(qz + 1), at(qz - 1));           // (±1,0,0)
+          P::add_sym(a, w[3], at(qz + A), at(qz - A - 1));       // (0,±1,0)
+          P::add_sym(a, w[5], at(qz - A), at(qz + A - 1));       // ±(1,-1,0)
+          P::add_sym(a, w[7], at(qu), at(qd));                   // (0,0,±1)
+          P::add_sym(a, w[8], at(qu - 1), at(qd + 1));           // ±(-1,0,1)
+          P::add_sym(a, w[9], at(qu - A), at(qd + A + 1));       // ±(0,-1,1)
+          P::add_sym(a, w[10], at(qu - A + 1), at(qd + A));      // ±(1,-1,1)
+          T r0, r1;
+          P::finish(a, r0, r1);
+          ym[zoff + p] = r0;
+          if (xx < K - yy) ym[zoff + p + 1] = r1;
+        } else {
+          const int q = wi - units;
+          int xx, yv;
+          if (z == 0) {
+            yv = tri_row(q, M);
+            xx = q - (yv * M - (yv * (yv - 1)) / 2);
+          } else if (M == 1) {
+            xx = 0;
+            yv = 0;
+          } else if (q < M) {  // y = 0
+            xx = q;
+            yv = 0;
+          } else if (q < 2 * M - 1) {  // x = 0, y = 1 .. M-1
+            xx = 0;
+            yv = q - M + 1;
+          } else {  // diagonal, y = 1 .. M-2
+            yv = q - (2 * M - 1) + 1;
+            xx = M - 1 - yv;
+          }
+          const int cls = (xx == 0 ? 1 : 0) | (yv == 0 ? 2 : 0) | (z == 0 ? 4 : 0) | (xx + yv == M - 1 ? 8 : 0);
+          const int p = yv * M - (yv * (yv - 1)) / 2 + xx;
+          const WSV* cwv = wcls + cls * NW3;
+          auto cw = [&](int k) { return WS::w(cwv[k]); };
+          const int qz = bz + p, qu = bu + p - yv, qd = bd + p + yv, A = M - yv;
+          typename P::Acc1 a;
+          P::first1(a, cw(0), SS::get(ring[qz]));
+          P::add1(a, cw(1), SS::get(ring[qz + 1]));
+          P::add1(a, cw(2), SS::get(ring[qz - 1]));
+          P::add1(a, cw(3), SS::get(ring[qz + A]));
+          P::add1(a, cw(4), SS::get(ring[qz - A - 1]));
+          P::add1(a, cw(5), SS::get(ring[qz - A]));
+          P::add1(a, cw(6), SS::get(ring[qz + A - 1]));
+          P::add1(a, cw(7), SS::get(ring[qu]));
+          P::add1(a, cw(8), SS::get(ring[qu - 1]));
+          P::add1(a, cw(9), SS::get(ring[qu - A]));
+          P::add1(a, cw(10), SS::get(ring[qu - A + 1]));
+          P::add1(a, cw(11), SS::get(ring[qd]));
+          P::add1(a, cw(12), SS::get(ring[qd + 1]));
+          P::add1(a, cw(13), SS::get(ring[qd + A + 1]));
+          P::add1(a, cw(14), SS::get(ring[qd + A]));
+          ym[zoff + p] = P::finish1(a);
         }
-        const int cls = (xx == 0 ? 1 : 0) | (yv == 0 ? 2 : 0) | (z == 0 ? 4 : 0) | (xx + yv == M - 1 ? 8 : 0);
-        const int p = yv * M - (yv * (yv - 1)) / 2 + xx;
-        const WSV* cwv = wcls + cls * NW3;
-        auto cw = [&](int k) { return WS::w(cwv[k]); };
-        const int qz = bz + p, qu = bu + p - yv, qd = bd + p + yv, A = M - yv;
-        typename P::Acc1 a;
-        P::first1(a, cw(0), SS::get(ring[qz]));
-        P::add1(a, cw(1), SS::get(ring[qz + 1]));
-        P::add1(a, cw(2), SS::get(ring[qz - 1]));
-        P::add1(a, cw(3), SS::get(ring[qz + A]));
-        P::add1(a, cw(4), SS::get(ring[qz - A - 1]));
-        P::add1(a, cw(5), SS::get(ring[qz - A]));
-        P::add1(a, cw(6), SS::get(ring[qz + A - 1]));
-        P::add1(a, cw(7), SS::get(ring[qu]));
-        P::add1(a, cw(8), SS::get(ring[qu - 1]));
-        P::add1(a, cw(9), SS::get(ring[qu - A]));
-        P::add1(a, cw(10), SS::get(ring[qu - A + 1]));
-        P::add1(a, cw(11), SS::get(ring[qd]));
-        P::add1(a, cw(12), SS::get(ring[qd + 1]));
-        P::add1(a, cw(13), SS::get(ring[qd + A + 1]));
-        P::add1(a, cw(14), SS::get(ring[qd + A]));
-        ym[zoff + p] = P::finish1(a);
       }
     }
     // slice z+2 has landed (staged during the previous iteration): convert it
