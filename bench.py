@@ -517,6 +517,25 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(v, device=None):
+    """The largest value of v over the ranks of the default process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(local_ms, units_per_rank, world, reduce_max=None):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units in local_ms milliseconds: the job takes the slowest
+    rank's time (max over ranks), and the value is all ranks' units over it,
+    in G units per second.  Returns (job ms, value)."""
+    ms = reduce_max(local_ms) if (reduce_max is not None and world > 1) else float(local_ms)
+    return ms, units_per_rank * world / (ms * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- main
 def main():
     args = parse()
@@ -550,13 +569,9 @@ def main():
     r = timed_applies(w, args.steps, args.warmup, stream, barrier)
     clocks = ClockSampler.summarise(sampler.stop(), r["t0"], r["t1"]) if sampler else None
 
-    total_ms = r["total_ms"]
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    reduce_max = (lambda v: max_over_ranks(v, device)) if world > 1 else None
+    total_ms, value = job_rate(r["total_ms"], w["ng"] * args.steps, world, reduce_max)
     ms_per_step = total_ms / args.steps
-    value = w["ng"] * args.steps * world / (total_ms * 1e-3) / 1e9
     dtype_label = {"f64": "f64 data, float-float (2 x f32) arithmetic", "f32": "f32",
                    "f64_ieee": "f64 (native fp64 FMA)"}[args.dtype]
 
@@ -571,12 +586,8 @@ def main():
         barrier()
     t = time.perf_counter()
     w["M"].apply_host_batch(w["L"], [xh] * e2e_steps, [yh] * e2e_steps, stream=stream)
-    e2e_s = (time.perf_counter() - t) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": w["ng"] * world / e2e_s / 1e9, "unit": UNIT,
+    e2e_ms, e2e_rate = job_rate(1e3 * (time.perf_counter() - t) / e2e_steps, w["ng"], world, reduce_max)
+    e2e = {"value": e2e_rate, "unit": UNIT,
            "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
            "d2h_bytes_per_step": int(yh.numel() * yh.element_size())}
     del xh, yh
