@@ -156,3 +156,14 @@ def test_p2_dof_map_matches_oracle(lib, kx, ky, jit, L):
     per = oracle.p2_dofs_per_macro(L)
     vslots = np.concatenate([np.arange(c * per, c * per + nv) for c in range(m.n_cells)])
     np.testing.assert_array_equal(mine[vslots], M.dof_map(L))
+
+
+def test_apply_batch_argument_checks_without_a_gpu(lib):
+    """hyteg_apply_batch validates its arguments before touching the device:
+    an empty batch is a no-op, a negative count or NULL arrays are EINVAL."""
+    C = lib._capi
+    n0 = C.lib.hyteg_apply_batch(None, None, lib.F64, None, None, 0, None)
+    assert n0 == 0
+    assert C.lib.hyteg_apply_batch(None, None, lib.F64, None, None, -1, None) == C.EINVAL
+    assert C.lib.hyteg_apply_batch(None, None, lib.F64, None, None, 1, None) == C.EINVAL
+    assert b"NULL" in C.lib.hyteg_last_error() or b"null" in C.lib.hyteg_last_error().lower()
