@@ -9,21 +9,21 @@ Performance Analysis of the HyTeG Finite Element Framework" (PASC '23):
 
 * `refine`   — uniform refinement of every macro-triangle / macro-tet of an
   unstructured coarse mesh to level L (Sec. 1.2), the global numbering of the
-  refined vertices and the per-macro triangular array layout (Sec. 3, the
-  generated vertex-to-vertex kernel; DoF counts of Sec. 2.1).
+  refined vertices and the per-macro triangular array layout (Sec. 4, the
+  generated vertex-to-vertex kernel; DoF counts of Sec. 3.1).
 * `assemble` — the P1 stiffness matrix of the refined mesh assembled from
-  element matrices into compressed row storage (Sec. 1.1, Sec. 2), Dirichlet
+  element matrices into compressed row storage (Sec. 1.1, Sec. 3), Dirichlet
   rows, and y = A x.  The paper's stencil apply reaches exactly this product:
   the constant stencil of a macro IS the matrix row of its interior points
-  (Sec. 1.2, Sec. 2).
-* `layout`   — the paper's closed-form DoF counts and memory volumes (Sec. 2.1,
+  (Sec. 1.2, Sec. 3).
+* `layout`   — the paper's closed-form DoF counts and memory volumes (Sec. 3.1,
   Table "memory level 10") and the triangular index map.
 * `p2`       — the P2 (vertex + edge DoF) stiffness of the refined 2D mesh:
   the discretisation whose vertex-to-vertex, edge-to-vertex, vertex-to-edge
-  and edge-to-edge kernels the paper analyses (Sec. 2.1, Sec. 4.2-4.5),
+  and edge-to-edge kernels the paper analyses (Sec. 3.1, Sec. 5.2-5.5),
   assembled from quadratic element matrices.
 * `multigrid` — a textbook V-cycle on the refinement hierarchy (levels as the
-  multigrid hierarchy, Sec. 1.2; smoothers, Sec. 4.1): linear prolongation,
+  multigrid hierarchy, Sec. 1.2; smoothers, Sec. 5.1): linear prolongation,
   R = P^T, weighted Jacobi, direct coarsest solve, lumped-mass right-hand
   side.
 

@@ -3,9 +3,9 @@
 Test infrastructure only; see the package docstring.
 
 The paper compares its matrix-free stencil apply with an assembled sparse
-matrix in compressed row storage (Sec. 1.1 "Sparse Matrices", Sec. 2): both
+matrix in compressed row storage (Sec. 1.1 "Sparse Matrices", Sec. 3): both
 give the same product, since the stencil of a macro is the matrix row of each
-of its interior points (Sec. 1.2, Sec. 2).  This module builds that matrix the
+of its interior points (Sec. 1.2, Sec. 3).  This module builds that matrix the
 textbook way:
 
 * element matrix of a simplex T with vertices P_0..P_d:

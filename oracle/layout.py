@@ -7,20 +7,20 @@ from __future__ import annotations
 
 def vertex_dofs_per_macro(level: int) -> int:
     """Vertex DoFs of one macro-triangle refined `level` times:
-    (2^l + 1)(2^l + 2) / 2 (Sec. 2.1, "#vertex")."""
+    (2^l + 1)(2^l + 2) / 2 (Sec. 3.1, "#vertex")."""
     n = 1 << level
     return (n + 1) * (n + 2) // 2
 
 
 def edge_dofs_per_orientation(level: int) -> int:
     """Edge DoFs of ONE orientation (X, Y or XY) of a refined macro-triangle:
-    2^l (2^l + 1) / 2 (Sec. 2.1, "#edge")."""
+    2^l (2^l + 1) / 2 (Sec. 3.1, "#edge")."""
     n = 1 << level
     return n * (n + 1) // 2
 
 
 def p2_dofs_per_macro(level: int) -> int:
-    """#dof = #vertex + 3 #edge (Sec. 2.1)."""
+    """#dof = #vertex + 3 #edge (Sec. 3.1)."""
     return vertex_dofs_per_macro(level) + 3 * edge_dofs_per_orientation(level)
 
 
@@ -37,8 +37,8 @@ def tri_index(x, y, level: int):
     """Row-major index of local point (x, y) in a macro-triangle array with x
     the inner, contiguous coordinate.  Row y holds the N - y points
     x = 0..N-1-y (N = 2^l + 1 points per macro edge), so row y starts after
-    sum_{k<y} (N - k) entries (Sec. 3, the array accesses of the generated
-    kernel; Sec. 4, iteration starts at the right angle with x inner)."""
+    sum_{k<y} (N - k) entries (Sec. 4, the array accesses of the generated
+    kernel; Sec. 5, iteration starts at the right angle with x inner)."""
     N = (1 << level) + 1
     return x + y * N - (y * (y - 1)) // 2
 

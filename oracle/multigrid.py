@@ -4,7 +4,7 @@ Test infrastructure only; see the package docstring.
 
 The paper names the refinement levels as the natural multigrid hierarchy
 (Sec. 1.2) and multigrid smoothers among the kernels HyTeG generates
-(Sec. 4.1).  It fixes no cycle; this module takes the standard one:
+(Sec. 5.1).  It fixes no cycle; this module takes the standard one:
 * A_l: the operator of level l (P1 stiffness, Dirichlet identity rows);
 * P_l: linear interpolation from level l-1 to level l — a fine vertex that
   coincides with a coarse vertex copies it, a fine vertex at the midpoint of
@@ -18,6 +18,8 @@ The paper names the refinement levels as the natural multigrid hierarchy
   zero on Dirichlet DoFs.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 import scipy.sparse as sp
@@ -134,3 +136,88 @@ class Hierarchy:
             if hist[-1] <= rtol:
                 break
         return u, hist
+
+
+# ---------------------------------------------------------------------------
+# Residuals beyond float64 rounding.  A float64 vector u can only approximate
+# the discrete solution u* to half an ulp per entry; its residual
+# b - A fl(u*) = A (u* - fl(u*)) then sets a floor on the attainable relative
+# residual, which grows like h^-2 in 2D (b shrinks like h^2 while A keeps its
+# scale).  These functions measure that floor exactly and reach below it with
+# an iterate of two float64 parts.
+# ---------------------------------------------------------------------------
+
+def _two_product(a: np.ndarray, b: np.ndarray):
+    """a * b = p + e exactly (Dekker's product with Veltkamp's split)."""
+    p = a * b
+    c = 134217729.0  # 2^27 + 1
+    def split(v):
+        t = c * v
+        hi = t - (t - v)
+        return hi, v - hi
+    ah, al = split(a)
+    bh, bl = split(b)
+    e = ((ah * bh - p) + ah * bl + al * bh) + al * bl
+    return p, e
+
+
+def exact_residual(A: sp.csr_matrix, b: np.ndarray, parts) -> np.ndarray:
+    """r = b - A (u_1 + u_2 + ...) for float64 vectors u_k, every product
+    a_ij u_kj split exactly into two float64 terms and every row summed by
+    math.fsum: the correctly rounded residual of the unevaluated sum."""
+    A = A.tocsr()
+    chunks = []
+    for u in parts:
+        p, e = _two_product(A.data, np.asarray(u, dtype=np.float64)[A.indices])
+        chunks.append((p, e))
+    r = np.empty(A.shape[0])
+    ip = A.indptr
+    for i in range(A.shape[0]):
+        lo, hi = ip[i], ip[i + 1]
+        vals = [b[i]]
+        for p, e in chunks:
+            vals.extend((-p[lo:hi]).tolist())
+            vals.extend((-e[lo:hi]).tolist())
+        r[i] = math.fsum(vals)
+    return r
+
+
+def relres_exact(A: sp.csr_matrix, b: np.ndarray, parts, interior: np.ndarray) -> float:
+    """||b - A sum(parts)||_2 / ||b||_2 over the rows `interior` (non-Dirichlet
+    DoFs), the residual rounded once per entry."""
+    r = exact_residual(A, b, parts)[interior]
+    return float(np.linalg.norm(r) / np.linalg.norm(b[interior]))
+
+
+def float64_floor_estimate(A: sp.csr_matrix, b: np.ndarray, u: np.ndarray, interior: np.ndarray) -> float:
+    """Expected relative residual of fl(u*) when the rounding errors of the
+    entries are independent and uniform in half an ulp:
+    sqrt(sum_j c_j ulp(u_j)^2 / 12) / ||b||, c_j the squared column norm of
+    A over the rows `interior`."""
+    Ai = A.tocsr()[interior]
+    c = np.asarray(Ai.multiply(Ai).sum(axis=0)).ravel()
+    ulp = np.spacing(np.abs(u))
+    return float(np.sqrt(np.sum(c * ulp ** 2) / 12.0) / np.linalg.norm(b[interior]))
+
+
+def solve_two_part(h: "Hierarchy", b: np.ndarray, cycles: int, nu1=3, nu2=3):
+    """Iterative refinement with an iterate of two float64 parts: each step
+    takes the exact residual of u_hi + u_lo, one V-cycle on the residual
+    equation from zero, and adds the correction to u_hi with the rounding
+    error of that addition carried into u_lo (TwoSum).  Returns (u_hi, u_lo)."""
+    L = h.level
+    A = h.A[L]
+    u_hi = np.zeros_like(b)
+    u_lo = np.zeros_like(b)
+    for _ in range(cycles):
+        r = exact_residual(A, b, (u_hi, u_lo))
+        e = h.vcycle(L, np.zeros_like(r), r, nu1, nu2)
+        s = u_hi + e
+        bv = s - u_hi
+        err = (u_hi - (s - bv)) + (e - bv)
+        u_hi = s
+        u_lo = u_lo + err
+    # renormalise: u_hi the float64 rounding of the sum, u_lo the rest
+    s = u_hi + u_lo
+    u_lo = u_lo - (s - u_hi)
+    return s, u_lo

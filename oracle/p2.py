@@ -3,9 +3,9 @@
 Test infrastructure only; see the package docstring.
 
 The paper's kernels belong to a discretisation with DoFs on the vertices AND
-on the edges of the refined triangles (Sec. 2.1: #vertex + 3 #edge DoFs per
-macro, the edges grouped into the three orientations X, Y and XY; Sec. 4.2 to
-4.5: the vertex-to-vertex, edge-to-vertex, vertex-to-edge and edge-to-edge
+on the edges of the refined triangles (Sec. 3.1: #vertex + 3 #edge DoFs per
+macro, the edges grouped into the three orientations X, Y and XY; Sec. 5.2 to
+5.5: the vertex-to-vertex, edge-to-vertex, vertex-to-edge and edge-to-edge
 couplings).  That is the P2 element: quadratic on every micro-triangle, one
 DoF per vertex and one per edge midpoint.  This module is its plain
 definition:

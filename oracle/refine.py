@@ -11,7 +11,7 @@ macro with vertices v_0..v_d sits at v_0 + sum_i (q_i / n)(v_i - v_0).
 Micro-elements of a macro:
 * 2D: "up" triangles (x,y),(x+1,y),(x,y+1) and "down" triangles
   (x+1,y),(x,y+1),(x+1,y+1) — the regular refinement drawn in Sec. 1.2.
-* 3D (the paper names 3D as future work, Sec. 6): Kuhn/Freudenthal simplices
+* 3D (the paper names 3D as future work, Sec. 7): Kuhn/Freudenthal simplices
   of the index map u = (x+y+z, y+z, z); each unit u-cube splits into the six
   simplices a, a+e_p, a+e_p+e_q, a+(1,1,1), kept when inside the macro.  This
   is Bey's regular refinement with n^3 tets per macro.

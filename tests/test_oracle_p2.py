@@ -70,7 +70,7 @@ def pin_pde_consistency():
 def pin_row_structure():
     """Symmetric, zero row sums, 19 entries in an interior vertex row (7
     vertices + 12 edges) and 9 in an interior edge row (4 vertices + 4 edges
-    + itself) (Sec. 2.1)."""
+    + itself) (Sec. 3.1)."""
     coarse = unit_square_mesh(2, 0.15, 0)
     pm = p2.P2Mesh(coarse.coords, coarse.cells, 3, dirichlet=True)
     K = pm.stiffness()
@@ -98,7 +98,7 @@ def pin_counts():
     assert pm.n_global == (2 * 2 * 4 + 1) ** 2  # a uniform grid of spacing h/2
 
 
-# Couplings printed in the paper's listings (Sec. 4.3-4.5), as (group, dx, dy)
+# Couplings printed in the paper's listings (Sec. 5.3-5.5), as (group, dx, dy)
 # offsets from the lattice point (x, y) of the target DoF; [y][x] indexing.
 # Reading: the X-group term of row y+1 reads x-1 instead of x in the
 # edge-to-vertex listing and the vertex term of row y+1 reads x instead of x-1
@@ -120,8 +120,8 @@ LISTING = {
 
 def pin_listing_couplings():
     """Inside a macro every DoF couples exactly with the DoFs of the paper's
-    four kernel listings (vertex-to-vertex shape of Sec. 4.2; edge-to-vertex,
-    vertex-to-edge and edge-to-edge of Sec. 4.3-4.5)."""
+    four kernel listings (vertex-to-vertex shape of Sec. 5.2; edge-to-vertex,
+    vertex-to-edge and edge-to-edge of Sec. 5.3-5.5)."""
     one = np.array([[0.0, 0.0], [1.0, 0.1], [0.3, 0.9]])
     L, n = 3, 8
     pm = p2.P2Mesh(one, np.array([[0, 1, 2]]), L, dirichlet=False)
