@@ -6,10 +6,18 @@
  * triangles (2D) or tetrahedra (3D) — the "macro-primitives" — is refined
  * uniformly L times, which gives a structured grid inside every macro
  * (Sec. 1.2).  Inside a macro every row of the P1 stiffness matrix is the same
- * constant stencil, so the matrix-vector product ("apply", Sec. 4.1) needs no
- * stored matrix (Sec. 1.2, Sec. 2): 7 points in 2D (the vertex-to-vertex
- * stencil of Sec. 4.2), 15 points in 3D.  The DoFs on macro vertices, edges
- * and (3D) faces are completed by the interface step (Sec. 4.1).
+ * constant stencil, so the matrix-vector product ("apply", Sec. 5.1) needs no
+ * stored matrix (Sec. 1.2, Sec. 3): 7 points in 2D (the vertex-to-vertex
+ * stencil of Sec. 5.2), 15 points in 3D.  The DoFs on macro vertices, edges
+ * and (3D) faces are completed by the interface step (Sec. 5.1).
+ *
+ * Sections cited, in the paper's numbering: 1.1 Sparse Matrices, 1.2 Hybrid
+ * Tetrahedral Grids, 1.3 Execution-Cache-Memory Model, 3 Comparing
+ * matrix-free against sparse matrix methods (3.1 Theoretical analysis,
+ * 3.2 Comparing implementations), 4 Code Generation, 5 Performance Modeling
+ * (5.1 Experiment Description, 5.2 Vertex to Vertex Kernel, 5.3 Edge-to-Vertex,
+ * 5.4 Vertex-to-Edge Kernel, 5.5 Edge-to-Edge), 6 Multi-Core Scaling,
+ * 7 Conclusion and Outlook.
  *
  * Conventions shared by every call
  *  - All functions return HYTEG_OK (0) or a negative HYTEG_E* code and never
@@ -25,7 +33,7 @@
  *    (n+1)(n+2)(n+3)/6 in 3D, n = 2^L.  Inside a 2D macro with vertices
  *    (v0, v1, v2) the refined vertex v0 + (i/n)(v1-v0) + (j/n)(v2-v0) sits at
  *    slot i + j(n+1) - j(j-1)/2 (row j, i inner — the index arithmetic of the
- *    generated kernel of Sec. 3).  A 3D macro stacks such triangles slice by
+ *    generated kernel of Sec. 4).  A 3D macro stacks such triangles slice by
  *    slice along v3 (slice k has side n+1-k).  Every DoF on a macro
  *    vertex/edge/face has one copy per incident macro; inputs must hold equal
  *    values in all copies and outputs are written to all copies.
@@ -59,10 +67,14 @@ extern "C" {
 
 /* ---- arithmetic / storage types of the apply --------------------------- */
 #define HYTEG_F64       1    /* float64 vectors; float-float (2 x fp32) arithmetic
-                                with integer-only conversions, relative error
-                                below 1e-13 of sum_j |a_ij x_j| for finite inputs
-                                with 2^-80 <= |x| < 2^126 (smaller values lose
-                                their low part, zero stays zero) */
+                                with integer-only conversions, error below 1e-13
+                                of sum_j |a_ij x_j| per row for every finite
+                                float64 input: rows whose inputs leave the
+                                float-float range (zero or 2^-80 <= |x| < 2^64)
+                                are recomputed with native fp64 FMAs in the same
+                                launch, and levels with a stencil whose largest
+                                weight leaves 2^-20 .. 2^14 run the native
+                                kernels */
 #define HYTEG_F32       2    /* float32 vectors, fp32 FMA arithmetic */
 #define HYTEG_F64_IEEE  3    /* float64 vectors, native fp64 FMA arithmetic */
 
@@ -93,7 +105,7 @@ int hyteg_mesh_create(int dim, int64_t n_verts, const double* coords, int64_t n_
 
 /* Refines every macro uniformly to levels 0..max_level (Sec. 1.2) and builds,
  * on the current CUDA device, the per-macro constant stencils (7 weights in
- * 2D, 15 in 3D, from the affine P1 element matrices; Sec. 1.2, Sec. 2), the
+ * 2D, 15 in 3D, from the affine P1 element matrices; Sec. 1.2, Sec. 3), the
  * interface tables and the kernels' work lists.  Allocates a few small device
  * tables with cudaMalloc (size O(cells * levels + interface primitives)),
  * owned by the mesh.  Synchronous.  May be called again with a larger level.
@@ -129,10 +141,10 @@ int hyteg_num_slots(const hyteg_mesh* mesh, int level, int64_t* n_slots, int64_t
  * level 0..15, no refine needed.  Errors: HYTEG_EINVAL. */
 int hyteg_dof_map(const hyteg_mesh* mesh, int level, int64_t* global_id);
 
-/* y = A x on refinement level `level` (Sec. 4.1 "apply"): A is the P1
+/* y = A x on refinement level `level` (Sec. 5.1 "apply"): A is the P1
  * stiffness matrix of the refined mesh with Dirichlet identity rows when the
  * mesh was created with HYTEG_BC_DIRICHLET.  Launches the macro-interior
- * stencil kernel (Sec. 4.2 for the 2D 7-point case; 15 points in 3D) and the
+ * stencil kernel (Sec. 5.2 for the 2D 7-point case; 15 points in 3D) and the
  * interface kernel, which completes the DoFs on macro vertices, edges and
  * faces by summing the contributions of every incident macro in ascending
  * macro order and writing the sum into every copy.
@@ -206,7 +218,7 @@ int hyteg_dirichlet_mask(const hyteg_mesh* mesh, int level, uint8_t* mask);
 
 /* ---- multigrid on the refinement hierarchy ------------------------------
  * The refinement levels are the multigrid hierarchy (Sec. 1.2) and smoothers
- * are among the generated kernels (Sec. 4.1).  The cycle is the textbook
+ * are among the generated kernels (Sec. 5.1).  The cycle is the textbook
  * V(nu1, nu2): weighted Jacobi with the stencil apply of this library,
  * restriction P^T and linear prolongation P between consecutive levels, and a
  * dense direct solve on level 0 (the coarse mesh, at most 4096 vertices).
@@ -261,15 +273,30 @@ int hyteg_vcycle(hyteg_mesh* mesh, int level, int dtype, const void* b, void* u,
 int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double rtol, int max_iter,
                 void* stream, int* iters, double* relres);
 
+/* hyteg_solve with an iterate of two float64 parts: the solution is the
+ * unevaluated sum u + u_lo of two device vectors (u_lo of the size of u; on
+ * input the low part of the initial guess, usually zeros).  The residual is
+ * formed from both parts (difference form) and every correction is added to
+ * u with its rounding error kept in u_lo (TwoSum), so the iteration is not
+ * held at the floor that the float64 rounding of u sets on the relative
+ * residual (about 2e-10 at level 10 of the unit-square Poisson problem, see
+ * hyteg_solve): it reaches rtol of 1e-10 and below.  u alone is the solution
+ * rounded to float64 up to the last bits (|u_lo| is about an ulp of u).
+ * *relres is the relative residual of u + u_lo.  Same modes, costs and
+ * synchronisation as hyteg_solve plus one float64 vector read per residual.
+ * Errors: as hyteg_solve; HYTEG_EINVAL also for u_lo == NULL or u_lo == u. */
+int hyteg_solve_two_part(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double* u_lo,
+                         double rtol, int max_iter, void* stream, int* iters, double* relres);
+
 /* ---- P2: vertex + edge DoFs (2D) -----------------------------------------
  * The discretisation of the paper's four kernels: quadratic elements on the
  * refined triangles, one DoF per refined vertex and one per micro-edge
- * (Sec. 2.1: #vertex + 3 #edge DoFs per macro, the edges grouped into the
+ * (Sec. 3.1: #vertex + 3 #edge DoFs per macro, the edges grouped into the
  * orientations X, Y and XY).  hyteg_p2_apply computes y = A x with A the P2
  * stiffness matrix (Dirichlet identity rows on the domain boundary when the
  * mesh was created with HYTEG_BC_DIRICHLET) in one pass over all four arrays:
  * the vertex-to-vertex, edge-to-vertex, vertex-to-edge and edge-to-edge
- * couplings of Sec. 4.2-4.5 merged, as the paper proposes (Sec. 6), then the
+ * couplings of Sec. 5.2-5.5 merged, as the paper proposes (Sec. 7), then the
  * interface reduction of the copies.  2D meshes only.
  *
  * Slot layout per macro (macros in cell order): the vertex array of the P1
@@ -360,6 +387,9 @@ typedef struct hyteg_request {
   double* u_out;          /* nullable host array [n_global]: the solution in global numbering,
                              written before the request turns HYTEG_REQ_DONE; must stay valid until then */
   double* b_out;          /* nullable host array [n_global]: the right-hand side, likewise */
+  double* u_lo_out;       /* nullable host array [n_global]: the low part of the solution, likewise: the
+                             server solves with hyteg_solve_two_part, whose solution is u_out + u_lo_out
+                             (u_out alone is its float64 rounding) and whose relres is that of the sum */
 } hyteg_request;
 
 #define HYTEG_REQ_QUEUED   0
@@ -372,7 +402,7 @@ typedef struct hyteg_result {
   int error;        /* HYTEG_OK, or the error code of a failed request */
   int iters;        /* solver iterations (done requests) */
   int cache_hit;    /* 1 if the request reused a cached refined mesh */
-  double relres;    /* final relative residual (done requests) */
+  double relres;    /* final relative residual of the two-part solution (done requests) */
   double queue_s;   /* seconds from submission to the start of the work */
   double run_s;     /* seconds from the start to the end of the work */
   int64_t n_global; /* DoFs of the request's problem */
@@ -421,16 +451,24 @@ void hyteg_server_destroy(hyteg_server* server);
 
 /* hyteg_apply_host without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot let the
- * library call cudaMalloc — code running while its stream is captured into a
- * CUDA graph, real-time loops that forbid allocation after start-up, and
- * processes whose device memory is fully reserved by another allocator.
+ * library call cudaMalloc — real-time loops that forbid allocation after
+ * start-up (an allocation may synchronise the device and stall), and
+ * processes whose device memory is reserved up front by another allocator.
  * x and y are staged in one fixed file-scope device array of
  * 2 * HYTEG_STATIC_STAGE_BYTES that every GPU loading the library holds until
  * the process exits.  Arguments and result as hyteg_apply_host; synchronises
- * `stream` before returning.
+ * `stream` before returning, so the result is in y_host on return.
+ *  - The array's memory is committed when the library's device code is
+ *    loaded on a device (the first kernel launch of the library there, or the
+ *    first call of this function, whichever comes first); a process that
+ *    hands all device memory to another allocator should make one call before
+ *    that allocator reserves it.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.  The current device must be the mesh's device.
+ *    (cudaGetSymbolAddress) and caches it.  The current device must be the
+ *    mesh's device.
+ *  - A stream that is being captured into a CUDA graph is refused with
+ *    HYTEG_ESTATE before anything is enqueued (the call must synchronise its
+ *    stream, which capture does not allow).
  *  - Every call on a device shares the array and leaves its contents behind;
  *    no part of it needs clearing, since each call overwrites all of x it
  *    reads and all of y it returns.  Calls that overlap on the GPU (from
@@ -438,7 +476,8 @@ void hyteg_server_destroy(hyteg_server* server);
  *    serialised by the caller.
  *  - Vectors larger than HYTEG_STATIC_STAGE_BYTES are rejected with
  *    HYTEG_EINVAL and a message naming the limit.
- * Errors: as hyteg_apply_host, HYTEG_ENOMEM never. */
+ * Errors: as hyteg_apply_host (HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA),
+ * HYTEG_ENOMEM never. */
 int hyteg_apply_host_static(const hyteg_mesh* mesh, int level, int dtype, const void* x_host,
                             void* y_host, void* stream);
 

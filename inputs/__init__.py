@@ -12,6 +12,7 @@ from .meshes import (
     rect_mesh,
     box_kuhn_mesh,
     random_vector,
+    range_vector,
     random_normal,
     workload,
     WORKLOADS,
@@ -24,6 +25,7 @@ __all__ = [
     "rect_mesh",
     "box_kuhn_mesh",
     "random_vector",
+    "range_vector",
     "random_normal",
     "workload",
     "WORKLOADS",

@@ -149,6 +149,32 @@ def random_vector(n: int, seed: int, low: float = -1.0, high: float = 1.0) -> np
     return _rng(seed).uniform(low, high, size=n)
 
 
+def range_vector(n: int, seed: int, pattern: str) -> np.ndarray:
+    """n float64 values from PCG64(seed) spanning the float64 range, for the
+    checks of an apply's arithmetic far from magnitude 1:
+      "scale:<k>"  U[-1, 1) * 2^k
+      "mixed"      U[-1, 1) times 1 or 1e-30, each with probability 1/2
+      "huge"       U[-1, 1) with 1 % of the entries +-U[0.5, 1) * 1e300
+      "sparse"     U[-1, 1) with 90 % of the entries +0.0 or -0.0
+      "subnormal"  U[-1, 1) * 2^-1040 (mostly float64 subnormals)"""
+    g = _rng(seed)
+    u = g.uniform(-1.0, 1.0, size=n)
+    if pattern.startswith("scale:"):
+        return np.ldexp(u, int(pattern.split(":")[1]))
+    if pattern == "mixed":
+        return np.where(g.random(n) < 0.5, u, u * 1e-30)
+    if pattern == "huge":
+        pick = g.random(n) < 0.01
+        big = np.sign(u) * g.uniform(0.5, 1.0, size=n) * 1e300
+        return np.where(pick, big, u)
+    if pattern == "sparse":
+        zero = g.random(n) < 0.9
+        return np.where(zero, np.where(u < 0, -0.0, 0.0), u)
+    if pattern == "subnormal":
+        return np.ldexp(u, -1040)
+    raise ValueError(f"unknown pattern {pattern!r}")
+
+
 def random_normal(n: int, seed: int) -> np.ndarray:
     """n float64 values ~ N(0, 1) from PCG64(seed), in index order."""
     return _rng(seed).standard_normal(n)
@@ -161,7 +187,7 @@ WORKLOADS = {
     # 32 jittered macro-triangles, level 11 (~67M DoFs): the 2D throughput case
     "square32jit_L11": dict(dim=2, k=4, jitter=0.15, mesh_seed=0, level=11, x_seed=1),
     # the same 32 macros with P2 (vertex + edge) DoFs at level 10: as many DoFs
-    # per macro as P1 at level 11 (the paper's #dof of Sec. 2.1, 67.2M slots)
+    # per macro as P1 at level 11 (the paper's #dof of Sec. 3.1, 67.2M slots)
     "square32jit_P2_L10": dict(dim=2, k=4, jitter=0.15, mesh_seed=0, level=10, x_seed=1, op="p2"),
     # 384 jittered Kuhn macro-tets, level 6 (~17M DoFs): the 3D throughput case
     "cube384jit_L6": dict(dim=3, k=4, jitter=0.1, mesh_seed=0, level=6, x_seed=1),

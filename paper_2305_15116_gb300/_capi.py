@@ -71,6 +71,10 @@ lib.hyteg_solve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.
                             ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_double)]
 lib.hyteg_solve.restype = ctypes.c_int
+lib.hyteg_solve_two_part.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+lib.hyteg_solve_two_part.restype = ctypes.c_int
 lib.hyteg_p2_num_slots.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p, c_i64p]
 lib.hyteg_p2_num_slots.restype = ctypes.c_int
 lib.hyteg_p2_dof_map.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p]
@@ -94,7 +98,7 @@ class Request(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n_verts", ctypes.c_int64), ("coords", c_dblp), ("n_cells", ctypes.c_int64),
                 ("cells", c_i64p), ("level", ctypes.c_int), ("mode", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("seed", ctypes.c_uint64), ("noise", ctypes.c_double),
-                ("u_out", c_dblp), ("b_out", c_dblp)]
+                ("u_out", c_dblp), ("b_out", c_dblp), ("u_lo_out", c_dblp)]
 
 
 class Result(ctypes.Structure):

@@ -10,6 +10,27 @@
 // product error, the high parts are summed with Knuth's TwoSum, and the result
 // h + l is rebuilt as a float64 with integer instructions and one fp64 add.
 //
+// Range.  The float-float weight tables hold every weight times 2^40 (an
+// exact scaling), so the row sums s + e come out times 2^40 and the final
+// conversion divides it back out through its exponent bias.  The arithmetic
+// is exact to about 2^-45 of sum_j |a_ij x_j|, plus at most 2^-150 of
+// max_j |a_ij| sum_j |x_j| from gradual underflow, while every quantity it
+// forms stays inside the fp32 exponent range.  That holds when every input is
+// zero or has 2^-80 <= |x| < 2^64 and the largest weight of every stencil has
+// 2^-20 <= max |w| <= 2^14 (smaller weights of a stencil are harmless): the
+// scaled products stay below 2^119 and their sums below 2^125, and what
+// gradual underflow rounds or a dropped subnormal s or e loses is below
+// 2^-126 in scaled units, far below one ulp of the row's largest weight times
+// |x|, which is the accuracy the weights themselves carry.  The weights are
+// checked once per level on the host (LevelDev::ff_ok; levels outside the
+// range run the native fp64 kernels).  An input outside the range (also an
+// fp64 subnormal, an infinity or a NaN) splits into a NaN high part; the NaN
+// reaches the row's sum of high parts, and the kernel recomputes exactly
+// those rows in native fp64 from memory (ArF64FF::bad / bad1 / Mark).  So
+// every finite float64 input gives the float64 row to the stated accuracy,
+// and the fast path costs a range check per loaded value and a NaN
+// accumulation per row.
+//
 // The kernels evaluate two independent points per thread (two row streams).
 // The float-float policy packs the two points into the two halves of 64-bit
 // registers and uses Blackwell's packed f32x2 add/sub/mul/fma, which do two
@@ -63,10 +84,15 @@ struct FF {
   float h, l;
 };
 
-// Split a float64 into (h, l) with integer instructions only.
-// Finite |v| < 2^127: h = v truncated to 24 bits, l = the next 23 bits
-// (|v - h - l| <= 2^-46 |v|); l is dropped for |v| < 2^-80 and both parts for
-// |v| < 2^-126 (signed zero).
+// The float-float input range: zero, or 2^FF_EMIN <= |v| < 2^FF_EMAX.
+constexpr int FF_EMIN = -80, FF_EMAX = 64;
+// the exponent of the weight tables' scaling
+constexpr int FF_WSCALE = 40;
+
+// Split a float64 into (h, l) with integer instructions only: h = v truncated
+// to 24 bits, l = the next 23 bits (|v - h - l| <= 2^-46 |v|).  Zero splits
+// into two zeros of its sign; every other value outside the float-float range
+// gives h = NaN, which marks the rows that read it.
 __device__ __forceinline__ FF ff_split(double v) {
   const unsigned hi = (unsigned)__double2hiint(v);
   const unsigned lo = (unsigned)__double2loint(v);
@@ -76,27 +102,34 @@ __device__ __forceinline__ FF ff_split(double v) {
   hb = (hb & 0x7FFFFFFFu) | (hi & 0x80000000u);
   // next 23 mantissa bits (bits 28..6 of the low word) as an exact integer
   const float t = __fsub_rn(__uint_as_float(0x4B000000u | ((lo >> 6) & 0x7FFFFFu)), 8388608.0f);
-  // their weight: 2^(exponent of v - 46), with the sign of v
+  // their weight: 2^(exponent of v - 46), with the sign of v (a normal fp32
+  // inside the range; finite for zero, where t = 0)
   const unsigned sb = (hb & 0xFF800000u) - (46u << 23);
+  const bool in_range = mag - (unsigned(1023 + FF_EMIN) << 20) < (unsigned(FF_EMAX - FF_EMIN) << 20);
+  const bool zero = (mag | lo) == 0u;
   FF r;
-  r.h = mag >= (897u << 20) ? __uint_as_float(hb) : __uint_as_float(hi & 0x80000000u);
-  r.l = mag >= (943u << 20) ? __fmul_rn(t, __uint_as_float(sb)) : 0.0f;
+  r.h = in_range ? __uint_as_float(hb) : (zero ? __uint_as_float(hi & 0x80000000u) : __int_as_float(0x7FC00000));
+  r.l = __fmul_rn(t, __uint_as_float(sb));
   return r;
 }
 
-// Exact float32 -> float64 with integer instructions (no conversion unit).
-// Zero maps to zero; fp32 subnormals (|f| < 2^-126) are flushed to zero.
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
+// Exact float32 -> float64 of 2^-40 f with integer instructions (no
+// conversion unit): the row sums carry the weights' 2^40 scaling.  Zero
+// maps to zero; fp32 subnormals (|f| < 2^-126) are dropped.
+__device__ __forceinline__ double f32s_to_f64_bits(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned a = u & 0x7FFFFFFFu;
-  const unsigned hi = a >= 0x00800000u ? (((a >> 3) + (896u << 20)) | (u & 0x80000000u)) : (u & 0x80000000u);
+  const unsigned hi =
+      a >= 0x00800000u ? (((a >> 3) + ((896u - unsigned(FF_WSCALE)) << 20)) | (u & 0x80000000u))
+                       : (u & 0x80000000u);
   const unsigned lo = a >= 0x00800000u ? (u << 29) : 0u;
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// float64 value of the unevaluated sum s + e.
+// float64 value of 2^-40 (s + e) for the unevaluated sum s + e of a row
+// (scaled weights).
 __device__ __forceinline__ double ff_join(float s, float e) {
-  return __dadd_rn(f32_to_f64_bits(s), f32_to_f64_bits(e));
+  return __dadd_rn(f32s_to_f64_bits(s), f32s_to_f64_bits(e));
 }
 
 // ---- stencil weights of one macro --------------------------------------------
@@ -120,6 +153,7 @@ struct StencilPtr {
 //   finish(acc, a, b)  the two results in T
 
 struct ArF32 {
+  static constexpr bool kPoison = false;  // no float-float range marks
   using T = float;
   using V = float;
   using P2 = float2;
@@ -154,9 +188,20 @@ struct ArF32 {
   static __device__ __forceinline__ void add1(float& a, W w, V v) { a = __fmaf_rn(w, v, a); }
   static __device__ __forceinline__ T finish1(float a) { return a; }
   using Acc1 = float;
+  static __device__ __forceinline__ bool bad(const Acc&) { return false; }
+  static __device__ __forceinline__ bool bad1(float) { return false; }
+  using Mark1 = int;
+  static __device__ __forceinline__ Mark1 mark1_0() { return 0; }
+  static __device__ __forceinline__ void mark1(Mark1&, float) {}
+  static __device__ __forceinline__ bool marked1(Mark1) { return false; }
+  using Mark = int;
+  static __device__ __forceinline__ Mark mark0() { return 0; }
+  static __device__ __forceinline__ void mark(Mark&, const Acc&) {}
+  static __device__ __forceinline__ bool marked(Mark) { return false; }
 };
 
 struct ArF64Native {
+  static constexpr bool kPoison = false;
   using T = double;
   using V = double;
   using P2 = double2;
@@ -189,9 +234,20 @@ struct ArF64Native {
   static __device__ __forceinline__ void add1(double& a, W w, V v) { a = __fma_rn(w, v, a); }
   static __device__ __forceinline__ T finish1(double a) { return a; }
   using Acc1 = double;
+  static __device__ __forceinline__ bool bad(const Acc&) { return false; }
+  static __device__ __forceinline__ bool bad1(double) { return false; }
+  using Mark1 = int;
+  static __device__ __forceinline__ Mark1 mark1_0() { return 0; }
+  static __device__ __forceinline__ void mark1(Mark1&, double) {}
+  static __device__ __forceinline__ bool marked1(Mark1) { return false; }
+  using Mark = int;
+  static __device__ __forceinline__ Mark mark0() { return 0; }
+  static __device__ __forceinline__ void mark(Mark&, const Acc&) {}
+  static __device__ __forceinline__ bool marked(Mark) { return false; }
 };
 
 struct ArF64FF {
+  static constexpr bool kPoison = true;  // rows reading an input outside the range come out marked
   using T = double;
   using V = FF;
   struct P2 {
@@ -267,6 +323,26 @@ struct ArF64FF {
     ra = ff_join(sa, ea);
     rb = ff_join(sb, eb);
   }
+  // A lane's NaN accumulator over many rows: mark() adds 0 * s, which stays
+  // zero unless a row's sum of high parts is NaN (an input outside the range;
+  // sums inside it are finite).  One packed FMA per two rows.
+  using Mark = f2_t;
+  static __device__ __forceinline__ Mark mark0() { return 0ull; }
+  static __device__ __forceinline__ void mark(Mark& k, const Acc& a) { k = f2_fma(a.s, 0ull, k); }
+  static __device__ __forceinline__ bool marked(Mark k) {
+    float u, v;
+    f2_unpack(k, u, v);
+    const float t = __fadd_rn(u, v);
+    return t != t;
+  }
+  // true when either row read an input outside the float-float range (its sum
+  // of high parts is NaN); such rows are recomputed in native fp64
+  static __device__ __forceinline__ bool bad(const Acc& a) {
+    float sa, sb;
+    f2_unpack(a.s, sa, sb);
+    const float t = __fadd_rn(sa, sb);
+    return t != t;
+  }
   // single-point forms (3D kernel)
   struct Acc1 {
     float s, e;
@@ -291,6 +367,12 @@ struct ArF64FF {
     a.e = __fmaf_rn(w.l1, v.h, e);
   }
   static __device__ __forceinline__ T finish1(const Acc1& a) { return ff_join(a.s, a.e); }
+  static __device__ __forceinline__ bool bad1(const Acc1& a) { return a.s != a.s; }
+  // single-row NaN accumulator (as Mark): one FMA per row
+  using Mark1 = float;
+  static __device__ __forceinline__ Mark1 mark1_0() { return 0.0f; }
+  static __device__ __forceinline__ void mark1(Mark1& k, const Acc1& a) { k = __fmaf_rn(a.s, 0.0f, k); }
+  static __device__ __forceinline__ bool marked1(Mark1 k) { return k != k; }
 };
 
 }  // namespace hyteg

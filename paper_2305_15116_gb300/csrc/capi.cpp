@@ -22,18 +22,9 @@ int cuda_fail(cudaError_t e, const char* where) {
   return fail(HYTEG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-size_t elem_size(int dtype) { return dtype == HYTEG_F32 ? 4 : 8; }
-
-bool valid_dtype(int dtype) { return dtype == HYTEG_F64 || dtype == HYTEG_F32 || dtype == HYTEG_F64_IEEE; }
-
-int check_level(const hyteg_mesh* mesh, int level) {
-  if (!mesh) return fail(HYTEG_EINVAL, "mesh is NULL");
-  if (level < 0) return fail(HYTEG_EINVAL, "level < 0");
-  if (level > mesh->m.max_level)
-    return fail(HYTEG_ESTATE, "level " + std::to_string(level) + " not refined (max " +
-                                  std::to_string(mesh->m.max_level) + ")");
-  return HYTEG_OK;
-}
+using hyteg::check_level;
+using hyteg::elem_size;
+using hyteg::valid_dtype;
 
 // Host-only queries need no refined device tables.
 int check_host_level(const hyteg_mesh* mesh, int level) {
@@ -45,6 +36,19 @@ int check_host_level(const hyteg_mesh* mesh, int level) {
 }  // namespace
 
 void hyteg::set_last_error(const std::string& msg) { g_last_error = msg; }
+
+size_t hyteg::elem_size(int dtype) { return dtype == HYTEG_F32 ? 4 : 8; }
+
+bool hyteg::valid_dtype(int dtype) { return dtype == HYTEG_F64 || dtype == HYTEG_F32 || dtype == HYTEG_F64_IEEE; }
+
+int hyteg::check_level(const hyteg_mesh* mesh, int level) {
+  if (!mesh) return fail(HYTEG_EINVAL, "mesh is NULL");
+  if (level < 0) return fail(HYTEG_EINVAL, "level < 0");
+  if (level > mesh->m.max_level)
+    return fail(HYTEG_ESTATE, "level " + std::to_string(level) + " not refined (max " +
+                                  std::to_string(mesh->m.max_level) + ")");
+  return HYTEG_OK;
+}
 
 extern "C" {
 
@@ -220,12 +224,14 @@ int hyteg_apply_batch(const hyteg_mesh* const* meshes, const int* levels, int dt
   std::vector<void*> y2;
   for (int i = 0; i < count; ++i) {
     const hyteg::Mesh& m = meshes[i]->m;
-    if (m.dim == 2) {
+    // 2D products share the batched launch, except float64 ones on a level
+    // whose weights need the native fp64 kernel (outside the float-float range)
+    if (m.dim == 2 && (dtype != HYTEG_F64 || m.levels[levels[i]].ff_ok)) {
       m2.push_back(&m);
       l2.push_back(levels[i]);
       x2.push_back(xs[i]);
       y2.push_back(ys[i]);
-    } else {  // 3D meshes: their own launches, in order
+    } else {  // 3D meshes and the others: their own launches, in order
       const char* what = "";
       const cudaError_t e = hyteg::launch_apply(m, levels[i], dtype, xs[i], ys[i], s, nullptr, &what);
       if (e != cudaSuccess) return cuda_fail(e, what);
@@ -451,7 +457,19 @@ int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* 
   if (mode != HYTEG_SOLVE_F64 && mode != HYTEG_SOLVE_MIXED) return fail(HYTEG_EINVAL, "unknown mode");
   if (!b || !u || !iters || !relres) return fail(HYTEG_EINVAL, "NULL argument");
   if (!(rtol > 0.0) || max_iter < 0) return fail(HYTEG_EINVAL, "bad rtol or max_iter");
-  const cudaError_t e = hyteg::mg_solve(mesh->m, level, mode, b, u, rtol, max_iter,
+  const cudaError_t e = hyteg::mg_solve(mesh->m, level, mode, b, u, nullptr, rtol, max_iter,
+                                        static_cast<cudaStream_t>(stream), iters, relres);
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "solve");
+}
+
+int hyteg_solve_two_part(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double* u_lo,
+                         double rtol, int max_iter, void* stream, int* iters, double* relres) {
+  if (int r = check_solver(mesh, level, 0)) return r;
+  if (mode != HYTEG_SOLVE_F64 && mode != HYTEG_SOLVE_MIXED) return fail(HYTEG_EINVAL, "unknown mode");
+  if (!b || !u || !u_lo || !iters || !relres) return fail(HYTEG_EINVAL, "NULL argument");
+  if (u_lo == u) return fail(HYTEG_EINVAL, "u and u_lo must be different vectors");
+  if (!(rtol > 0.0) || max_iter < 0) return fail(HYTEG_EINVAL, "bad rtol or max_iter");
+  const cudaError_t e = hyteg::mg_solve(mesh->m, level, mode, b, u, u_lo, rtol, max_iter,
                                         static_cast<cudaStream_t>(stream), iters, relres);
   return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "solve");
 }

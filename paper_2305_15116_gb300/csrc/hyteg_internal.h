@@ -12,8 +12,8 @@ namespace hyteg {
 
 // Neighbour offsets of the macro-interior stencils.
 //
-// 2D: the seven points of the vertex-to-vertex stencil (Sec. 4.2), in the
-// order of the weight slots of the generated kernel (Sec. 3):
+// 2D: the seven points of the vertex-to-vertex stencil (Sec. 5.2), in the
+// order of the weight slots of the generated kernel (Sec. 4):
 //   0 S (0,-1)  1 SE (1,-1)  2 W (-1,0)  3 C (0,0)  4 E (1,0)  5 NW (-1,1)  6 N (0,1)
 // 3D: centre, the six in-slice neighbours, then the four neighbours in the
 // slice above (z+1) and the four in the slice below (z-1).  These are exactly
@@ -35,8 +35,11 @@ struct LevelDev {
   // class stencils [cell][class][weight]
   double* st64 = nullptr;
   float* st32 = nullptr;
-  float* st_hi = nullptr;          // float-float split of st64
+  float* st_hi = nullptr;          // float-float split of 2^40 st64 (arith.cuh)
   float* st_lo = nullptr;
+  // every nonzero weight inside the float-float weight range (arith.cuh);
+  // otherwise HYTEG_F64 applies of this level run the native fp64 kernels
+  bool ff_ok = true;
   // macro-interior work list: int4 (x0, y0, y1, z)
   int4* tiles = nullptr;
   int n_tiles = 0;                 // per macro
@@ -79,6 +82,7 @@ struct LevelDev {
   float* p2_st32 = nullptr;
   float* p2_hi = nullptr;
   float* p2_lo = nullptr;
+  bool p2_ff_ok = true;  // as ff_ok, for the P2 weights
   int4* p2_items = nullptr;
   int n_p2_items = 0;
   // P2 row-kernel work list: int4 (x0, y0, y1, 0): lattice columns x0..x0+29,
@@ -95,6 +99,11 @@ constexpr int P2W = 8 * P2_NV + 3 * 2 * P2_NE;  // 206
 constexpr int P2_EOFF = 8 * P2_NV;               // first edge-class weight
 
 int64_t p2_edge_slots(int level);  // n(n+1)/2 edges of one group per macro
+
+// True when the largest |weight| of every stencil (consecutive groups of
+// per_stencil weights of st) lies inside the float-float weight range of
+// arith.cuh (2^-20 <= max |w| <= 2^14) or the stencil is all zero.
+bool ff_weights_in_range(const std::vector<double>& st, int per_stencil);
 int64_t p2_slots_per_macro(int level);
 
 // Interface primitive (coarse vertex, edge or face) and its incident cells.
@@ -275,8 +284,8 @@ cudaError_t mg_diag_setup(const Mesh& m, int level, MgLevel& g, cudaStream_t s);
 cudaError_t mg_restrict(const Mesh& m, int fine_level, int dtype, const void* rf, void* bc, cudaStream_t s);
 cudaError_t mg_prolong_add(const Mesh& m, int fine_level, int dtype, const void* ec, void* uf, cudaStream_t s);
 cudaError_t mg_vcycle(Mesh& m, int level, int dtype, const void* b, void* u, cudaStream_t s);
-cudaError_t mg_solve(Mesh& m, int level, int mode, const double* b, double* u, double rtol, int max_iter,
-                     cudaStream_t s, int* iters, double* relres);
+cudaError_t mg_solve(Mesh& m, int level, int mode, const double* b, double* u, double* ulo, double rtol,
+                     int max_iter, cudaStream_t s, int* iters, double* relres);
 
 // ---- kernels ----------------------------------------------------------------
 // dtype: 1 = f64 (float-float arithmetic), 2 = f32, 3 = f64 native.
@@ -312,3 +321,14 @@ cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, voi
 struct hyteg_mesh {
   hyteg::Mesh m;
 };
+
+namespace hyteg {
+
+// Argument checks shared by the C ABI's entry points (capi.cpp): element size
+// and validity of a HYTEG_F* code, and a refined level of a non-null mesh
+// (HYTEG_EINVAL / HYTEG_ESTATE with the message in hyteg_last_error).
+size_t elem_size(int dtype);
+bool valid_dtype(int dtype);
+int check_level(const hyteg_mesh* mesh, int level);
+
+}  // namespace hyteg

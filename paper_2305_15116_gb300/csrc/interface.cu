@@ -2,7 +2,7 @@
 // edges and faces.
 //
 // The paper hands the points on the macro boundary to separate "interface
-// primitives" (Sec. 4.1).  Here every copy of such a point in an incident
+// primitives" (Sec. 5.1).  Here every copy of such a point in an incident
 // macro holds its macro's PARTIAL row (the stencil restricted to the
 // micro-elements of that macro, written by the 3D kernels); the partials of
 // all incident macros are summed in ascending macro order — a fixed order,
@@ -216,6 +216,7 @@ cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const Lev
 cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
                          cudaEvent_t ev_mid, const char** what) {
   const LevelDev& L = m.levels[level];
+  if (dtype == 1 && !L.ff_ok) dtype = 3;  // weights outside the float-float range: native fp64
   cudaError_t e;
   if (m.dim == 2) {
     // one launch: macro-interior tiles and interface points side by side

@@ -1,4 +1,4 @@
-// Macro-interior stencil sweep, 2D (the vertex-to-vertex kernel of Sec. 4.2).
+// Macro-interior stencil sweep, 2D (the vertex-to-vertex kernel of Sec. 5.2).
 //
 // For every macro-triangle m and every point strictly inside it
 // (x >= 1, y >= 1, x + y <= n - 1):
@@ -6,7 +6,7 @@
 //          + SE x[x+1,y-1] + NW x[x-1,y+1]
 // with the constant weights of macro m.  The triangular array of a macro is
 // row-major with x contiguous; row r starts at r(n+2) - r(r+1)/2 and holds
-// n+1-r points (Sec. 3).
+// n+1-r points (Sec. 4).
 //
 // GPU mapping: one warp per tile of 64 consecutive columns and up to 64 rows;
 // the same launch also completes the points on macro vertices and edges (the
@@ -16,11 +16,12 @@
 // Each lane stages its two columns of the next RING rows in shared memory with
 // cp.async, which keeps RING rows per warp in flight without spending
 // registers on them, and keeps three rows in registers (the layer condition
-// of Sec. 2.3 held in the register file).  The neighbour columns beyond its
+// of Sec. 1.3 held in the register file).  The neighbour columns beyond its
 // pair come from the adjacent lanes by warp shuffles, so every value is read
 // from memory once per tile plus two halo rows.  62 of the 64 columns are
 // written; the outermost two only supply the horizontal halo.
 #include "arith.cuh"
+#include "fallback.cuh"
 #include "hyteg_internal.h"
 
 namespace hyteg {
@@ -267,6 +268,7 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
   };
   Cursor out = cr;  // the row being written (set after the first take)
   const bool wa = lane >= 1, wbb = lane <= 30;  // lane 0's A and lane 31's B are halo
+  typename P::Mark mk = P::mark0();
   // output row from (below, centre, above)
   auto step = [&](const Row<P>& lo, const Row<P>& ce, const Row<P>& hi) {
     // the interior stencil is symmetric (w(d) = w(-d), made bitwise equal on
@@ -279,6 +281,7 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
     T outa, outb;
     P::finish(a, outa, outb);
     // point (c, r) is interior when c <= n - 1 - r, i.e. c < len - 1
+    P::mark(mk, a);  // float-float: notes a row that read an input outside the range
     if (SWEEP) {  // the centre values of the row are u (fp32 data)
       float ua = 0.0f, ub = 0.0f;
       if constexpr (SWEEP) {
@@ -309,6 +312,20 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
     step(r2, r0, r1);
   }
   cp_async_wait<0>();
+  if constexpr (P::kPoison) {
+    // a row of this lane read an input outside the float-float range: its
+    // two columns of the tile again, in native fp64 from memory
+    if (P::marked(mk)) {
+      const double* wd = st.d + wb;
+      Cursor rw;
+      rw.init(n, t.y);
+      for (int r = t.y; r < t.z; ++r) {
+        if (wa && ca < rw.len - 1) ym[rw.off + ca] = native_row2d(xm + rw.off + ca, rw.len, wd);
+        if (wbb && cb < rw.len - 1) ym[rw.off + cb] = native_row2d(xm + rw.off + cb, rw.len, wd);
+        rw.next();
+      }
+    }
+  }
 }
 
 template <class P, int MODE>

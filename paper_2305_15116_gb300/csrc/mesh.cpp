@@ -334,6 +334,15 @@ void free_level(const Mesh& m, LevelDev& L) {
   L = LevelDev{};
 }
 
+bool ff_weights_in_range(const std::vector<double>& st, int per_stencil) {
+  for (size_t b = 0; b + per_stencil <= st.size(); b += per_stencil) {
+    double wmax = 0.0;  // largest weight of one stencil (class or row group)
+    for (int k = 0; k < per_stencil; ++k) wmax = std::max(wmax, std::fabs(st[b + k]));
+    if (wmax != 0.0 && !(wmax >= std::ldexp(1.0, -20) && wmax <= std::ldexp(1.0, 14))) return false;
+  }
+  return true;
+}
+
 std::string build_level(Mesh& m, int level, LevelDev& L) {
   const int d = m.dim;
   const int nv = d + 1;
@@ -418,13 +427,26 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
       for (auto& pr : pairs) W[pr[0]] = W[pr[1]] = 0.5 * (W[pr[0]] + W[pr[1]]);
     }
   }
+  // A weight that vanishes in exact arithmetic (the diagonal couplings of an
+  // unjittered Kuhn cube, a right angle in 2D) leaves a rounding residue of a
+  // few ulps of the macro's largest weight in the element sums above; such
+  // residues (below 2^-46 of the macro's largest weight) are set to zero.
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    double* W = &st[size_t(c) * ncls * nw];
+    double wmax = 0.0;
+    for (int i = 0; i < ncls * nw; ++i) wmax = std::max(wmax, std::fabs(W[i]));
+    for (int i = 0; i < ncls * nw; ++i)
+      if (std::fabs(W[i]) < std::ldexp(wmax, -46)) W[i] = 0.0;
+  }
   L.st_host = st;
   std::vector<float> st32(st.size()), sth(st.size()), stl(st.size());
-  for (size_t i = 0; i < st.size(); ++i) {
+  for (size_t i = 0; i < st.size(); ++i) {  // float-float parts of 2^40 w (arith.cuh)
+    const double ws = std::ldexp(st[i], 40);
     st32[i] = float(st[i]);
-    sth[i] = float(st[i]);
-    stl[i] = float(st[i] - double(sth[i]));
+    sth[i] = float(ws);
+    stl[i] = float(ws - double(sth[i]));
   }
+  L.ff_ok = ff_weights_in_range(st, ncls * nw);
 
   // ---- 2D macro-interior work lists: strips of columns x chunks of rows ----
   // a warp loads 64 consecutive columns and writes the 62 inner ones.  A warp

@@ -4,7 +4,7 @@
 // the level-0 operator.
 //
 // The paper uses the refinement levels as the multigrid hierarchy (Sec. 1.2)
-// and names smoothers among the generated kernels (Sec. 4.1); the cycle
+// and names smoothers among the generated kernels (Sec. 5.1); the cycle
 // itself (weighted Jacobi, linear interpolation, R = P^T) is the textbook one.
 #include <algorithm>
 #include <array>

@@ -4,7 +4,7 @@
 // float64 V-cycles or fp32 V-cycles inside float64 iterative refinement.
 //
 // The paper takes the refinement levels as the natural multigrid hierarchy
-// (Sec. 1.2) and lists smoothers among the kernels HyTeG generates (Sec. 4.1);
+// (Sec. 1.2) and lists smoothers among the kernels HyTeG generates (Sec. 5.1);
 // the operator apply of every smoothing step is the stencil apply of this
 // library (interior2d.cu / slab3d.cu + interface.cu).
 //
@@ -96,6 +96,33 @@ __global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ e, i
     u[i] = u[i] + (double)e[i];
 }
 
+// (u, ulo) <- (fl(u + ulo), the rest): u becomes the float64 rounding of the
+// two-part value (Fast2Sum, exact while |ulo| <= |u|, which the corrections
+// keep: ulo collects rounding errors of u).
+__global__ void k_normalize_two_part(double* __restrict__ u, double* __restrict__ ulo, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = u[i], b = ulo[i];
+    const double sum = __dadd_rn(a, b);
+    u[i] = sum;
+    ulo[i] = __dsub_rn(b, __dsub_rn(sum, a));
+  }
+}
+
+// (u + ulo) += e for an iterate of two float64 parts: u takes the rounded
+// sum, and its rounding error (Knuth's TwoSum, exact) goes into ulo.
+template <class T>
+__global__ void k_add_two_part(double* __restrict__ u, double* __restrict__ ulo, const T* __restrict__ e,
+                               int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = u[i], d = (double)e[i];
+    const double sum = __dadd_rn(a, d);
+    const double bv = __dsub_rn(sum, a);
+    const double err = __dadd_rn(__dsub_rn(a, __dsub_rn(sum, bv)), __dsub_rn(d, bv));
+    u[i] = sum;
+    ulo[i] = __dadd_rn(ulo[i], err);
+  }
+}
+
 // ---- accurate residual ------------------------------------------------------
 // Macro-local part of (A u) at every slot in difference form,
 //   sum_{k != centre} w_k (u_k - u_centre),
@@ -105,8 +132,10 @@ __global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ e, i
 // (the residual of a converged solve, where b ~ h^d f).  Weights of the
 // point's boundary class; neighbours outside the macro have weight 0 and are
 // not read.
+// With `ulo` (an iterate u + ulo of two float64 parts) the differences of the
+// low parts join those of the high parts: sum w_k ((u_k - u_c) + (lo_k - lo_c)).
 template <int DIM>
-__global__ void k_partial_diff(const double* __restrict__ u, double* __restrict__ y,
+__global__ void k_partial_diff(const double* __restrict__ u, const double* __restrict__ ulo, double* __restrict__ y,
                                const unsigned* __restrict__ lpts, const double* __restrict__ st, int n, int64_t S,
                                int64_t total) {
   constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
@@ -120,7 +149,9 @@ __global__ void k_partial_diff(const double* __restrict__ u, double* __restrict_
     const int cls = pclass<DIM>(n, q);
     const double* __restrict__ w = st + (cell * NCLS + cls) * NW;
     const double* __restrict__ um = u + cell * S;
+    const double* __restrict__ lm = ulo ? ulo + cell * S : nullptr;
     const double uc = um[i - cell * S];
+    const double lc = lm ? lm[i - cell * S] : 0.0;
     double acc = 0.0;
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
@@ -136,7 +167,10 @@ __global__ void k_partial_diff(const double* __restrict__ u, double* __restrict_
         j[2] = q[2] + c_off3[k][2];
       }
       if (!inside<DIM>(n, j)) continue;
-      acc = __fma_rn(__ldg(w + k), __dsub_rn(um[slotq<DIM>(n, j)], uc), acc);
+      const int64_t sj = slotq<DIM>(n, j);
+      double d = __dsub_rn(um[sj], uc);
+      if (lm) d = __dadd_rn(d, __dsub_rn(lm[sj], lc));
+      acc = __fma_rn(__ldg(w + k), d, acc);
     }
     y[i] = acc;
   }
@@ -634,25 +668,30 @@ cudaError_t mg_vcycle(Mesh& m, int l, int dtype, const void* b, void* u, cudaStr
                     : vcycle_t<double>(m, l, (const double*)b, (double*)u, s);
 }
 
-// y = A u in float64, difference form; Dirichlet rows: y = u.
-cudaError_t accurate_apply(const Mesh& m, int l, const double* u, double* y, cudaStream_t s) {
+// y = A (u + ulo) in float64, difference form (ulo nullable); Dirichlet
+// rows: y = u.
+cudaError_t accurate_apply(const Mesh& m, int l, const double* u, const double* ulo, double* y, cudaStream_t s) {
   const Solver& sv = *m.solver;
   const LevelDev& L = m.levels[l];
   const int64_t ns = L.slots_per_macro * m.n_cells;
   if (m.dim == 2)
-    k_partial_diff<2><<<grid_for(ns), THREADS, 0, s>>>(u, y, sv.lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns);
+    k_partial_diff<2><<<grid_for(ns), THREADS, 0, s>>>(u, ulo, y, sv.lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns);
   else
-    k_partial_diff<3><<<grid_for(ns), THREADS, 0, s>>>(u, y, sv.lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns);
+    k_partial_diff<3><<<grid_for(ns), THREADS, 0, s>>>(u, ulo, y, sv.lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns);
   HY_TRY(cudaGetLastError());
   return launch_interface_reduce(3, m.dim, m, L, u, y, s);  // sum the copies; Dirichlet rows: y = u
 }
 
-cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, double rtol, int max_iter,
-                     cudaStream_t s, int* iters, double* relres) {
+cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, double* ulo, double rtol,
+                     int max_iter, cudaStream_t s, int* iters, double* relres) {
   // Residual correction: r = b - A u (float64), e = V-cycle(A e = r)
   // from e = 0 in fp32 (HYTEG_SOLVE_MIXED) or float64 (HYTEG_SOLVE_F64),
   // u += e.  The float64 residual bounds the attainable accuracy; the cycles
-  // only need to reduce the error by their convergence factor.
+  // only need to reduce the error by their convergence factor.  With `ulo`
+  // the iterate is the unevaluated sum u + ulo of two float64 vectors: the
+  // residual takes both parts and every update keeps its rounding error in
+  // ulo, which lifts the floor that the float64 rounding of u sets on the
+  // relative residual (it grows like h^-2).
   Solver& sv = *m.solver;
   MgLevel& g = sv.lv[l];
   const int64_t ns = m.levels[l].slots_per_macro * m.n_cells;
@@ -676,7 +715,7 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
       const char* what = "";
       HY_TRY(launch_apply(m, l, 1, u, g.y64, s, nullptr, &what));
     } else {
-      HY_TRY(accurate_apply(m, l, u, g.y64, s));
+      HY_TRY(accurate_apply(m, l, u, ulo, g.y64, s));
     }
     if (mode == 2)
       k_residual_norm<float><<<RED_BLOCKS, THREADS, 0, s>>>(g.b32, first ? g.u32 : nullptr, g.dinv32,
@@ -718,14 +757,24 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
     if (mode == 2) {
       if (!first) HY_TRY(cudaMemsetAsync(g.u32, 0, sizeof(float) * ns, s));
       HY_TRY(vcycle_own<float>(m, l, s, first));
-      k_add_f32<<<grid_for(ns), THREADS, 0, s>>>(u, g.u32, ns);
+      if (ulo)
+        k_add_two_part<float><<<grid_for(ns), THREADS, 0, s>>>(u, ulo, g.u32, ns);
+      else
+        k_add_f32<<<grid_for(ns), THREADS, 0, s>>>(u, g.u32, ns);
       HY_TRY(cudaGetLastError());
     } else {
       if (!first) HY_TRY(cudaMemsetAsync(g.u64, 0, sizeof(double) * ns, s));
       HY_TRY(vcycle_own<double>(m, l, s, first));
-      k_add_f64<<<grid_for(ns), THREADS, 0, s>>>(u, g.u64, ns);
+      if (ulo)
+        k_add_two_part<double><<<grid_for(ns), THREADS, 0, s>>>(u, ulo, g.u64, ns);
+      else
+        k_add_f64<<<grid_for(ns), THREADS, 0, s>>>(u, g.u64, ns);
       HY_TRY(cudaGetLastError());
     }
+  }
+  if (ulo) {  // u: the float64 rounding of the solution, ulo: the rest
+    k_normalize_two_part<<<grid_for(ns), THREADS, 0, s>>>(u, ulo, ns);
+    HY_TRY(cudaGetLastError());
   }
   *iters = it;
   *relres = rel;

@@ -2,15 +2,17 @@
 //
 // hyteg_apply_host stages x and y in device buffers that it allocates with
 // cudaMalloc the first time it sees a vector of that size.  Some callers must
-// not trigger a device allocation at that point: code that runs while its
-// stream is being captured into a CUDA graph (allocation calls are not allowed
-// during capture), real-time loops that forbid allocation after start-up
-// (an allocation can synchronise the device and stall for milliseconds), and
-// processes whose device memory is entirely pre-reserved by another allocator
-// (a framework's caching pool), where a stray cudaMalloc fails or fragments it.
-// hyteg_apply_host_static serves them: its staging memory is one fixed
-// file-scope device array, present on every GPU that loads the library for as
-// long as the process lives, and the call makes no allocation of its own.
+// not trigger a device allocation at that point: real-time loops that forbid
+// allocation after start-up (an allocation can synchronise the device and
+// stall for milliseconds), and processes whose device memory is entirely
+// pre-reserved by another allocator (a framework's caching pool), where a
+// stray cudaMalloc fails or fragments it.  hyteg_apply_host_static serves
+// them: its staging memory is one fixed file-scope device array, present on
+// every GPU that loads the library for as long as the process lives, and the
+// call makes no allocation of its own.  It synchronises its stream before
+// returning (the result must be in host memory on return), so it cannot run
+// on a stream that is being captured into a CUDA graph: it checks that first
+// and refuses with HYTEG_ESTATE.
 #include <mutex>
 #include <string>
 
@@ -55,19 +57,26 @@ int fail(int code, const std::string& msg) {
 
 extern "C" int hyteg_apply_host_static(const hyteg_mesh* mesh, int level, int dtype, const void* x_host,
                                        void* y_host, void* stream) {
-  if (!mesh) return fail(HYTEG_EINVAL, "mesh is NULL");
+  if (int r = hyteg::check_level(mesh, level)) return r;
   const hyteg::Mesh& m = mesh->m;
-  if (level < 0 || level > m.max_level) return fail(HYTEG_ESTATE, "level not refined");
-  if (dtype != HYTEG_F64 && dtype != HYTEG_F32 && dtype != HYTEG_F64_IEEE) return fail(HYTEG_EINVAL, "unknown dtype");
+  if (!hyteg::valid_dtype(dtype)) return fail(HYTEG_EINVAL, "unknown dtype");
   if (!x_host || !y_host) return fail(HYTEG_EINVAL, "x_host or y_host is NULL");
-  const size_t bytes = size_t(m.n_cells) * size_t(hyteg::slots_per_macro(m.dim, level)) *
-                       (dtype == HYTEG_F32 ? 4 : 8);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the call ends by synchronising `s`, which a stream under graph capture
+  // does not allow: refuse before touching the stream
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(HYTEG_ESTATE, "hyteg_apply_host_static: the stream is being captured into a CUDA graph; the call "
+                              "synchronises its stream and cannot be captured");
+  const size_t bytes = size_t(m.n_cells) * size_t(hyteg::slots_per_macro(m.dim, level)) * hyteg::elem_size(dtype);
   if (bytes > kStageBytes)
     return fail(HYTEG_EINVAL, "hyteg_apply_host_static: a vector of this level needs " + std::to_string(bytes) +
                                   " bytes, more than the static staging limit of " + std::to_string(kStageBytes) +
                                   " bytes (HYTEG_STATIC_STAGE_BYTES); use hyteg_apply_host");
   int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev != m.device || dev < 0 || dev >= kMaxDevices)
     return fail(HYTEG_ESTATE, "the current device is not the device the mesh was refined on");
@@ -76,7 +85,6 @@ extern "C" int hyteg_apply_host_static(const hyteg_mesh* mesh, int level, int dt
   if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   void* xd = base;
   void* yd = base + kStageBytes;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   e = cudaMemcpyAsync(xd, x_host, bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fail(HYTEG_ECUDA, std::string("cudaMemcpyAsync H2D: ") + cudaGetErrorString(e));
   const char* what = "";

@@ -1,6 +1,6 @@
 // P2 operator apply (2D): the vertex-to-vertex, edge-to-vertex,
-// vertex-to-edge and edge-to-edge kernels of Sec. 4.2-4.5 merged into one
-// pass, as the paper proposes for its next step (Sec. 6: one kernel instead
+// vertex-to-edge and edge-to-edge kernels of Sec. 5.2-5.5 merged into one
+// pass, as the paper proposes for its next step (Sec. 7: one kernel instead
 // of four, so every array is read and written once).
 //
 // One thread per lattice point (x, y) of a macro computes up to four rows:
@@ -15,6 +15,7 @@
 // Layout per macro: vertex array (row y at y(n+2) - y(y+1)/2), then the X, Y
 // and XY edge arrays, edge (x, y) at y n - y(y-1)/2 + x.
 #include "arith.cuh"
+#include "fallback.cuh"
 #include "hyteg_internal.h"
 
 namespace hyteg {
@@ -60,6 +61,8 @@ __device__ __forceinline__ typename P::W wget(const StencilPtr& st, int64_t i) {
 }
 
 // One row: sum_k w_k x[nb_k], over the valid neighbours when `check`.
+// A float-float row that read an input outside the float-float range
+// (arith.cuh) is recomputed in native fp64 from memory.
 template <class P, int NN>
 __device__ __forceinline__ typename P::T row(const typename P::T* __restrict__ xm, const Geo& G, const NbD* nb,
                                              const StencilPtr& st, int64_t wbase, int x, int y, bool check) {
@@ -70,6 +73,9 @@ __device__ __forceinline__ typename P::T row(const typename P::T* __restrict__ x
     const int kx = x + nb[k].dx, ky = y + nb[k].dy;
     if (check && !G.valid(nb[k].kind, kx, ky)) continue;
     P::add1(a, wget<P>(st, wbase + k), P::load(xm + G.idx(nb[k].kind, kx, ky)));
+  }
+  if constexpr (P::kPoison) {
+    if (P::bad1(a)) return row<ArF64Native, NN>(xm, G, nb, st, wbase, x, y, true);
   }
   return P::finish1(a);
 }
@@ -284,6 +290,7 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
   int yo = t.y;  // output row
   Cur co;
   co.init(n, t.y);
+  typename P::Mark1 mk = P::mark1_0();  // float-float: notes rows that read an input outside the range
   auto step = [&](const P2Row<P>& lo, const P2Row<P>& ce, const P2Row<P>& hi) {
     const int cx = c;
     // vertex row (NBV order)
@@ -302,6 +309,7 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
       P::add1(a, W[12], lo.yc);
       P::add1(a, W[16], ce.dw);
       P::add1(a, W[17], lo.dc);
+      P::mark1(mk, a);
       ym[co.ov + cx] = P::finish1(a);
     }
     if (writer && cx + yo <= n - 1) {
@@ -315,6 +323,7 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
         P::add1(a, W[25], lo.ye);
         P::add1(a, W[26], ce.dc);
         P::add1(a, W[27], lo.dc);
+        P::mark1(mk, a);
         e0[0] = P::finish1(a);
       }
       if (cx >= 1) {  // Y (NBY order)
@@ -326,6 +335,7 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
         P::add1(a, W[34], hi.xw);
         P::add1(a, W[35], ce.dc);
         P::add1(a, W[36], ce.dw);
+        P::mark1(mk, a);
         e0[se] = P::finish1(a);
       }
       if (cx + yo <= n - 2) {  // XY (NBD order)
@@ -337,6 +347,7 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
         P::add1(a, W[43], hi.xc);
         P::add1(a, W[44], ce.yc);
         P::add1(a, W[45], ce.ye);
+        P::mark1(mk, a);
         e0[2 * se] = P::finish1(a);
       }
     }
@@ -357,6 +368,23 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
     step(r2, r0, r1);
   }
   p2_wait<0>();
+  if constexpr (P::kPoison) {
+    // rows that read an input outside the float-float range: this lane's
+    // column of the tile again, every row it wrote, in native fp64
+    if (P::marked1(mk)) {
+      const int64_t wv = m * (int64_t)P2W, we = wv + P2_EOFF;
+      for (int yy = t.y; yy < t.z; ++yy) {
+        if (c >= 1 && yy >= 1 && c + yy <= n - 1)
+          ym[G.vidx(c, yy)] = row<ArF64Native, P2_NV>(xm, G, c_nbv, st, wv, c, yy, true);
+        if (c + yy <= n - 1) {
+          if (yy >= 1) ym[G.eidx(0, c, yy)] = row<ArF64Native, P2_NE>(xm, G, c_nbe[0], st, we, c, yy, true);
+          if (c >= 1) ym[G.eidx(1, c, yy)] = row<ArF64Native, P2_NE>(xm, G, c_nbe[1], st, we + 2 * P2_NE, c, yy, true);
+          if (c + yy <= n - 2)
+            ym[G.eidx(2, c, yy)] = row<ArF64Native, P2_NE>(xm, G, c_nbe[2], st, we + 4 * P2_NE, c, yy, true);
+        }
+      }
+    }
+  }
 }
 
 // Edge DoFs on coarse edges: sum the copies' partial rows in ascending macro
@@ -468,6 +496,7 @@ cudaError_t launch_t(const Mesh& m, const LevelDev& L, const void* x, void* y, c
 cudaError_t launch_p2_apply(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
                             cudaEvent_t ev_mid, const char** what) {
   const LevelDev& L = m.levels[level];
+  if (dtype == 1 && !L.p2_ff_ok) dtype = 3;  // weights outside the float-float range: native fp64
   switch (dtype) {
     case 1: return launch_t<ArF64FF>(m, L, x, y, s, ev_mid, what);
     case 2: return launch_t<ArF32>(m, L, x, y, s, ev_mid, what);

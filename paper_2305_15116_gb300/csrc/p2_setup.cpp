@@ -2,8 +2,8 @@
 // class stencils from quadratic element matrices, the interface work list of
 // the edge DoFs on coarse edges, and the global P2 numbering.
 //
-// The paper's kernels belong to this discretisation (Sec. 2.1: a vertex array
-// and three edge arrays X, Y, XY per macro; Sec. 4.2-4.5: vertex-to-vertex,
+// The paper's kernels belong to this discretisation (Sec. 3.1: a vertex array
+// and three edge arrays X, Y, XY per macro; Sec. 5.2-5.5: vertex-to-vertex,
 // edge-to-vertex, vertex-to-edge and edge-to-edge couplings).  Inside a macro
 // all up-triangles are translates of each other and all down-triangles are
 // their point reflections, and the P2 stiffness of a triangle does not change
@@ -199,10 +199,18 @@ std::string build_p2_level(Mesh& m, int level, LevelDev& L) {
     }
   }
   std::vector<float> st32(st.size()), sth(st.size()), stl(st.size());
-  for (size_t i = 0; i < st.size(); ++i) {
+  for (size_t i = 0; i < st.size(); ++i) {  // float-float parts of 2^40 w (arith.cuh)
+    const double ws = std::ldexp(st[i], 40);
     st32[i] = float(st[i]);
-    sth[i] = float(st[i]);
-    stl[i] = float(st[i] - double(sth[i]));
+    sth[i] = float(ws);
+    stl[i] = float(ws - double(sth[i]));
+  }
+  // the largest weight of every vertex class (19) and edge class (9) row
+  L.p2_ff_ok = true;
+  for (int64_t c = 0; c < m.n_cells; ++c) {
+    const std::vector<double> v(st.begin() + c * P2W, st.begin() + c * P2W + P2_EOFF);
+    const std::vector<double> e(st.begin() + c * P2W + P2_EOFF, st.begin() + (c + 1) * P2W);
+    L.p2_ff_ok = L.p2_ff_ok && ff_weights_in_range(v, P2_NV) && ff_weights_in_range(e, P2_NE);
   }
   // edge DoFs on coarse edges: chunks of at most 128 micro-edges
   std::vector<int4> items;

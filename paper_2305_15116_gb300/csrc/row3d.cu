@@ -1,5 +1,5 @@
 // 3D stencil sweep over every slot of every macro-tetrahedron (the 15-point
-// Kuhn stencil; the paper's 3D extension, Sec. 6), as a warp row kernel.
+// Kuhn stencil; the paper's 3D extension, Sec. 7), as a warp row kernel.
 //
 // A macro array stacks triangular slices z = 0..n (slice z has side
 // M = n+1-z and starts at T3(n+1) - T3(n+1-z), T3(k) = k(k+1)(k+2)/6); the
@@ -25,6 +25,7 @@
 // take their partial stencils uniformly).  The interface step then sums the
 // copies' partial rows (k_interface_reduce).
 #include "arith.cuh"
+#include "fallback.cuh"
 #include "hyteg_internal.h"
 
 namespace hyteg {
@@ -217,7 +218,11 @@ __global__ void __launch_bounds__(R3THREADS) k_row3d(const typename P::T* __rest
         P::add1(a, P::weight(st, cb + 13), hi.d.c);
         P::add1(a, P::weight(st, cb + 14), hi.d.w);
       }
-      ym[co.off + c] = P::finish1(a);
+      T r = P::finish1(a);
+      if constexpr (P::kPoison) {  // an input outside the float-float range: native fp64 row
+        if (P::bad1(a)) r = native_row3d(xm, n, c, yo, z, st.d + wb + cls * NW3);
+      }
+      ym[co.off + c] = r;
     }
     ++yo;
     co.next();
@@ -282,7 +287,11 @@ __global__ void __launch_bounds__(128) k_row3d_lines(const typename P::T* __rest
     if (qx < 0 || qy < 0 || qz < 0 || qx + qy + qz > n) continue;
     P::add1(a, P::weight(st, cb + k), P::load(xm + r3_slot(n, qx, qy, qz)));
   }
-  y[cell * S + r3_slot(n, px, yy, z)] = P::finish1(a);
+  typename P::T r = P::finish1(a);
+  if constexpr (P::kPoison) {  // an input outside the float-float range: native fp64 row
+    if (P::bad1(a)) r = native_row3d(xm, n, px, yy, z, st.d + cb);
+  }
+  y[cell * S + r3_slot(n, px, yy, z)] = r;
 }
 
 template <class P>

@@ -39,6 +39,7 @@ struct Entry {
   hyteg_mesh* mesh = nullptr;
   double* b = nullptr;
   double* u = nullptr;
+  double* ulo = nullptr;  // low part of the two-part iterate u + ulo
   double* glob = nullptr;
   int64_t n_global = 0;
   bool busy = false;
@@ -53,6 +54,7 @@ struct Req {
   std::vector<int64_t> cells;
   double* u_out = nullptr;
   double* b_out = nullptr;
+  double* u_lo_out = nullptr;
   std::string key;
   size_t est = 0;
   hyteg_result res{};
@@ -64,8 +66,8 @@ int64_t slots_of(int dim, int level, int64_t n_cells) { return hyteg::slots_per_
 
 // Device bytes of a request: per level the solver workspace (2 inverse
 // diagonals, owner flags, 4 float64 and 4 fp32 vectors: 61 B per slot) and
-// its tables (3D: the interface slot table), plus b, u (slot layout) and the global-order buffer on the
-// finest level, with a margin for tables and allocation rounding.
+// its tables (3D: the interface slot table), plus b, u, u_lo (slot layout) and the global-order buffer on
+// the finest level, with a margin for tables and allocation rounding.
 size_t estimate_bytes(int dim, int level, int64_t n_cells, int64_t n_verts) {
   size_t b = 0;
   for (int l = 0; l <= level; ++l) {
@@ -74,7 +76,7 @@ size_t estimate_bytes(int dim, int level, int64_t n_cells, int64_t n_verts) {
     b += size_t(dim == 3 ? 69 : 61) * size_t(S * n_cells) + size_t(4) * size_t(S) + (size_t(64) << 10);
   }
   const int64_t ns = slots_of(dim, level, n_cells);
-  b += size_t(24) * size_t(ns);
+  b += size_t(32) * size_t(ns);
   // 3D: scratch vectors of the slab work-split autotuner (two float64
   // vectors on the levels it times, all levels together below 20 B per slot)
   if (dim == 3) b += size_t(20) * size_t(ns);
@@ -130,6 +132,7 @@ void hyteg_server::destroy_entry(Entry* e) {
     cudaStreamSynchronize(m.mem.stream);
     hyteg::dev_free(m, e->b);
     hyteg::dev_free(m, e->u);
+    hyteg::dev_free(m, e->ulo);
     hyteg::dev_free(m, e->glob);
     hyteg_mesh_destroy(e->mesh);  // its blocks outside the region go back here
     hyteg::arena_free(arena, region);
@@ -215,6 +218,7 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
       e->n_global = hyteg::n_global_dofs(m, r.level);
       if (hyteg::dev_alloc(m, (void**)&e->b, size_t(ns) * 8) != cudaSuccess ||
           hyteg::dev_alloc(m, (void**)&e->u, size_t(ns) * 8) != cudaSuccess ||
+          hyteg::dev_alloc(m, (void**)&e->ulo, size_t(ns) * 8) != cudaSuccess ||
           hyteg::dev_alloc(m, (void**)&e->glob, size_t(e->n_global) * 8) != cudaSuccess)
         rc = HYTEG_ENOMEM;
     }
@@ -266,18 +270,22 @@ int hyteg_server::run(Req& r, cudaStream_t s, bool* hit, hyteg_result* res, std:
   int rc = HYTEG_OK;
   cudaError_t ce = hyteg::poisson_rhs(m, r.level, r.seed, r.noise, e->b, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(e->u, 0, size_t(ns) * 8, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(e->ulo, 0, size_t(ns) * 8, s);
   if (ce != cudaSuccess) {
     rc = HYTEG_ECUDA;
     *msg = std::string("right-hand side: ") + cudaGetErrorString(ce);
   }
   if (rc == HYTEG_OK) {
-    rc = hyteg_solve(e->mesh, r.level, r.mode, e->b, e->u, r.rtol, r.max_iter, s, &res->iters, &res->relres);
+    // the iterate of two float64 parts reaches rtol below the floor of a
+    // float64 solution's rounding (which grows like h^-2)
+    rc = hyteg_solve_two_part(e->mesh, r.level, r.mode, e->b, e->u, e->ulo, r.rtol, r.max_iter, s, &res->iters,
+                              &res->relres);
     if (rc != HYTEG_OK) *msg = hyteg_last_error();
   }
-  for (int k = 0; k < 2 && rc == HYTEG_OK; ++k) {
-    double* host = k == 0 ? r.u_out : r.b_out;
+  for (int k = 0; k < 3 && rc == HYTEG_OK; ++k) {
+    double* host = k == 0 ? r.u_out : k == 1 ? r.b_out : r.u_lo_out;
     if (!host) continue;
-    ce = hyteg::to_global(m, r.level, k == 0 ? e->u : e->b, e->glob, s);
+    ce = hyteg::to_global(m, r.level, k == 0 ? e->u : k == 1 ? e->b : e->ulo, e->glob, s);
     if (ce == cudaSuccess)
       ce = cudaMemcpyAsync(host, e->glob, size_t(e->n_global) * 8, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -412,6 +420,7 @@ int hyteg_server_submit(hyteg_server* sv, const hyteg_request* q, uint64_t* tick
   r->cells.assign(q->cells, q->cells + q->n_cells * (q->dim + 1));
   r->u_out = q->u_out;
   r->b_out = q->b_out;
+  r->u_lo_out = q->u_lo_out;
   r->key = make_key(*r);
   r->est = estimate_bytes(q->dim, q->level, q->n_cells, q->n_verts);
   if (r->est > sv->cap) return sfail(HYTEG_EINVAL, "request can never fit the memory cap");

@@ -7,7 +7,7 @@
 // slice z only to slices z-1 and z+1 (offsets 0, ±(1,0,0), ±(0,1,0),
 // ±(0,0,1), ±(1,-1,0), ±(1,0,-1), ±(0,1,-1), ±(1,-1,1)), so one CTA walks up a
 // range of slices of one macro with three slices resident in shared memory —
-// the paper's layer condition (Sec. 2.3, Sec. 4.2) one dimension up.  A fourth
+// the paper's layer condition (Sec. 1.3, Sec. 5.2) one dimension up.  A fourth
 // ring buffer receives the next slice by cp.async while the current one is
 // computed (through a staging buffer and one split into float-float for the
 // fp64 path), so each slice costs one barrier.
@@ -18,7 +18,7 @@
 //  * points on the macro's own faces/edges/vertices: the macro's PARTIAL row
 //    (the class stencil of the micro-elements inside this macro).  The
 //    interface kernel then sums the copies' partials over the incident
-//    macros (Sec. 4.1's interface primitives).
+//    macros (Sec. 5.1's interface primitives).
 // Neighbour positions inside slice z (side M), slice z+1 (side M-1) and slice
 // z-1 (side M+1) for point p = s(y) + x, s(y) = yM - y(y-1)/2:
 //   z  : p±1, p+M-y (0,1,0), p+M-y-1 (-1,1,0), p-M+y-1 (0,-1,0), p-M+y (1,-1,0)
@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "arith.cuh"
+#include "fallback.cuh"
 #include "hyteg_internal.h"
 
 namespace hyteg {
@@ -251,6 +252,13 @@ __global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(cons
           P::add_sym(a, w[10], at(qu - A + 1), at(qd + A));      // ±(1,-1,1)
           T r0, r1;
           P::finish(a, r0, r1);
+          if constexpr (P::kPoison) {
+            if (P::bad(a)) {  // an input outside the float-float range: native fp64 rows
+              const double* wd = st.d + (int64_t)m * (NCLS3 * NW3);
+              r0 = native_row3d(xm, n, xx, yy, z, wd);
+              if (xx < K - yy) r1 = native_row3d(xm, n, xx + 1, yy, z, wd);
+            }
+          }
           ym[zoff + p] = r0;
           if (xx < K - yy) ym[zoff + p + 1] = r1;
         } else {
@@ -293,7 +301,11 @@ __global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(cons
           P::add1(a, cw(12), SS::get(ring[qd + 1]));
           P::add1(a, cw(13), SS::get(ring[qd + A + 1]));
           P::add1(a, cw(14), SS::get(ring[qd + A]));
-          ym[zoff + p] = P::finish1(a);
+          T r = P::finish1(a);
+          if constexpr (P::kPoison) {
+            if (P::bad1(a)) r = native_row3d(xm, n, xx, yv, z, st.d + ((int64_t)m * NCLS3 + cls) * NW3);
+          }
+          ym[zoff + p] = r;
         }
       }
     }

@@ -206,6 +206,19 @@ class Mesh:
                 "hyteg_solve")
         return it.value, rel.value
 
+    def solve_two_part(self, level: int, b, u, u_lo, mode: int = SOLVE_MIXED, rtol: float = 1e-10,
+                       max_iter: int = 100, stream=None):
+        """Solve A (u + u_lo) = b with an iterate of two float64 device
+        tensors (u_lo: the low part, zeros to start); returns (iterations,
+        relative residual of u + u_lo)."""
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        C.check(C.lib.hyteg_solve_two_part(self._h, level, mode, ctypes.c_void_p(b.data_ptr()),
+                                           ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u_lo.data_ptr()), rtol,
+                                           max_iter, ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(it),
+                                           ctypes.byref(rel)),
+                "hyteg_solve_two_part")
+        return it.value, rel.value
+
     # ---- Poisson model problem -------------------------------------------------
     def poisson_rhs(self, level: int, seed: int, noise: float, b, stream=None):
         """b (float64 device tensor, slot layout) = lumped mass * (prod sin(pi p)

@@ -46,24 +46,25 @@ class Server:
 
     def submit(self, coords, cells, level: int, seed: int, noise: float = 0.1, mode: int = SOLVE_MIXED,
                rtol: float = 1e-8, max_iter: int = 100, u_out: np.ndarray | None = None,
-               b_out: np.ndarray | None = None):
+               b_out: np.ndarray | None = None, u_lo_out: np.ndarray | None = None):
         """Enqueue one request; returns its ticket, or None when the memory cap
         refuses it for now (HYTEG_EAGAIN)."""
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int64)
-        for a in (u_out, b_out):
+        for a in (u_out, b_out, u_lo_out):
             if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
-                raise ValueError("u_out / b_out must be C-contiguous float64 arrays")
+                raise ValueError("u_out / b_out / u_lo_out must be C-contiguous float64 arrays")
         req = C.Request(int(coords.shape[1]), coords.shape[0], coords.ctypes.data_as(C.c_dblp), cells.shape[0],
                         cells.ctypes.data_as(C.c_i64p), level, mode, rtol, max_iter, seed, noise,
                         u_out.ctypes.data_as(C.c_dblp) if u_out is not None else None,
-                        b_out.ctypes.data_as(C.c_dblp) if b_out is not None else None)
+                        b_out.ctypes.data_as(C.c_dblp) if b_out is not None else None,
+                        u_lo_out.ctypes.data_as(C.c_dblp) if u_lo_out is not None else None)
         t = ctypes.c_uint64()
         code = C.lib.hyteg_server_submit(self._h, ctypes.byref(req), ctypes.byref(t))
         if code == EAGAIN:
             return None
         C.check(code, "hyteg_server_submit")
-        self._keep[t.value] = (u_out, b_out)
+        self._keep[t.value] = (u_out, b_out, u_lo_out)
         return t.value
 
     def poll(self, ticket: int) -> Result:

@@ -147,6 +147,72 @@ def test_full_size_sampled(cuda, kind):
     check_close(yg[slots], yref, absrow, kind, "L11 sampled")
 
 
+def _tiles_2d(n, th):
+    """The macro-interior tiles of a level as the library cuts them: strips of
+    62 written columns from x = 1, rows chunked by th from y = 1 (64 for the
+    float64 kernels and 16 for fp32 at the benchmark's level)."""
+    out = []
+    for x0 in range(1, n - 1, 62):
+        ymax = n - 1 - x0
+        for y0 in range(1, ymax + 1, th):
+            out.append((x0, y0, min(y0 + th, ymax + 1)))
+    return out
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_full_size_every_tile_stratified(cuda, kind):
+    """Level 11 (67M DoFs), every tile of the launch's work list: the first
+    and last row of the tile at its first and last written column, against
+    the oracle's row-by-row evaluation.  The 32 macros share one tile list;
+    tile i is checked in macro i mod 32, so every macro takes part."""
+    coarse, L, seed = workload("square32jit_L11")
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
+    ns, ng = M.num_slots(L)
+    smap = M.dof_map(L)
+    x = random_vector(ng, seed)
+    if kind == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    yg = gpu_apply(M, L, x[smap], kind)
+    n = 1 << L
+    S = (n + 1) * (n + 2) // 2
+    pts = set()
+    for i, (x0, y0, y1) in enumerate(_tiles_2d(n, 16 if kind == "f32" else 64)):
+        m = i % coarse.n_cells
+        for yy in (y0, y1 - 1):
+            for xx in (x0, min(x0 + 61, n - 1 - yy)):
+                pts.add(m * S + yy * (n + 2) - yy * (yy + 1) // 2 + xx)
+    slots = np.array(sorted(pts))
+    rm = oracle.RefinedMesh(coarse.coords, coarse.cells, L)
+    gids = smap[slots]
+    yref = oracle.row_apply(rm, gids, x)
+    absrow = np.array([_absrow(rm, g, x) for g in gids])
+    check_close(yg[slots], yref, absrow, kind, f"L11 tile corners ({len(slots)} rows)")
+
+
+@pytest.fixture(scope="module")
+def level9_oracle():
+    coarse, _, seed = workload("square32jit_L11", level=9)
+    rm = oracle.RefinedMesh(coarse.coords, coarse.cells, 9)
+    A = oracle.operator_matrix(rm)
+    return coarse, rm, A, seed
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_level9_element_wise(cuda, kind, level9_oracle):
+    """The 32-macro workload at level 9 (4.2M DoFs), element by element: a
+    level whose tiles are cut into 32-row chunks for the float64 kernels."""
+    coarse, rm, A, seed = level9_oracle
+    M = _lib().Mesh(coarse.coords, coarse.cells).refine(9)
+    x = random_vector(rm.n_global, seed)
+    if kind == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    smap = M.dof_map(9)
+    yg = gpu_apply(M, 9, x[smap], kind)
+    y = oracle.spmv(A, x)
+    absrow = abs(A) @ np.abs(x)
+    check_close(yg, y[smap], absrow[smap], kind, "L9 element-wise")
+
+
 def _absrow(rm, g, x):
     """sum_j |a_gj x_j| from the oracle's micro-elements around g."""
     from oracle.assemble import _incidences, _macro_element_matrices

@@ -102,3 +102,76 @@ def test_solve_reaches_1e10(cuda, dim, L, mode):
     # and the solution agrees with the oracle's multigrid solution
     uo, _ = H.solve(b, rtol=1e-12)
     assert np.abs(ug - uo).max() <= 1e-8 * np.abs(uo).max()
+
+
+@pytest.mark.parametrize("mode", ["mixed", "f64"])
+def test_two_part_solve_below_the_float64_floor(cuda, mode):
+    """hyteg_solve_two_part on 32 right-isosceles macro-triangles at level 7:
+    their stencil weights (4, -1, 0) are exact in binary, so the library's
+    operator and the oracle's assembled matrix agree bitwise and the oracle's
+    exactly rounded residual can confirm the two-part solution below the
+    floor that a float64 iterate cannot pass (about 3e-12 at this level; the
+    oracle measures it on u, the float64 rounding of u + u_lo).  On jittered
+    meshes the two operators differ by a few ulps of their entries, which
+    shows in the residual at the size of that same floor."""
+    import torch
+    Hh = _lib()
+    c = unit_square_mesh(4, 0.0, 0)
+    L = 7
+    M = Hh.Mesh(c.coords, c.cells).refine(L).solver_setup(L)
+    H = omg.Hierarchy(c.coords, c.cells, L)
+    b = _rhs(H, L, seed=6)
+    smap = M.dof_map(L)
+    bd = _dev(b[smap], torch.float64)
+    u = torch.zeros_like(bd)
+    ulo = torch.zeros_like(bd)
+    it, rel = M.solve_two_part(L, bd, u, ulo, mode=Hh.SOLVE_MIXED if mode == "mixed" else Hh.SOLVE_F64,
+                               rtol=1e-12, max_iter=80)
+    assert rel <= 1e-12 and it < 80, (it, rel)
+    us, ls = u.cpu().numpy(), ulo.cpu().numpy()
+    order = np.argsort(smap, kind="stable")
+    same = smap[order][1:] == smap[order][:-1]
+    assert np.array_equal(us[order][1:][same], us[order][:-1][same])
+    assert np.array_equal(ls[order][1:][same], ls[order][:-1][same])
+    n = H.meshes[L].n_global
+    ug, lg = np.zeros(n), np.zeros(n)
+    ug[smap], lg[smap] = us, ls
+    assert np.all(np.abs(lg) <= np.spacing(np.abs(ug)))  # u is the float64 rounding of u + u_lo
+    inter = ~H.meshes[L].boundary
+    exact = omg.relres_exact(H.A[L], b, (ug, lg), inter)
+    assert exact <= 1.05e-12 and abs(exact - rel) <= 0.05 * exact + 1e-15, (exact, rel)
+    floor = omg.relres_exact(H.A[L], b, (ug,), inter)
+    est = omg.float64_floor_estimate(H.A[L], b, ug, inter)
+    assert 0.5 * est < floor < 2.0 * est and floor > 2.0 * exact, (floor, est, exact)
+
+
+@pytest.mark.parametrize("mode", ["mixed", "f64"])
+@pytest.mark.parametrize("dim,L", [(2, 6), (3, 4)])
+def test_two_part_solve_jittered(cuda, dim, L, mode):
+    """The two-part solve on jittered meshes reaches 1e-12 on the library's
+    operator; copies agree, u is the float64 rounding of u + u_lo, and the
+    oracle's float64 product confirms the residual to the level at which
+    the two operators' entries differ."""
+    import torch
+    Hh = _lib()
+    c, M, H = _setup(dim, L)
+    b = _rhs(H, L, seed=7)
+    smap = M.dof_map(L)
+    bd = _dev(b[smap], torch.float64)
+    u = torch.zeros_like(bd)
+    ulo = torch.zeros_like(bd)
+    it, rel = M.solve_two_part(L, bd, u, ulo, mode=Hh.SOLVE_MIXED if mode == "mixed" else Hh.SOLVE_F64,
+                               rtol=1e-12, max_iter=80)
+    assert rel <= 1e-12 and it < 80, (it, rel)
+    us, ls = u.cpu().numpy(), ulo.cpu().numpy()
+    order = np.argsort(smap, kind="stable")
+    same = smap[order][1:] == smap[order][:-1]
+    assert np.array_equal(us[order][1:][same], us[order][:-1][same])
+    n = H.meshes[L].n_global
+    ug, lg = np.zeros(n), np.zeros(n)
+    ug[smap], lg[smap] = us, ls
+    assert np.all(np.abs(lg) <= np.spacing(np.abs(ug)))
+    inter = ~H.meshes[L].boundary
+    exact = omg.relres_exact(H.A[L], b, (ug, lg), inter)
+    est = omg.float64_floor_estimate(H.A[L], b, ug, inter)
+    assert exact <= 1e-12 + 4.0 * est, (exact, est)
