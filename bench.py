@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "GDoF-updates/s of A*x (P1 stiffness apply, distinct DoFs)"
 UNIT = "GDoF/s"
 WORKLOAD = "square32jit_L11"
+FP64_PEAK_GOPS = 625.0  # nominal GB300 dense fp64: 1.25 TFLOP/s, an FMA counting two
 CPU_SAMPLE_LEVEL = 10  # the oracle's sample of the 2D workload (assembly takes about a minute)
 
 
@@ -50,7 +51,7 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "f64_ieee"])
     p.add_argument("--level", type=int, default=None,
                    help="override the refinement level (smaller cases for ncu captures; not a bench line)")
-    p.add_argument("--serve-requests", type=int, default=512,
+    p.add_argument("--serve-requests", type=int, default=4096,
                    help="requests of the solve-server workload timed after the apply (0: skip)")
     p.add_argument("--serve-workers", type=int, default=8)
     p.add_argument("--profile", action="store_true",
@@ -373,7 +374,7 @@ def solve_workload(device, stream, reps=3, rtol=1e-10):
 
 
 # ---------------------------------------------------------------- solve server
-def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=None):
+def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=None, rate=2000.0):
     """The solve server under the synthetic request stream of inputs.serving:
     Poisson arrivals at 2000/s, half 2D (4..64 macro-triangles, levels 5..10),
     half 3D (6..384 macro-tets, levels 3..6), each request a lumped-mass
@@ -389,7 +390,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
     if mode is None:
         mode = H.SOLVE_MIXED
     from inputs.serving import request_stream, coarse_mesh
-    reqs = request_stream(n_requests)
+    reqs = request_stream(n_requests, rate=rate)
     ng_of = {}
     for q in reqs:  # DoF counts from the library's host-side layout (untimed)
         key = (q.dim, q.shape, q.level)
@@ -472,6 +473,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
                      + ("fp32 V(3,3) cycles in float64 refinement" if mode == H.SOLVE_MIXED else
                         "float64 V(3,3) cycles") + "; every solution copied to host memory; "
                      f"{workers} worker streams, {cap_bytes >> 30} GiB device arena"),
+        "offered_rate_per_s": rate,
         "solves_per_s": len(lat) / span, "gdofs_solved_per_s": float(np.sum(ngs)) / span / 1e9,
         "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
         "service_ms_p50": pct(run, 50), "service_ms_p99": pct(run, 99), "queue_ms_p50": pct(queue_s, 50),
@@ -678,6 +680,20 @@ def main():
                 "interior_ms": rv["interior_ms"], "interface_ms": rv["iface_ms"]})
             if v["kernel"] == "k_slab3d":  # the work split the refinement's autotuner picked
                 variants[-1]["slab_z_ranges_per_macro"] = v["M"].autotune_choice(v["L"], vcode)
+            if name == WORKLOAD and vcode == H.F64_IEEE:
+                # the native fp64 apply is bound by the fp64 pipe: 7 fp64
+                # operations per macro-interior point (one multiply, three
+                # adds of opposite neighbours, three FMAs) against the fp64
+                # peak of the GB300 (1.25 TFLOP/s dense = 625 G FMA/s)
+                ops = 7.0 * v["interior"]
+                achieved = ops / (rv["interior_ms"] * 1e-3) / 1e9
+                line["roofline_native_fp64"] = {
+                    "bound": "alu", "kernel": f"{v['kernel']} (f64_ieee)", "achieved": achieved,
+                    "peak": FP64_PEAK_GOPS, "unit": "G fp64 ops/s", "frac": achieved / FP64_PEAK_GOPS,
+                    "peak_kind": "nominal dense fp64 (1.25 TFLOP/s / 2 flops per FMA)",
+                    "ops_per_launch": ops, "interior_ms": rv["interior_ms"],
+                    "GDoF_per_s": variants[-1]["value"],
+                    "hbm_frac": variants[-1]["interior_frac"]}
             del v
             torch.cuda.empty_cache()
         line["variants"] = variants
@@ -705,6 +721,13 @@ def main():
         # the mixed-precision server is compared with
         line["serving_fp64_cycles"] = serve_workload(args.serve_requests, args.serve_workers,
                                                      mode=H.SOLVE_F64)
+        # below capacity: the same stream offered at 25 % and 50 % of the
+        # measured solves/s, so that latency shows service rather than queueing
+        cap = line["serving"]["solves_per_s"]
+        n_low = min(args.serve_requests, 256)
+        line["serving_load_levels"] = [
+            {k: v for k, v in serve_workload(n_low, args.serve_workers, rate=f * cap).items() if k != "workload"}
+            | {"load_fraction": f} for f in (0.25, 0.5)]
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         r = cpu_oracle_run(10, 2)

@@ -441,6 +441,13 @@ typedef struct hyteg_server_stats {
 
 int hyteg_server_stats_get(hyteg_server* server, hyteg_server_stats* out);
 
+/* Makes the next `count` allocations from the server's device arena fail, as
+ * if the arena were exhausted (host-side fault injection for testing the
+ * failure paths; no device memory or GPU state is touched).  A request whose
+ * build meets such a failure while no other request holds memory fails at
+ * once with HYTEG_ENOMEM.  Errors: HYTEG_EINVAL (NULL server, count < 0). */
+int hyteg_server_inject_alloc_failures(hyteg_server* server, int count);
+
 /* Stops the server: queued requests fail with HYTEG_ESTATE, running ones are
  * finished, the workers are joined and all device memory is released. */
 void hyteg_server_destroy(hyteg_server* server);

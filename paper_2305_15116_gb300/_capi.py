@@ -127,6 +127,8 @@ lib.hyteg_server_release.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
 lib.hyteg_server_release.restype = ctypes.c_int
 lib.hyteg_server_stats_get.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerStats)]
 lib.hyteg_server_stats_get.restype = ctypes.c_int
+lib.hyteg_server_inject_alloc_failures.argtypes = [ctypes.c_void_p, ctypes.c_int]
+lib.hyteg_server_inject_alloc_failures.restype = ctypes.c_int
 lib.hyteg_server_destroy.argtypes = [ctypes.c_void_p]
 lib.hyteg_server_destroy.restype = None
 lib.hyteg_last_error.argtypes = []

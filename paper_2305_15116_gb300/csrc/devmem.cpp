@@ -20,6 +20,7 @@ struct Arena {
   size_t used = 0;
   std::map<size_t, size_t> free_blocks;            // offset -> size, coalesced
   std::unordered_map<size_t, size_t> live;         // offset -> size
+  int fail_next = 0;                               // injected failures still to come
   std::mutex mu;
 };
 
@@ -51,6 +52,10 @@ void arena_destroy(Arena* a) {
 void* arena_alloc(Arena* a, size_t bytes) {
   const size_t need = round_up(bytes ? bytes : 1);
   std::lock_guard<std::mutex> lk(a->mu);
+  if (a->fail_next > 0) {  // a failure injected on the host (testing the failure paths)
+    --a->fail_next;
+    return nullptr;
+  }
   for (auto it = a->free_blocks.begin(); it != a->free_blocks.end(); ++it) {
     if (it->second < need) continue;
     const size_t off = it->first, sz = it->second;
@@ -61,6 +66,11 @@ void* arena_alloc(Arena* a, size_t bytes) {
     return a->base + off;
   }
   return nullptr;
+}
+
+void arena_inject_failures(Arena* a, int count) {
+  std::lock_guard<std::mutex> lk(a->mu);
+  a->fail_next = count > 0 ? count : 0;
 }
 
 void arena_free(Arena* a, void* p) {

@@ -251,6 +251,8 @@ cudaError_t launch_p2_apply(const Mesh& m, int level, int dtype, const void* x, 
 Arena* arena_create(size_t bytes, std::string& err);
 void arena_destroy(Arena* a);
 void* arena_alloc(Arena* a, size_t bytes);
+// The next `count` arena_alloc calls fail (host-side fault injection).
+void arena_inject_failures(Arena* a, int count);
 void arena_free(Arena* a, void* p);
 size_t arena_used(Arena* a);
 size_t arena_largest_free(Arena* a);

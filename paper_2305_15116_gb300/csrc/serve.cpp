@@ -181,7 +181,10 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
         if (region || !evict_one()) break;
       }
       if (!region) {
-        if (Clock::now() > deadline || cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+        // only another request in flight can hand memory back: with none, fail now
+        const bool others = submitted - done - failed > 1;
+        if (!others || Clock::now() > deadline ||
+            cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
           *err = HYTEG_ENOMEM;
           *msg = "device arena exhausted";
           return nullptr;
@@ -239,7 +242,8 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
     // the mesh outgrew its region and the arena: drop an idle mesh and retry
     std::unique_lock<std::mutex> lk(mu);
     if (evict_one()) continue;
-    if (Clock::now() > deadline || cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+    const bool others = submitted - done - failed > 1;
+    if (!others || Clock::now() > deadline || cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
       *err = HYTEG_ENOMEM;
       *msg = "device arena exhausted: " + why;
       return nullptr;
@@ -474,6 +478,12 @@ int hyteg_server_release(hyteg_server* sv, uint64_t ticket) {
   const int st = it->second->res.status;
   if (st != HYTEG_REQ_DONE && st != HYTEG_REQ_FAILED) return sfail(HYTEG_ESTATE, "request not finished");
   sv->reqs.erase(it);
+  return HYTEG_OK;
+}
+
+int hyteg_server_inject_alloc_failures(hyteg_server* sv, int count) {
+  if (!sv || count < 0) return sfail(HYTEG_EINVAL, "NULL server or negative count");
+  hyteg::arena_inject_failures(sv->arena, count);
   return HYTEG_OK;
 }
 

@@ -85,6 +85,10 @@ class Server:
         C.check(C.lib.hyteg_server_release(self._h, ticket), "hyteg_server_release")
         self._keep.pop(ticket, None)
 
+    def inject_alloc_failures(self, count: int) -> None:
+        """The next `count` arena allocations fail (host-side fault injection)."""
+        C.check(C.lib.hyteg_server_inject_alloc_failures(self._h, count), "hyteg_server_inject_alloc_failures")
+
     def stats(self) -> dict:
         s = C.ServerStats()
         C.check(C.lib.hyteg_server_stats_get(self._h, ctypes.byref(s)), "hyteg_server_stats_get")

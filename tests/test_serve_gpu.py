@@ -173,3 +173,42 @@ def test_server_admission_and_errors(cuda):
         t4 = sv.submit(bad, big.cells, 3, 1)
         r4 = sv.wait(t4, 300)
         assert r4.status == H.REQ_FAILED and r4.error == -4
+
+
+def test_server_wait_times_out_deterministically(cuda):
+    """One worker: a request queued behind a long one (a level-10 solve on
+    32 macros, which takes far longer than a millisecond to build and solve)
+    cannot finish within 1 ms: the bounded wait reports HYTEG_ETIMEDOUT and
+    the request is still queued."""
+    H = _lib()
+    big, small = rect_mesh(4, 4, 0.15, 0), rect_mesh(2, 1, 0.15, 1)
+    with _server(workers=1) as sv:
+        t1 = sv.submit(big.coords, big.cells, 10, 1, 0.1, rtol=1e-9)
+        t2 = sv.submit(small.coords, small.cells, 4, 2, 0.1, rtol=1e-9)
+        assert t1 is not None and t2 is not None
+        assert sv.wait(t2, 0.001) is None  # HYTEG_ETIMEDOUT
+        assert sv.poll(t2).status == H.REQ_QUEUED
+        with pytest.raises(H.HytegError) as ei:
+            sv.release(t2)  # not finished
+        assert ei.value.code == -5
+        assert sv.wait(t1, 300).status == H.REQ_DONE
+        assert sv.wait(t2, 300).status == H.REQ_DONE
+
+
+def test_server_allocation_failure_is_reported(cuda):
+    """A device allocation that fails inside the server (injected on the host:
+    the arena refuses the next allocation) fails that request with
+    HYTEG_ENOMEM at once; the server keeps serving the next request."""
+    H = _lib()
+    coarse = rect_mesh(3, 2, 0.15, 4)
+    with _server(workers=1) as sv:
+        sv.inject_alloc_failures(1)
+        t1 = sv.submit(coarse.coords, coarse.cells, 5, 1, 0.1, rtol=1e-9)
+        r1 = sv.wait(t1, 300)
+        assert r1.status == H.REQ_FAILED and r1.error == -2, r1
+        assert "arena" in r1.message
+        t2 = sv.submit(coarse.coords, coarse.cells, 5, 2, 0.1, rtol=1e-9)
+        r2 = sv.wait(t2, 300)
+        assert r2.status == H.REQ_DONE and r2.relres <= 1e-9
+        s = sv.stats()
+        assert s["failed"] == 1 and s["done"] == 1
