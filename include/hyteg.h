@@ -109,22 +109,25 @@ int hyteg_mesh_create(int dim, int64_t n_verts, const double* coords, int64_t n_
  * interface tables and the kernels' work lists.  Allocates a few small device
  * tables with cudaMalloc (size O(cells * levels + interface primitives)),
  * owned by the mesh.  Synchronous.  May be called again with a larger level.
- * 3D levels of at least 2^20 slots with n <= 64 are autotuned here: the slab
- * kernel is timed on two scratch float64 vectors of the level's size (freed
- * before returning) for several work splits (float-float and fp32; native
- * fp64 takes the float-float choice), and the fastest split is kept (choices
- * cached per macro count and level for the process; see
- * hyteg_autotune_choice).  Meshes built by the solve server only take cached
- * choices: their timings would run among other requests' kernels.
+ * Levels of at least 2^20 slots are autotuned here: the 3D slab kernel (n <=
+ * 64) for several work splits (float-float and fp32; native fp64 takes the
+ * float-float choice), the 2D kernel for tiles of 8, 16, 32 and 64 rows (each
+ * element type), timed on two scratch float64 vectors of the level's size
+ * (freed before returning); the fastest is kept (choices cached per macro
+ * count and level for the process; see hyteg_autotune_choice).  Meshes built
+ * by the solve server only take cached choices: their timings would run
+ * among other requests' kernels.
  * Errors: HYTEG_EINVAL (max_level < 0 or > 15), HYTEG_ECUDA, HYTEG_ENOMEM. */
 int hyteg_mesh_refine(hyteg_mesh* mesh, int max_level);
 
-/* The work split the autotuner picked for the 3D slab kernel on `level` and
- * element type `dtype` (HYTEG_F64, HYTEG_F32, HYTEG_F64_IEEE): the number of
- * z-ranges every macro-tetrahedron is cut into, one thread block each; 0 when
- * the level was not autotuned (2D, n > 64, or fewer than 2^20 slots: two
- * z-ranges).  Errors: HYTEG_EINVAL (null, dtype), HYTEG_ESTATE (level not
- * refined). */
+/* What the autotuner picked on `level` for element type `dtype` (HYTEG_F64,
+ * HYTEG_F32, HYTEG_F64_IEEE).  3D: the number of z-ranges every
+ * macro-tetrahedron is cut into for the slab kernel, one thread block each;
+ * 0 when the level was not autotuned (n > 64, or fewer than 2^20 slots: two
+ * z-ranges).  2D: the rows per macro-interior tile (8, 16, 32 or 64), timed
+ * on levels of at least 2^20 slots; 0 when the level keeps the default
+ * tiles (64 rows for float64, 16 for fp32, fewer on levels with few tiles).
+ * Errors: HYTEG_EINVAL (null, dtype), HYTEG_ESTATE (level not refined). */
 int hyteg_autotune_choice(const hyteg_mesh* mesh, int level, int dtype, int* value);
 
 /* Frees the mesh and its device tables (synchronises the device first). */
@@ -157,6 +160,20 @@ int hyteg_dof_map(const hyteg_mesh* mesh, int level, int64_t* global_id);
  * HYTEG_ESTATE (level not refined), HYTEG_ECUDA (launch failure). */
 int hyteg_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y,
                 void* stream);
+
+/* hyteg_apply without the interface step: y = A x at the points inside the
+ * macros, while every copy of a point on a macro vertex, edge or (3D) face
+ * holds its own macro's PARTIAL row — the stencil restricted to that macro's
+ * micro-elements (its boundary class) — and no Dirichlet row is applied.
+ * Summing the copies of such a point in ascending macro order, from zero,
+ * gives hyteg_apply's value bitwise; a Dirichlet point's value is x.  The
+ * building block of an apply over macros partitioned across processes
+ * (one block of macros per process, the interface partials exchanged between
+ * neighbours, Sec. 6's one macro per process): a partition of a mesh gives
+ * every process a mesh of its own cells (HYTEG_BC_NONE), whose partial
+ * rows are those of the whole mesh.  Arguments, layout and errors as
+ * hyteg_apply. */
+int hyteg_apply_partial(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream);
 
 /* y_i = A_i x_i for `count` independent products (meshes[i] on level
  * levels[i], device vectors xs[i] -> ys[i], all of element type `dtype`):

@@ -41,6 +41,9 @@ lib.hyteg_dof_map.restype = ctypes.c_int
 lib.hyteg_apply.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                             ctypes.c_void_p]
 lib.hyteg_apply.restype = ctypes.c_int
+lib.hyteg_apply_partial.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]
+lib.hyteg_apply_partial.restype = ctypes.c_int
 lib.hyteg_apply_timed.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
 lib.hyteg_apply_timed.restype = ctypes.c_int

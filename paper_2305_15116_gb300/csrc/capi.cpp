@@ -115,6 +115,9 @@ int hyteg_mesh_refine(hyteg_mesh* mesh, int max_level) {
       if (m.dim == 3) {  // pick the 3D slab kernel's work split for this level
         e = hyteg::slab3d_autotune(m, m.levels.back());
         if (e != cudaSuccess) return cuda_fail(e, "slab work-split autotuning");
+      } else {  // and the 2D kernel's tile height
+        e = hyteg::tiles2d_autotune(m, m.levels.back());
+        if (e != cudaSuccess) return cuda_fail(e, "2D tile autotuning");
       }
     }
     e = hyteg::dev_sync(m);
@@ -152,7 +155,8 @@ int hyteg_autotune_choice(const hyteg_mesh* mesh, int level, int dtype, int* val
   if (int r = check_level(mesh, level)) return r;
   if (!value) return fail(HYTEG_EINVAL, "value is NULL");
   if (dtype != HYTEG_F64 && dtype != HYTEG_F32 && dtype != HYTEG_F64_IEEE) return fail(HYTEG_EINVAL, "bad dtype");
-  *value = mesh->m.levels[level].slab_chunks[dtype];
+  const hyteg::LevelDev& L = mesh->m.levels[level];
+  *value = mesh->m.dim == 3 ? L.slab_chunks[dtype] : L.tile_rows[dtype];
   return HYTEG_OK;
 }
 
@@ -198,6 +202,20 @@ int hyteg_apply_timed(const hyteg_mesh* mesh, int level, int dtype, const void* 
 
 int hyteg_apply(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream) {
   return hyteg_apply_timed(mesh, level, dtype, x, y, stream, nullptr, nullptr, nullptr);
+}
+
+int hyteg_apply_partial(const hyteg_mesh* mesh, int level, int dtype, const void* x, void* y, void* stream) {
+  if (int r = check_level(mesh, level)) return r;
+  if (!valid_dtype(dtype)) return fail(HYTEG_EINVAL, "unknown dtype");
+  if (!x || !y) return fail(HYTEG_EINVAL, "x or y is NULL");
+  const hyteg::Mesh& m = mesh->m;
+  const size_t bytes = size_t(m.n_cells) * size_t(hyteg::slots_per_macro(m.dim, level)) * elem_size(dtype);
+  const char* xb = static_cast<const char*>(x);
+  const char* yb = static_cast<const char*>(y);
+  if (xb < yb + bytes && yb < xb + bytes) return fail(HYTEG_EINVAL, "x and y overlap");
+  const char* what = "";
+  const cudaError_t e = hyteg::launch_apply_partial(m, level, dtype, x, y, static_cast<cudaStream_t>(stream), &what);
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, what);
 }
 
 int hyteg_apply_batch(const hyteg_mesh* const* meshes, const int* levels, int dtype, const void* const* xs,

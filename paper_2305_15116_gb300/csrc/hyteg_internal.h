@@ -45,6 +45,11 @@ struct LevelDev {
   int n_tiles = 0;                 // per macro
   int4* tiles32 = nullptr;         // the fp32 kernels' list (shorter row chunks)
   int n_tiles32 = 0;               // per macro
+  // per element type (1 float-float, 2 fp32, 3 native fp64): the tile list
+  // the 2D autotuner picked (nullptr: tiles / tiles32), and its rows per tile
+  int4* tiles_dt[4] = {nullptr, nullptr, nullptr, nullptr};
+  int n_tiles_dt[4] = {0, 0, 0, 0};
+  int tile_rows[4] = {0, 0, 0, 0};
   // interface work list: int4 (prim, b, a0, a1)
   int4* items = nullptr;
   int n_items = 0;
@@ -238,6 +243,17 @@ std::vector<int4> slab_work_list(int n, int64_t n_cells, int chunks);
 // type and keep the fastest list (levels of at least 2^20 slots; results are
 // cached per (macro count, level size) for the process).  Synchronous.
 cudaError_t slab3d_autotune(Mesh& m, LevelDev& L);
+// The 2D macro-interior tiles of one macro (same list for every macro):
+// strips of 62 columns from x = 1, rows cut into chunks of `rows`, ordered
+// row chunk by row chunk.
+std::vector<int4> tile_list_2d(int n, int rows);
+cudaError_t tiles2d_autotune(Mesh& m, LevelDev& L);
+// the 2D apply over an explicit tile list (the autotuner's candidates)
+cudaError_t launch_apply2d_tiles(int dtype, const Mesh& m, const LevelDev& L, const int4* tiles, int n_tiles,
+                                 const void* x, void* y, cudaStream_t s);
+// the 2D apply with every interface copy left holding its macro's partial row
+cudaError_t launch_apply2d_partial(int dtype, const Mesh& m, const LevelDev& L, const void* x, void* y,
+                                   cudaStream_t s);
 void free_level(const Mesh& m, LevelDev& L);
 
 // ---- P2 (p2_setup.cpp, p2.cu) ------------------------------------------------
@@ -316,6 +332,10 @@ cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const Lev
 // null, is recorded between them.  Returns the failing step in *what.
 cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
                          cudaEvent_t ev_mid, const char** what);
+// The apply without the interface sum: every copy of an interface point holds
+// its own macro's partial row (no Dirichlet rows).
+cudaError_t launch_apply_partial(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
+                                 const char** what);
 
 }  // namespace hyteg
 

@@ -244,4 +244,17 @@ cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, voi
   return launch_interface_reduce(dtype, m.dim, m, L, x, y, s);
 }
 
+cudaError_t launch_apply_partial(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
+                                 const char** what) {
+  const LevelDev& L = m.levels[level];
+  if (dtype == 1 && !L.ff_ok) dtype = 3;  // weights outside the float-float range: native fp64
+  if (m.dim == 2) {
+    *what = "2D apply kernel (partial rows)";
+    return launch_apply2d_partial(dtype, m, L, x, y, s);
+  }
+  // 3D: the slab or row kernel writes the partial rows; no reduction
+  *what = "3D kernel";
+  return L.n_slabs > 0 ? launch_slab3d(dtype, L, x, y, s) : launch_row3d(dtype, L, m.n_cells, x, y, s);
+}
+
 }  // namespace hyteg

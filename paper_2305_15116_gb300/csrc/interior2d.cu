@@ -79,7 +79,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //   MODE_JACOBI:   y = u + omega dinv (b - A u)   (one weighted Jacobi sweep)
 //   MODE_RESIDUAL: y = b - A u
 // (u = x at the point; b and dinv in the slot layout, copies equal).
-constexpr int MODE_APPLY = 0, MODE_JACOBI = 1, MODE_RESIDUAL = 2;
+//   MODE_PARTIAL:  y = A u inside the macros; at interface points every copy
+//                  receives its own macro's partial row instead of the sum
+constexpr int MODE_APPLY = 0, MODE_JACOBI = 1, MODE_RESIDUAL = 2, MODE_PARTIAL = 3;
 
 struct ModeArgs {
   const void* b;
@@ -133,6 +135,25 @@ __device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __rest
     if (p.type == 1 && inc.corner[1] >= 1) q[inc.corner[1] - 1] += wv1;
   };
   T acc = T(0);
+  if (MODE == MODE_PARTIAL) {  // each copy keeps its own macro's partial row
+    for (int i = 0; i < p.inc_count; ++i) {
+      const Inc inc = incs[p.inc_begin + i];
+      int q[2];
+      local(inc, q);
+      const int cls = (q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[0] + q[1] == n ? 4 : 0);
+      const int64_t base = (int64_t)inc.cell * S;
+      const int64_t wb = ((int64_t)inc.cell * NCLS2 + cls) * NW2;
+      T part = T(0);
+#pragma unroll
+      for (int k = 0; k < NW2; ++k) {
+        const int dx = c_if_off[k][0], dy = c_if_off[k][1];
+        if (((cls & 1) && dx < 0) || ((cls & 2) && dy < 0) || ((cls & 4) && dx + dy > 0)) continue;
+        part = if_fma(if_w(st, wb + k, T(0)), __ldg(x + base + if_slot(n, q[0] + dx, q[1] + dy)), part);
+      }
+      y[base + if_slot(n, q[0], q[1])] = part;
+    }
+    return;
+  }
   if (p.boundary) {
     int q[2];
     local(incs[p.inc_begin], q);
@@ -155,7 +176,7 @@ __device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __rest
       acc += part;
     }
   }
-  if (MODE != MODE_APPLY) {  // copies hold equal u, b and dinv: use the first
+  if (MODE == MODE_JACOBI || MODE == MODE_RESIDUAL) {  // copies hold equal u, b and dinv: use the first
     int q[2];
     local(incs[p.inc_begin], q);
     acc = mode_out<MODE>(acc, x, md, (int64_t)incs[p.inc_begin].cell * S + if_slot(n, q[0], q[1]));
@@ -200,7 +221,7 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
                                               typename P::T (*ringb_all)[RING][32][2]) {
   using T = typename P::T;
   constexpr int THR = Thr2<MODE>::value;
-  constexpr bool SWEEP = MODE != MODE_APPLY;
+  constexpr bool SWEEP = MODE == MODE_JACOBI || MODE == MODE_RESIDUAL;
   static_assert(!SWEEP || sizeof(T) == 4, "the sweep modes are built for fp32");
   if (block < n_if_blocks) {
     const int item = (THR / 128) * block + (int)(threadIdx.x >> 7);
@@ -339,7 +360,7 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
                                                           ModeArgs md) {
   using T = typename P::T;
   constexpr int THR = Thr2<MODE>::value;
-  constexpr bool SWEEP = MODE != MODE_APPLY;
+  constexpr bool SWEEP = MODE == MODE_JACOBI || MODE == MODE_RESIDUAL;
   __shared__ T ring_all[THR / 32][RING][32][2];
   __shared__ T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
   apply2d_block<P, MODE>((int)blockIdx.x, x, y, tiles, n_tiles, n_warps, S, n, st, items, n_items, prims, incs,
@@ -389,11 +410,30 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d_batch(const __grid_con
                                d.n_items, d.prims, d.incs, d.n_if_blocks, md, ring_all, ring_all);
 }
 
+// Element-type index of a policy (1 float-float, 2 fp32, 3 native fp64).
+template <class P>
+constexpr int dt_of() {
+  return sizeof(typename P::T) == 4 ? 2 : (P::kPoison ? 1 : 3);
+}
+
+// The tile list of a level for a policy: the autotuned one when present,
+// else the default list of its element size.
+template <class P>
+__host__ void tiles_of(const LevelDev& L, const int4** tiles, int* n_tiles) {
+  constexpr int dt = dt_of<P>();
+  if (L.tiles_dt[dt]) {
+    *tiles = L.tiles_dt[dt];
+    *n_tiles = L.n_tiles_dt[dt];
+  } else {
+    const bool f32 = dt == 2;
+    *tiles = f32 ? L.tiles32 : L.tiles;
+    *n_tiles = f32 ? L.n_tiles32 : L.n_tiles;
+  }
+}
+
 template <class P, int MODE>
-cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s, const ModeArgs& md) {
-  const bool f32 = sizeof(typename P::T) == 4;
-  const int4* tiles = f32 ? L.tiles32 : L.tiles;
-  const int n_tiles = f32 ? L.n_tiles32 : L.n_tiles;
+cudaError_t launch_on(const Mesh& m, const LevelDev& L, const int4* tiles, int n_tiles, const void* x, void* y,
+                      cudaStream_t s, const ModeArgs& md) {
   const int64_t n_warps = (int64_t)n_tiles * m.n_cells;
   const int threads = Thr2<MODE>::value;
   const int64_t int_blocks = (n_warps * 32 + threads - 1) / threads;
@@ -407,6 +447,14 @@ cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cud
   return cudaGetLastError();
 }
 
+template <class P, int MODE>
+cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s, const ModeArgs& md) {
+  const int4* tiles = nullptr;
+  int n_tiles = 0;
+  tiles_of<P>(L, &tiles, &n_tiles);
+  return launch_on<P, MODE>(m, L, tiles, n_tiles, x, y, s, md);
+}
+
 template <class P>
 cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const void* const* xs, void* const* ys,
                            int count, cudaStream_t s) {
@@ -417,8 +465,9 @@ cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const v
     for (int i = i0; i < count && i < i0 + BATCH2D; ++i) {
       const Mesh& m = *meshes[i];
       const LevelDev& L = m.levels[levels[i]];
-      const bool f32 = sizeof(typename P::T) == 4;
-      const int n_tiles = f32 ? L.n_tiles32 : L.n_tiles;
+      const int4* tiles = nullptr;
+      int n_tiles = 0;
+      tiles_of<P>(L, &tiles, &n_tiles);
       const int64_t n_warps = (int64_t)n_tiles * m.n_cells;
       const int64_t int_blocks = (n_warps * 32 + THREADS2D - 1) / THREADS2D;
       const int if_blocks = (L.n_items + THREADS2D / 128 - 1) / (THREADS2D / 128);
@@ -427,7 +476,7 @@ cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const v
       Apply2dDesc& d = b.d[b.count++];
       d.x = xs[i];
       d.y = ys[i];
-      d.tiles = f32 ? L.tiles32 : L.tiles;
+      d.tiles = tiles;
       d.items = L.items;
       d.prims = m.d_prims;
       d.incs = m.d_incs;
@@ -457,6 +506,28 @@ cudaError_t launch_apply2d(int dtype, const Mesh& m, const LevelDev& L, const vo
     case 1: return launch<ArF64FF, MODE_APPLY>(m, L, x, y, s, md);
     case 2: return launch<ArF32, MODE_APPLY>(m, L, x, y, s, md);
     case 3: return launch<ArF64Native, MODE_APPLY>(m, L, x, y, s, md);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_apply2d_partial(int dtype, const Mesh& m, const LevelDev& L, const void* x, void* y,
+                                   cudaStream_t s) {
+  const ModeArgs md{nullptr, nullptr, 0.0};
+  switch (dtype) {
+    case 1: return launch<ArF64FF, MODE_PARTIAL>(m, L, x, y, s, md);
+    case 2: return launch<ArF32, MODE_PARTIAL>(m, L, x, y, s, md);
+    case 3: return launch<ArF64Native, MODE_PARTIAL>(m, L, x, y, s, md);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_apply2d_tiles(int dtype, const Mesh& m, const LevelDev& L, const int4* tiles, int n_tiles,
+                                 const void* x, void* y, cudaStream_t s) {
+  const ModeArgs md{nullptr, nullptr, 0.0};
+  switch (dtype) {
+    case 1: return launch_on<ArF64FF, MODE_APPLY>(m, L, tiles, n_tiles, x, y, s, md);
+    case 2: return launch_on<ArF32, MODE_APPLY>(m, L, tiles, n_tiles, x, y, s, md);
+    case 3: return launch_on<ArF64Native, MODE_APPLY>(m, L, tiles, n_tiles, x, y, s, md);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -316,6 +316,7 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.st_lo);
   dev_free(m, L.tiles);
   dev_free(m, L.tiles32);
+  for (int t = 0; t < 4; ++t) dev_free(m, L.tiles_dt[t]);
   dev_free(m, L.items);
   dev_free(m, L.slabs);
   for (int t = 0; t < 4; ++t) dev_free(m, L.slabs_dt[t]);
@@ -332,6 +333,21 @@ void free_level(const Mesh& m, LevelDev& L) {
   dev_free(m, L.p2_items);
   dev_free(m, L.p2_tiles);
   L = LevelDev{};
+}
+
+std::vector<int4> tile_list_2d(int n, int rows) {
+  constexpr int TW2 = 62;
+  std::vector<int4> tl;
+  for (int x0 = 1; x0 <= n - 2; x0 += TW2) {
+    const int ymax = n - 1 - x0;
+    for (int y0 = 1; y0 <= ymax; y0 += rows) tl.push_back(make_int4(x0, y0, std::min(y0 + rows, ymax + 1), 0));
+  }
+  // rows of neighbouring strips run side by side, so halo rows hit in L2
+  std::stable_sort(tl.begin(), tl.end(), [](const int4& p, const int4& q) {
+    if (p.y != q.y) return p.y < q.y;
+    return p.x < q.x;
+  });
+  return tl;
 }
 
 bool ff_weights_in_range(const std::vector<double>& st, int per_stencil) {
@@ -475,16 +491,7 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
     };
     int th = th_max;
     while (th > 8 && n_warps(th) < 16 * int64_t(sms)) th /= 2;
-    for (int x0 = 1; x0 <= n - 2; x0 += TW2) {
-      const int ymax = n - 1 - x0;
-      for (int y0 = 1; y0 <= ymax; y0 += th) tl.push_back(make_int4(x0, y0, std::min(y0 + th, ymax + 1), 0));
-    }
-    // rows of neighbouring strips run side by side, so halo rows hit in L2
-    std::stable_sort(tl.begin(), tl.end(), [](const int4& p, const int4& q) {
-      if (p.y != q.y) return p.y < q.y;
-      return p.x < q.x;
-    });
-    return tl;
+    return tile_list_2d(n, th);
   };
   std::vector<int4> tiles = strips(64), tiles32 = strips(16);
   L.n_tiles32 = int(tiles32.size());

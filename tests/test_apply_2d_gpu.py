@@ -161,10 +161,11 @@ def _tiles_2d(n, th):
 
 @pytest.mark.parametrize("kind", KINDS)
 def test_full_size_every_tile_stratified(cuda, kind):
-    """Level 11 (67M DoFs), every tile of the launch's work list: the first
-    and last row of the tile at its first and last written column, against
-    the oracle's row-by-row evaluation.  The 32 macros share one tile list;
-    tile i is checked in macro i mod 32, so every macro takes part."""
+    """Level 11 (67M DoFs), every tile of the launch's work list (the tile
+    height the refinement's autotuner picked): the first and last row of the
+    tile at its first and last written column, against the oracle's
+    row-by-row evaluation.  The 32 macros share one tile list; tile i is
+    checked in macro i mod 32, so every macro takes part."""
     coarse, L, seed = workload("square32jit_L11")
     M = _lib().Mesh(coarse.coords, coarse.cells).refine(L)
     ns, ng = M.num_slots(L)
@@ -175,8 +176,11 @@ def test_full_size_every_tile_stratified(cuda, kind):
     yg = gpu_apply(M, L, x[smap], kind)
     n = 1 << L
     S = (n + 1) * (n + 2) // 2
+    H = _lib()
+    rows = M.autotune_choice(L, {"f64": H.F64, "f32": H.F32, "f64_ieee": H.F64_IEEE}[kind])
+    assert rows in (8, 16, 32, 64)  # the level was autotuned
     pts = set()
-    for i, (x0, y0, y1) in enumerate(_tiles_2d(n, 16 if kind == "f32" else 64)):
+    for i, (x0, y0, y1) in enumerate(_tiles_2d(n, rows)):
         m = i % coarse.n_cells
         for yy in (y0, y1 - 1):
             for xx in (x0, min(x0 + 61, n - 1 - yy)):
@@ -211,6 +215,20 @@ def test_level9_element_wise(cuda, kind, level9_oracle):
     y = oracle.spmv(A, x)
     absrow = abs(A) @ np.abs(x)
     check_close(yg, y[smap], absrow[smap], kind, "L9 element-wise")
+
+
+def test_tile_autotuner_choices(cuda):
+    """Levels of at least 2^20 slots get an autotuned tile height per element
+    type; smaller levels keep the default tiles (choice 0).  The level-9
+    element-wise test above runs the autotuned lists."""
+    H = _lib()
+    coarse = unit_square_mesh(4, 0.15, 0)
+    M = H.Mesh(coarse.coords, coarse.cells).refine(9)
+    for L, tuned in ((6, False), (7, False), (8, True), (9, True)):  # 32 x 8,385 slots at level 7 < 2^20
+        for dt in (H.F64, H.F32, H.F64_IEEE):
+            c = M.autotune_choice(L, dt)
+            assert (c in (8, 16, 32, 64)) if tuned else c == 0, (L, dt, c)
+    M.close()
 
 
 def _absrow(rm, g, x):
