@@ -167,6 +167,16 @@ def setup(name, device, dtype_code, level=None):
     n = 1 << L
     interior = coarse.n_cells * ((n - 1) * (n - 2) // 2 if coarse.dim == 2 else (n - 1) * (n - 2) * (n - 3) // 6)
     slab = True  # every apply kernel writes every slot (interface copies included)
+    # the library's kernel launches per apply: 2D one (macro interiors and
+    # interface points together); 3D the slab kernel (or the row kernel and
+    # its row-end companion) and the interface reduction; P2 the row and
+    # boundary kernels and the vertex and edge reductions
+    if p2:
+        launches = 4
+    elif coarse.dim == 2:
+        launches = 1
+    else:
+        launches = 2 if n <= 64 else 3
     if p2:
         kernel = "k_p2_apply"
         raw = lambda l, c, xp, yp, sp: M.p2_apply_timed(l, c, xp, yp, sp, 0, 0, 0)
@@ -175,14 +185,20 @@ def setup(name, device, dtype_code, level=None):
         kernel = "k_interior2d" if coarse.dim == 2 else ("k_slab3d" if n <= 64 else "k_row3d")
         raw, timed = M.apply_raw, M.apply_timed
     return dict(M=M, L=L, ns=ns, ng=ng, xs=xs, ys=ys, smap=smap, x_global=x, coarse=coarse,
-                interior=interior, elem=4 if dtype_code == H.F32 else 8, code=dtype_code,
+                interior=interior, elem=4 if dtype_code == H.F32 else 8, code=dtype_code, launches=launches,
                 slab=slab or p2, kernel=kernel, apply_raw=raw, apply_timed=timed, op="p2" if p2 else "p1")
 
 
-def timed_applies(w, steps, warmup, stream, barrier=None):
+L2_BYTES = 129 * 2 ** 20
+
+
+def timed_applies(w, steps, warmup, stream, barrier=None, flush=None):
     """Warm-up, then exactly `steps` applies timed with CUDA events on the
     launching stream; per-kernel durations from events recorded by the
-    library between its two launches."""
+    library between its two launches.  With `flush` (a device buffer larger
+    than L2) the buffer is overwritten before every timed apply, so that no
+    apply finds its vectors in L2; the per-apply times then exclude the
+    flush."""
     import torch
     M, L, code = w["M"], w["L"], w["code"]
     xp, yp, sp = w["xs"].data_ptr(), w["ys"].data_ptr(), stream.cuda_stream
@@ -198,20 +214,28 @@ def timed_applies(w, steps, warmup, stream, barrier=None):
         barrier()
     torch.cuda.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # an NVTX range around the timed applies, so that a profiler can select
+    # them (the refinement's autotuner launches the same kernels before)
+    torch.cuda.nvtx.range_push("timed_applies")
     t0 = time.time()
     start.record(stream)
     for k in range(steps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(k)
         w["apply_timed"](L, code, xp, yp, sp, ev[k][0].cuda_event, ev[k][1].cuda_event, ev[k][2].cuda_event)
     end.record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
+    torch.cuda.nvtx.range_pop()
     if barrier:
         barrier()
     total_ms = start.elapsed_time(end)
     interior_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(steps)]
     iface_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(steps)]
+    apply_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(steps)]
     return dict(total_ms=total_ms, interior_ms=float(np.mean(interior_ms)), iface_ms=float(np.mean(iface_ms)),
-                t0=t0, t1=t1)
+                apply_ms=float(np.mean(apply_ms)), t0=t0, t1=t1)
 
 
 def graph_replay_us(w, reps, stream):
@@ -310,7 +334,8 @@ def ncu_traffic(kernel_key):
     src = os.path.join(ROOT, entry["source"])
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        h2 = hashlib.sha256(open(os.path.join(ROOT, "paper_2305_15116_gb300", "csrc", "arith.cuh"), "rb").read()).hexdigest()[:16]
+        arith = os.path.join(ROOT, "paper_2305_15116_gb300", "csrc", "arith.cuh")
+        h2 = hashlib.sha256(open(arith, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
     if entry.get("source_sha") != h or entry.get("arith_sha") != h2:
@@ -319,6 +344,29 @@ def ncu_traffic(kernel_key):
 
 
 # ---------------------------------------------------------------- solver
+def vcycle_bytes(M, L, elem, nu1=3, nu2=3):
+    """Algorithmic bytes of one V(nu1, nu2) cycle from level L (element size
+    elem, 2D fused sweeps): per level k >= 1 with S_k slots, the pre-sweeps
+    (nu1 on the finest level, nu1 - 1 below, where the restriction has done
+    the first one), the residual sweep and nu2 post-sweeps each read u and b
+    and write one vector (3 elem per slot); the restriction reads r (elem per
+    fine slot) and writes b, and below level 1 also u, of the coarser level
+    reading its inverse diagonal (3 elem per coarse slot, 1 for level 0); the
+    prolongation reads the coarse correction and updates u (elem per coarse
+    slot, 2 elem per fine slot); an odd number of sweeps copies u back
+    (2 elem per slot).  Level 0: the direct solve reads b and writes u."""
+    S = [M.num_slots(k)[0] for k in range(L + 1)]
+    total = 2 * elem * S[0]
+    for k in range(L, 0, -1):
+        pre = nu1 if k == L else nu1 - 1
+        total += 3 * elem * S[k] * (pre + 1 + nu2)
+        total += elem * S[k] + (3 if k - 1 > 0 else 1) * elem * S[k - 1]
+        total += elem * S[k - 1] + 2 * elem * S[k]
+        if (pre + nu2) % 2:
+            total += 2 * elem * S[k]
+    return total
+
+
 def solve_workload(device, stream, reps=3, rtol=1e-10):
     """Poisson solve -Lap u = f on the 32-macro jittered mesh at level 10,
     f = sin(pi x) sin(pi y) + 0.1 N(0,1) (noise per global DoF from seed 2),
@@ -365,10 +413,37 @@ def solve_workload(device, stream, reps=3, rtol=1e-10):
             rels.append(rel)
         out[label] = {"solves_per_s": 1.0 / float(np.median(times)), "ms_per_solve": 1e3 * float(np.median(times)),
                       "iterations": its[-1], "relres": rels[-1], "reached_rtol": bool(rels[-1] <= rtol)}
+    # one fp32 V(3,3) cycle on its own: device time and its algorithmic bytes
+    b32 = bd.float()
+    u32 = torch.zeros_like(b32)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            M.vcycle(L, b32, u32, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(20):
+            M.vcycle(L, b32, u32, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    vb = vcycle_bytes(M, L, 4)
+    peak, peak_kind = measured_peaks()
+    out["vcycle_fp32"] = {
+        "ms": ms, "algorithmic_bytes": vb, "achieved_GBps": vb / (ms * 1e-3) / 1e9,
+        "frac": vb / (ms * 1e-3) / 1e9 / peak, "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth",
+        "share_of_mixed_solve": ms * out["mixed_fp32_vcycles_two_part_refinement"]["iterations"]
+        / out["mixed_fp32_vcycles_two_part_refinement"]["ms_per_solve"],
+        "note": "one fp32 V(3,3) cycle from level 10 down to level 0 (hyteg_vcycle), 20 cycles timed with CUDA "
+                "events; algorithmic bytes: every sweep reads u and b and writes its result, the residual sweep "
+                "likewise, the restriction reads r and writes b and u of the coarser level, the prolongation "
+                "reads the coarse correction and updates u, an odd sweep count copies u back (4 B per slot "
+                "each)"}
     out["note"] = ("two_part: the iterate is u + u_lo, two float64 vectors (hyteg_solve_two_part), which reaches "
-                   "rtol; the float64-iterate loops stop at rtol or when two iterations no longer halve the "
-                   "residual: at level 10 the rounding of a float64 solution leaves a relative residual of about "
-                   "1.9e-10 (pinned by the oracle's exactly rounded residual at levels 4-6, 4x per level)")
+                   "rtol; the float64-iterate loops stop at rtol or when two iterations in a row each reduce "
+                   "the residual by less than 10 %: at level 10 the rounding of a float64 solution leaves a "
+                   "relative residual of about 1.9e-10 (pinned by the oracle's exactly rounded residual at "
+                   "levels 4-6, 4x per level)")
     M.close()
     return out
 
@@ -414,7 +489,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
     pending = collections.deque(reqs)
     retry = collections.deque()
     outstanding = {}
-    lat, run, queue_s, iters, rels, ngs, setup = [], [], [], [], [], [], []
+    lat, run, queue_s, iters, rels, ngs, setup, missed = [], [], [], [], [], [], [], []
     hits = failed = eagain = 0
     errors = collections.Counter()
     t0 = time.perf_counter()
@@ -458,6 +533,8 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
             queue_s.append(r.queue_s)
             iters.append(r.iters)
             rels.append(r.relres)
+            if r.relres > rtol:
+                missed.append((q.dim, list(q.shape), q.level, r.iters, r.relres))
             ngs.append(r.n_global)
             hits += int(r.cache_hit)
         if not progressed:
@@ -484,7 +561,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
         "relres_max": float(np.max(rels)) if rels else None,
         "reached_rtol": bool(rels and max(rels) <= rtol),
         "reached_rtol_share": float(np.mean(np.asarray(rels) <= rtol)) if rels else None,
-        "stopped_at_float64_floor": int(np.sum(np.asarray(rels) > rtol)) if rels else 0,
+        "not_reached_rtol": [dict(zip(("dim", "shape", "level", "iters", "relres"), m)) for m in missed[:8]],
     }
 
 
@@ -646,7 +723,7 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": w["launches"] * args.steps,
         "clocks": clocks,
         "impl": "ours",
     }
@@ -669,15 +746,26 @@ def main():
                 continue
             v = setup(name, device, vcode)
             steps = min(args.steps, 100)
-            rv = timed_applies(v, steps, args.warmup, stream)
+            # vectors that (nearly) fit in L2 are timed with an L2 flush
+            # before every apply; the value is then from the per-apply events
+            small = 2 * v["ns"] * v["elem"] < 4 * L2_BYTES
+            flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device) if small else None
+            rv = timed_applies(v, steps, args.warmup, stream, flush=flush)
+            del flush
             vb = interior_bytes(v)
+            vms = rv["apply_ms"] if small else rv["total_ms"] / steps
             variants.append({
                 "workload": name, "dtype": label, "kernel": v["kernel"],
-                "value": v["ng"] * steps / (rv["total_ms"] * 1e-3) / 1e9,
-                "unit": UNIT, "ms_per_step": rv["total_ms"] / steps,
+                "value": v["ng"] / (vms * 1e-3) / 1e9,
+                "unit": UNIT, "ms_per_step": vms,
+                "l2": ("flushed before every apply (x+y = %.0f MB)" if small else
+                       "inputs larger than L2 (x+y = %.0f MB), no flush") % (2 * v["ns"] * v["elem"] / 1e6),
                 "interior_GBps": vb / (rv["interior_ms"] * 1e-3) / 1e9,
                 "interior_frac": vb / (rv["interior_ms"] * 1e-3) / 1e9 / peak,
-                "interior_ms": rv["interior_ms"], "interface_ms": rv["iface_ms"]})
+                "interior_ms": rv["interior_ms"], "interface_ms": rv["iface_ms"],
+                "traffic": ncu_traffic("%s_%s_%s" % ("k_p2_rows" if v["op"] == "p2" else v["kernel"],
+                                                     {H.F64: "f64", H.F32: "f32", H.F64_IEEE: "f64_ieee"}[vcode],
+                                                     name))})
             if v["kernel"] == "k_slab3d":  # the work split the refinement's autotuner picked
                 variants[-1]["slab_z_ranges_per_macro"] = v["M"].autotune_choice(v["L"], vcode)
             if name == WORKLOAD and vcode == H.F64_IEEE:
@@ -692,6 +780,7 @@ def main():
                     "peak": FP64_PEAK_GOPS, "unit": "G fp64 ops/s", "frac": achieved / FP64_PEAK_GOPS,
                     "peak_kind": "nominal dense fp64 (1.25 TFLOP/s / 2 flops per FMA)",
                     "ops_per_launch": ops, "interior_ms": rv["interior_ms"],
+                    "traffic": variants[-1]["traffic"],
                     "GDoF_per_s": variants[-1]["value"],
                     "hbm_frac": variants[-1]["interior_frac"]}
             del v

@@ -280,12 +280,12 @@ int hyteg_vcycle(hyteg_mesh* mesh, int level, int dtype, const void* b, void* u,
  * residual corrections: the float64 residual is computed in difference form,
  * sum_k a_ik (u_k - u_i), whose terms stay small for smooth u, so it remains
  * accurate when A u nearly cancels b.  The loop also stops when two
- * consecutive iterations fail to halve the residual: the attainable relative
- * residual of a float64 u grows like h^-2 (about 1e-11 at level 8 and 2e-10
- * at level 10 for the unit-square Poisson problem), and *relres then reports
- * that floor.  Synchronises `stream` once per iteration to read the residual
- * norm.  *iters receives the iterations done, *relres the final relative
- * residual.
+ * consecutive iterations each reduce the residual by less than 10 %: the
+ * attainable relative residual of a float64 u grows like h^-2 (about 1e-11
+ * at level 8 and 2e-10 at level 10 for the unit-square Poisson problem), and
+ * *relres then reports that floor.  Synchronises `stream` once per
+ * iteration to read the residual norm.  *iters receives the iterations done,
+ * *relres the final relative residual.
  * Errors: HYTEG_EINVAL, HYTEG_ESTATE, HYTEG_ECUDA. */
 int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double rtol, int max_iter,
                 void* stream, int* iters, double* relres);

@@ -739,10 +739,12 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
       HY_TRY(residual(false, &rel));
     }
     if (rel <= rtol || it >= max_iter || !std::isfinite(rel)) break;  // a non-finite residual ends the loop
-    // A cycle reduces the residual by its convergence factor (about 0.4)
-    // until the float64 representation of u is reached; two iterations in a
-    // row that no longer halve it mean that floor has been reached.
-    stalled = (it > 0 && rel > 0.5 * prev) ? stalled + 1 : 0;
+    // A cycle reduces the residual by its convergence factor (about 0.4 on
+    // most meshes, up to about 0.8 on strongly distorted 3D ones) until the
+    // representation of u is reached: the float64 rounding of u, or far
+    // lower for the two-part iterate.  Two iterations in a row that each
+    // remove less than a tenth of it mean that floor has been reached.
+    stalled = (it > 0 && rel > 0.9 * prev) ? stalled + 1 : 0;
     if (stalled >= 2) {
       if (fast) {  // a stall seen on the float-float residual: decide on the accurate one
         fast = false;

@@ -123,3 +123,66 @@ def test_slab_autotune_choices_and_parity(cuda):
         yref = oracle.row_apply(rm, gids, x)
         absrow = np.array([_absrow(rm, g, x) for g in gids])
         check_close(yg[slots], yref, absrow, kind, f"autotuned 3D L6 {kind}")
+
+
+def _z_cuts(n, chunks):
+    """z-ranges of one macro-tet in the slab kernel's work list: a cut is
+    placed after the slice at which the running count of slice points first
+    reaches c/chunks of the macro's points, c = 1..chunks-1."""
+    S = (n + 1) * (n + 2) * (n + 3) // 6
+    cuts, acc = [0], 0
+    for z in range(n + 1):
+        m = n + 1 - z
+        acc += m * (m + 1) // 2
+        if len(cuts) < chunks and acc * chunks >= S * len(cuts) and z < n:
+            cuts.append(z + 1)
+    return cuts + [n + 1]
+
+
+def _tet_slot(n, x, y, z):
+    """Position of micro-vertex (x, y, z) in a macro's slot block: slices
+    z = 0..n, each a triangle of rows y, each row x = 0..n-z-y."""
+    N = n + 1
+    b = N - z
+    zs = N * (N + 1) * (N + 2) // 6 - b * (b + 1) * (b + 2) // 6
+    return zs + y * b - y * (y - 1) // 2 + x
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_full_size_every_z_range_edge(cuda, kind):
+    """The benchmark's launch (384 jittered macro-tets, level 6) with the
+    work split the refinement's autotuner chose for this element type: the
+    first and last slice of every z-range, at the start and end of its first
+    row and at its last row, in the first and last macro and six others."""
+    coarse, L, seed = workload("cube384jit_L6")
+    H = _lib()
+    M = H.Mesh(coarse.coords, coarse.cells).refine(L)
+    code = {"f64": H.F64, "f32": H.F32, "f64_ieee": H.F64_IEEE}[kind]
+    chunks = M.autotune_choice(L, code) or 2
+    n = 1 << L
+    cuts = _z_cuts(n, chunks)
+    assert len(cuts) == chunks + 1 and all(a < b for a, b in zip(cuts, cuts[1:]))
+    ns, ng = M.num_slots(L)
+    S = ns // coarse.n_cells
+    assert S == (n + 1) * (n + 2) * (n + 3) // 6
+    smap = M.dof_map(L)
+    x = random_vector(ng, seed)
+    if kind == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+    yg = gpu_apply(M, L, x[smap], kind)
+    assert np.all(np.isfinite(yg))
+    rng = np.random.default_rng(41)
+    cells = [0, coarse.n_cells - 1] + list(rng.choice(np.arange(1, coarse.n_cells - 1), 6, replace=False))
+    slots = []
+    for c in cells:
+        for z0, z1 in zip(cuts, cuts[1:]):
+            for z in sorted({z0, z1 - 1}):
+                w = n - z  # the slice's rows y = 0..w, row y has x = 0..w-y
+                pts = {(0, 0), (w, 0), (0, w)} if w < 2 else {(1, 1), (w - 2, 1), (1, w - 2), (0, 0), (w, 0)}
+                slots += [c * S + _tet_slot(n, px, py, z) for px, py in pts]
+    slots = np.unique(slots)
+    rm = oracle.RefinedMesh(coarse.coords, coarse.cells, L)
+    gids = smap[slots]
+    yref = oracle.row_apply(rm, gids, x)
+    absrow = np.array([_absrow(rm, g, x) for g in gids])
+    check_close(yg[slots], yref, absrow, kind, f"L6 3D z-range edges ({chunks} per macro) {kind}")
