@@ -305,6 +305,29 @@ int hyteg_solve(hyteg_mesh* mesh, int level, int mode, const double* b, double* 
 int hyteg_solve_two_part(hyteg_mesh* mesh, int level, int mode, const double* b, double* u, double* u_lo,
                          double rtol, int max_iter, void* stream, int* iters, double* relres);
 
+/* hyteg_solve_two_part for `count` problems at once (a group), each on its
+ * own mesh: meshes[i] (set up by hyteg_solver_setup to at least `level`),
+ * b[i], u[i], u_lo[i] its device vectors as in hyteg_solve_two_part.  The
+ * problems advance in lockstep: every step of the solve loop and of the
+ * V-cycle is one kernel launch for all problems still iterating (each with
+ * its own vectors, tables and block count), and one synchronisation per
+ * residual pass reads all their norms.  Each problem keeps its own stopping
+ * decisions, so iters[i] and relres[i] (arrays of `count`) and u[i], u_lo[i]
+ * are bitwise those of hyteg_solve_two_part on that problem alone.  The
+ * multigrid hierarchy of the paper (Sec. 1.2) with the kernels of Sec. 5.1
+ * shared by many problems.  The meshes must have one dimension and the same
+ * sweep counts, and each mesh may appear once (its workspace holds the
+ * problem's cycle vectors); 3D levels above 6 are solved one problem after
+ * another.  The problems' slot-layout vectors are owned by the caller.
+ * Synchronises `stream` once per residual pass.
+ * Errors: HYTEG_EINVAL (count < 1, NULL arrays or vectors, meshes of
+ * different dimensions or sweep counts, a repeated mesh, bad mode, rtol or
+ * max_iter), HYTEG_ESTATE (a mesh without solver set-up for the level),
+ * HYTEG_ECUDA. */
+int hyteg_solve_two_part_group(hyteg_mesh* const* meshes, int count, int level, int mode, const double* const* b,
+                               double* const* u, double* const* u_lo, double rtol, int max_iter, void* stream,
+                               int* iters, double* relres);
+
 /* ---- P2: vertex + edge DoFs (2D) -----------------------------------------
  * The discretisation of the paper's four kernels: quadratic elements on the
  * refined triangles, one DoF per refined vertex and one per micro-edge

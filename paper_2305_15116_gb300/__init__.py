@@ -7,9 +7,9 @@ L, and y = A x with constant per-macro stencils plus an interface step
 (Sec. 1.2, Sec. 5).  PyTorch provides device memory and streams only.
 """
 from .mesh import (Mesh, F64, F32, F64_IEEE, BC_NONE, BC_DIRICHLET, SOLVE_F64, SOLVE_MIXED, HytegError,
-                   version, apply_batch)
+                   version, apply_batch, solve_two_part_group)
 from .server import Server, Result
 from ._capi import REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED
 
 __all__ = ["Mesh", "F64", "F32", "F64_IEEE", "BC_NONE", "BC_DIRICHLET", "SOLVE_F64", "SOLVE_MIXED", "HytegError",
-           "version", "apply_batch", "Server", "Result", "REQ_QUEUED", "REQ_RUNNING", "REQ_DONE", "REQ_FAILED"]
+           "version", "apply_batch", "solve_two_part_group", "Server", "Result", "REQ_QUEUED", "REQ_RUNNING", "REQ_DONE", "REQ_FAILED"]

@@ -78,6 +78,12 @@ lib.hyteg_solve_two_part.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int
                                      ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
 lib.hyteg_solve_two_part.restype = ctypes.c_int
+lib.hyteg_solve_two_part_group.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double)]
+lib.hyteg_solve_two_part_group.restype = ctypes.c_int
 lib.hyteg_p2_num_slots.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p, c_i64p]
 lib.hyteg_p2_num_slots.restype = ctypes.c_int
 lib.hyteg_p2_dof_map.argtypes = [ctypes.c_void_p, ctypes.c_int, c_i64p]

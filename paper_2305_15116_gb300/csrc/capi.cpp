@@ -492,6 +492,42 @@ int hyteg_solve_two_part(hyteg_mesh* mesh, int level, int mode, const double* b,
   return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "solve");
 }
 
+int hyteg_solve_two_part_group(hyteg_mesh* const* meshes, int count, int level, int mode, const double* const* b,
+                               double* const* u, double* const* u_lo, double rtol, int max_iter, void* stream,
+                               int* iters, double* relres) {
+  if (count < 1) return fail(HYTEG_EINVAL, "count < 1");
+  if (!meshes || !b || !u || !u_lo || !iters || !relres) return fail(HYTEG_EINVAL, "NULL argument");
+  if (mode != HYTEG_SOLVE_F64 && mode != HYTEG_SOLVE_MIXED) return fail(HYTEG_EINVAL, "unknown mode");
+  if (!(rtol > 0.0) || max_iter < 0) return fail(HYTEG_EINVAL, "bad rtol or max_iter");
+  std::vector<hyteg::Mesh*> ms(count);
+  for (int i = 0; i < count; ++i) {
+    if (int r = check_solver(meshes[i], level, 0)) return r;
+    const std::string at = " (entry " + std::to_string(i) + ")";
+    if (!b[i] || !u[i] || !u_lo[i]) return fail(HYTEG_EINVAL, "NULL vector" + at);
+    if (u_lo[i] == u[i]) return fail(HYTEG_EINVAL, "u and u_lo must be different vectors" + at);
+    ms[i] = &meshes[i]->m;
+    if (ms[i]->dim != ms[0]->dim) return fail(HYTEG_EINVAL, "meshes of different dimensions" + at);
+    if (ms[i]->solver->nu1 != ms[0]->solver->nu1 || ms[i]->solver->nu2 != ms[0]->solver->nu2)
+      return fail(HYTEG_EINVAL, "meshes with different sweep counts" + at);
+    for (int j = 0; j < i; ++j)
+      if (ms[j] == ms[i]) return fail(HYTEG_EINVAL, "a mesh appears twice" + at);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // 3D levels above the slab kernel's (n > 64) have no group launch: the
+  // meshes are solved one after another
+  if (ms[0]->dim == 3 && ms[0]->levels[level].n_slabs == 0) {
+    for (int i = 0; i < count; ++i) {
+      const cudaError_t e = hyteg::mg_solve(*ms[i], level, mode, b[i], u[i], u_lo[i], rtol, max_iter, s, iters + i,
+                                            relres + i);
+      if (e != cudaSuccess) return cuda_fail(e, "solve");
+    }
+    return HYTEG_OK;
+  }
+  const cudaError_t e = hyteg::mg_solve_group(ms.data(), count, level, mode, b, u, u_lo, rtol, max_iter, s, iters,
+                                              relres);
+  return e == cudaSuccess ? HYTEG_OK : cuda_fail(e, "group solve");
+}
+
 int hyteg_p2_num_slots(const hyteg_mesh* mesh, int level, int64_t* n_slots, int64_t* n_global) {
   if (int r = check_host_level(mesh, level)) return r;
   if (mesh->m.dim != 2) return fail(HYTEG_EINVAL, "the P2 operator is built for 2D meshes");

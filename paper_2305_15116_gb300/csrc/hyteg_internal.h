@@ -304,6 +304,12 @@ cudaError_t mg_prolong_add(const Mesh& m, int fine_level, int dtype, const void*
 cudaError_t mg_vcycle(Mesh& m, int level, int dtype, const void* b, void* u, cudaStream_t s);
 cudaError_t mg_solve(Mesh& m, int level, int mode, const double* b, double* u, double* ulo, double rtol,
                      int max_iter, cudaStream_t s, int* iters, double* relres);
+// mg_solve for a group of meshes (same dimension and sweep counts, distinct
+// workspaces) in lockstep: each iterates on its own residuals, the ones still
+// iterating share every launch.  ulo: null, or one low part per mesh.
+cudaError_t mg_solve_group(Mesh* const* ms, int count, int level, int mode, const double* const* b,
+                           double* const* u, double* const* ulo, double rtol, int max_iter, cudaStream_t s,
+                           int* iters, double* relres);
 
 // ---- kernels ----------------------------------------------------------------
 // dtype: 1 = f64 (float-float arithmetic), 2 = f32, 3 = f64 native.
@@ -316,6 +322,14 @@ cudaError_t launch_apply2d_batch(int dtype, const Mesh* const* meshes, const int
 // apply) or 2 (fp32).
 cudaError_t launch_sweep2d(int dtype, bool jacobi, const Mesh& m, const LevelDev& L, const void* u, const void* b,
                            const void* dinv, double omega, void* out, cudaStream_t s);
+// the fp32 fused sweeps of several 2D meshes in one launch (per mesh its
+// level, vectors, inverse diagonal and omega)
+cudaError_t launch_sweep2d_group(bool jacobi, const Mesh* const* ms, const int* levels, const void* const* u,
+                                 const void* const* b, const void* const* dinv, const double* omega,
+                                 void* const* out, int count, cudaStream_t s);
+// the slab kernel of several 3D meshes (levels with n <= 64) in one launch
+cudaError_t launch_slab3d_group(int dtype, const Mesh* const* ms, const int* levels, const void* const* xs,
+                                void* const* ys, int count, cudaStream_t s);
 cudaError_t launch_slab3d(int dtype, const LevelDev& L, const void* x, void* y, cudaStream_t s);
 // raises the slab kernels' shared-memory limit (once per process; before any
 // stream capture)
@@ -325,8 +339,10 @@ cudaError_t launch_slab3d_items(int dtype, const LevelDev& L, const int4* items,
                                 void* y, cudaStream_t s);
 cudaError_t launch_row3d(int dtype, const LevelDev& L, int64_t n_cells, const void* x, void* y, cudaStream_t s);
 cudaError_t build_iface_slots(const Mesh& m, const LevelDev& L, cudaStream_t s);
-cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x,
-                                    void* y, cudaStream_t s);
+cudaError_t launch_interface_reduce(int dtype, const Mesh& m, int level, const void* x, void* y, cudaStream_t s);
+// the interface reduction of several meshes of one dimension
+cudaError_t launch_interface_reduce_group(int dtype, const Mesh* const* ms, const int* levels, const void* const* x,
+                                          void* const* y, int count, cudaStream_t s);
 
 // The launch sequence of one apply y = A x (two kernels); `ev_mid`, when not
 // null, is recorded between them.  Returns the failing step in *what.

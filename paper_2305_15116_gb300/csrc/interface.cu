@@ -14,8 +14,10 @@
 // Work list: one block per item (primitive, row b, points a0..a1-1) of at most
 // 128 points; a vertex item has one point.
 #include <algorithm>
+#include <vector>
 
 #include "arith.cuh"
+#include "group.cuh"
 #include "hyteg_internal.h"
 
 namespace hyteg {
@@ -83,111 +85,161 @@ __global__ void __launch_bounds__(128) k_build_iface_slots(int64_t* __restrict__
 // thread per point: two copies are summed (lower macro first) and the sum
 // written to both, or a Dirichlet point of one copy gets y = x.  Pair blocks
 // run in table order, so that the points in flight at any time lie close
-// together in the vectors.  The two sets of points are disjoint.
+// together in the vectors.  The two sets of points are disjoint.  A body of
+// group.cuh: one launch serves one mesh or a group.
 template <class T>
-__global__ void __launch_bounds__(256) k_interface_reduce_flat(const T* __restrict__ x, T* __restrict__ y,
-                                                               const longlong2* __restrict__ pairs, int64_t n_pairs,
-                                                               const int4* __restrict__ items,
-                                                               const Prim* __restrict__ prims,
-                                                               const int64_t* __restrict__ item_base,
-                                                               const int64_t* __restrict__ slots,
-                                                               const int* __restrict__ list, int n_rest,
-                                                               int rest_blocks) {
-  if ((int)blockIdx.x < rest_blocks) {
-    const int k = 2 * (int)blockIdx.x + (int)(threadIdx.x >> 7);
-    if (k >= n_rest) return;
-    const int item = list[k];
-    const int4 it = items[item];
-    const int a = it.z + (int)(threadIdx.x & 127);
-    if (a >= it.w) return;
-    const Prim p = prims[it.x];
-    if (!p.boundary && p.inc_count == 1) return;
-    const int64_t* sl = slots + item_base[item] + (int64_t)(a - it.z) * p.inc_count;
-    T acc = T(0);
-    if (p.boundary) {
-      acc = __ldg(x + __ldg(sl));
-    } else {
-      for (int i = 0; i < p.inc_count; ++i) acc += y[__ldg(sl + i)];
-    }
-    for (int i = 0; i < p.inc_count; ++i) y[__ldg(sl + i)] = acc;
-    return;
-  }
-  const int64_t i = (int64_t)(blockIdx.x - rest_blocks) * blockDim.x + threadIdx.x;
-  if (i >= n_pairs) return;
-  const longlong2 pr = pairs[i];
-  if (pr.y == -2) {
-    y[pr.x] = __ldg(x + pr.x);
-  } else {
-    const T v = y[pr.x] + y[pr.y];
-    y[pr.x] = v;
-    y[pr.y] = v;
-  }
-}
-
-// Reduce variant: the copies already hold their macro's partial row (written
-// by the 3D slab kernel); sum them in ascending macro order and write the sum
-// into every copy.  A point with a single copy is already complete.
-template <class T, int DIM>
-__global__ void __launch_bounds__(128) k_interface_reduce(const T* __restrict__ x, T* __restrict__ y,
-                                                          const int4* __restrict__ items,
-                                                          const Prim* __restrict__ prims,
-                                                          const Inc* __restrict__ incs, int n, int64_t S) {
-  const int4 it = items[blockIdx.x];
-  const int a = it.z + threadIdx.x;
-  if (a >= it.w) return;
-  const Prim p = prims[it.x];
-  if (!p.boundary && p.inc_count == 1) return;
-  const int b = it.y;
-  int wv[3] = {0, 0, 0};
-  if (p.type == 0) {
-    wv[0] = n;
-  } else if (p.type == 1) {
-    wv[0] = n - a;
-    wv[1] = a;
-  } else {
-    wv[0] = n - a - b;
-    wv[1] = a;
-    wv[2] = b;
-  }
-  const int nverts = p.type + 1;
-  // slot of this point in the i-th incident cell
-  auto slot_of = [&](int i) -> int64_t {
-    const Inc inc = incs[p.inc_begin + i];
-    int q[3] = {0, 0, 0};
-    for (int j = 0; j < nverts; ++j) {
-      const int c = inc.corner[j];
-      if (c >= 1) q[c - 1] += wv[j];
-    }
-    return (int64_t)inc.cell * S + (DIM == 2 ? tri_slot(n, q[0], q[1]) : tet_slot(n, q[0], q[1], q[2]));
+struct ReduceFlat {
+  static constexpr int kThreads = 256;
+  struct Prm {
+    const T* x;
+    T* y;
+    const longlong2* pairs;
+    int64_t n_pairs;
+    const int4* items;
+    const Prim* prims;
+    const int64_t *item_base, *slots;
+    const int* list;
+    int n_rest, rest_blocks;
   };
-  T acc = T(0);
-  if (p.boundary) {
-    acc = __ldg(x + slot_of(0));
-  } else {
-    for (int i = 0; i < p.inc_count; ++i) acc += y[slot_of(i)];
+  static __device__ __forceinline__ void run(const Prm& p, int block, int) {
+    if (block < p.rest_blocks) {
+      const int k = 2 * block + (int)(threadIdx.x >> 7);
+      if (k >= p.n_rest) return;
+      const int item = p.list[k];
+      const int4 it = p.items[item];
+      const int a = it.z + (int)(threadIdx.x & 127);
+      if (a >= it.w) return;
+      const Prim pr = p.prims[it.x];
+      if (!pr.boundary && pr.inc_count == 1) return;
+      const int64_t* sl = p.slots + p.item_base[item] + (int64_t)(a - it.z) * pr.inc_count;
+      T acc = T(0);
+      if (pr.boundary) {
+        acc = __ldg(p.x + __ldg(sl));
+      } else {
+        for (int i = 0; i < pr.inc_count; ++i) acc += p.y[__ldg(sl + i)];
+      }
+      for (int i = 0; i < pr.inc_count; ++i) p.y[__ldg(sl + i)] = acc;
+      return;
+    }
+    const int64_t i = (int64_t)(block - p.rest_blocks) * 256 + threadIdx.x;
+    if (i >= p.n_pairs) return;
+    const longlong2 pr = p.pairs[i];
+    if (pr.y == -2) {
+      p.y[pr.x] = __ldg(p.x + pr.x);
+    } else {
+      const T v = p.y[pr.x] + p.y[pr.y];
+      p.y[pr.x] = v;
+      p.y[pr.y] = v;
+    }
   }
-  for (int i = 0; i < p.inc_count; ++i) y[slot_of(i)] = acc;
+};
+
+// Reduce variant without the tables (2D levels): the copies already hold
+// their macro's partial row; sum them in ascending macro order and write the
+// sum into every copy.  A point with a single copy is already complete.
+template <class T, int DIM>
+struct ReduceItems {
+  static constexpr int kThreads = 128;
+  struct Prm {
+    const T* x;
+    T* y;
+    const int4* items;
+    const Prim* prims;
+    const Inc* incs;
+    int n;
+    int64_t S;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int) {
+    const int4 it = p.items[block];
+    const int a = it.z + threadIdx.x;
+    if (a >= it.w) return;
+    const Prim pr = p.prims[it.x];
+    if (!pr.boundary && pr.inc_count == 1) return;
+    const int n = p.n;
+    const int b = it.y;
+    int wv[3] = {0, 0, 0};
+    if (pr.type == 0) {
+      wv[0] = n;
+    } else if (pr.type == 1) {
+      wv[0] = n - a;
+      wv[1] = a;
+    } else {
+      wv[0] = n - a - b;
+      wv[1] = a;
+      wv[2] = b;
+    }
+    const int nverts = pr.type + 1;
+    // slot of this point in the i-th incident cell
+    auto slot_of = [&](int i) -> int64_t {
+      const Inc inc = p.incs[pr.inc_begin + i];
+      int q[3] = {0, 0, 0};
+      for (int j = 0; j < nverts; ++j) {
+        const int c = inc.corner[j];
+        if (c >= 1) q[c - 1] += wv[j];
+      }
+      return (int64_t)inc.cell * p.S + (DIM == 2 ? tri_slot(n, q[0], q[1]) : tet_slot(n, q[0], q[1], q[2]));
+    };
+    T acc = T(0);
+    if (pr.boundary) {
+      acc = __ldg(p.x + slot_of(0));
+    } else {
+      for (int i = 0; i < pr.inc_count; ++i) acc += p.y[slot_of(i)];
+    }
+    for (int i = 0; i < pr.inc_count; ++i) p.y[slot_of(i)] = acc;
+  }
+};
+
+template <class T, int DIM>
+cudaError_t reduce_items(const Mesh* const* ms, const int* levels, const void* const* x, void* const* y, int cnt,
+                         cudaStream_t s) {
+  std::vector<typename ReduceItems<T, DIM>::Prm> p;
+  std::vector<int> blocks;
+  for (int i = 0; i < cnt; ++i) {
+    const LevelDev& L = ms[i]->levels[levels[i]];
+    p.push_back({(const T*)x[i], (T*)y[i], L.items, ms[i]->d_prims, ms[i]->d_incs, L.n, L.slots_per_macro});
+    blocks.push_back(L.n_items);
+  }
+  return launch_group<ReduceItems<T, DIM>>(p.data(), blocks.data(), cnt, s);
 }
 
+// The interface reduction of every mesh of a group (the same dimension), one
+// launch per kind of table: the flat tables where the level has them (3D),
+// else the item list.
 template <class T>
-cudaError_t launch_reduce_t(int dim, const Mesh& m, const LevelDev& L, const void* x, void* y, cudaStream_t s) {
-  if (L.n_items == 0) return cudaSuccess;
-  if (L.if_slots) {
-    const int rest_blocks = (L.n_if_rest + 1) / 2;
-    const int64_t blocks = rest_blocks + (L.n_if_pairs + 255) / 256;
-    if (blocks > 0)
-      k_interface_reduce_flat<T><<<(unsigned)blocks, 256, 0, s>>>((const T*)x, (T*)y, L.if_pairs, L.n_if_pairs,
-                                                                  L.items, m.d_prims, L.if_item_base, L.if_slots,
-                                                                  L.if_rest, L.n_if_rest, rest_blocks);
-    return cudaGetLastError();
+cudaError_t launch_reduce_group_t(const Mesh* const* ms, const int* levels, const void* const* x, void* const* y,
+                                  int cnt, cudaStream_t s) {
+  std::vector<typename ReduceFlat<T>::Prm> pf;
+  std::vector<int> bf;
+  std::vector<const Mesh*> mi;
+  std::vector<int> li;
+  std::vector<const void*> xi;
+  std::vector<void*> yi;
+  for (int i = 0; i < cnt; ++i) {
+    const Mesh& m = *ms[i];
+    const LevelDev& L = m.levels[levels[i]];
+    if (L.n_items == 0) continue;
+    if (L.if_slots) {
+      const int rest_blocks = (L.n_if_rest + 1) / 2;
+      const int64_t blocks = rest_blocks + (L.n_if_pairs + 255) / 256;
+      if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
+      pf.push_back({(const T*)x[i], (T*)y[i], L.if_pairs, L.n_if_pairs, L.items, m.d_prims, L.if_item_base,
+                    L.if_slots, L.if_rest, L.n_if_rest, rest_blocks});
+      bf.push_back(int(blocks));
+    } else {
+      mi.push_back(ms[i]);
+      li.push_back(levels[i]);
+      xi.push_back(x[i]);
+      yi.push_back(y[i]);
+    }
   }
-  if (dim == 2)
-    k_interface_reduce<T, 2><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, m.d_incs, L.n,
-                                                        L.slots_per_macro);
-  else
-    k_interface_reduce<T, 3><<<L.n_items, 128, 0, s>>>((const T*)x, (T*)y, L.items, m.d_prims, m.d_incs, L.n,
-                                                        L.slots_per_macro);
-  return cudaGetLastError();
+  if (!pf.empty()) {
+    const cudaError_t e = launch_group<ReduceFlat<T>>(pf.data(), bf.data(), int(pf.size()), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (mi.empty()) return cudaSuccess;
+  const int k = int(mi.size());
+  return ms[0]->dim == 2 ? reduce_items<T, 2>(mi.data(), li.data(), xi.data(), yi.data(), k, s)
+                         : reduce_items<T, 3>(mi.data(), li.data(), xi.data(), yi.data(), k, s);
 }
 
 }  // namespace
@@ -203,14 +255,20 @@ cudaError_t build_iface_slots(const Mesh& m, const LevelDev& L, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-cudaError_t launch_interface_reduce(int dtype, int dim, const Mesh& m, const LevelDev& L, const void* x, void* y,
-                                    cudaStream_t s) {
+cudaError_t launch_interface_reduce_group(int dtype, const Mesh* const* ms, const int* levels, const void* const* x,
+                                          void* const* y, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
   switch (dtype) {
     case 1:
-    case 3: return launch_reduce_t<double>(dim, m, L, x, y, s);
-    case 2: return launch_reduce_t<float>(dim, m, L, x, y, s);
+    case 3: return launch_reduce_group_t<double>(ms, levels, x, y, count, s);
+    case 2: return launch_reduce_group_t<float>(ms, levels, x, y, count, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_interface_reduce(int dtype, const Mesh& m, int level, const void* x, void* y, cudaStream_t s) {
+  const Mesh* mp = &m;
+  return launch_interface_reduce_group(dtype, &mp, &level, &x, &y, 1, s);
 }
 
 cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,
@@ -241,7 +299,7 @@ cudaError_t launch_apply(const Mesh& m, int level, int dtype, const void* x, voi
     if (e != cudaSuccess) return e;
   }
   *what = "interface reduce kernel";
-  return launch_interface_reduce(dtype, m.dim, m, L, x, y, s);
+  return launch_interface_reduce(dtype, m, level, x, y, s);
 }
 
 cudaError_t launch_apply_partial(const Mesh& m, int level, int dtype, const void* x, void* y, cudaStream_t s,

@@ -20,6 +20,8 @@
 // pair come from the adjacent lanes by warp shuffles, so every value is read
 // from memory once per tile plus two halo rows.  62 of the 64 columns are
 // written; the outermost two only supply the horizontal halo.
+#include <vector>
+
 #include "arith.cuh"
 #include "fallback.cuh"
 #include "hyteg_internal.h"
@@ -380,21 +382,25 @@ struct Apply2dDesc {
   const Prim* prims;
   const Inc* incs;
   StencilPtr st;
+  ModeArgs md;  // the sweep modes' b, inverse diagonal and omega
   int64_t n_warps;
   int64_t S;
   int n_tiles, n, n_items, n_if_blocks;
   int block_begin;  // first block of this mesh in the launch
 };
-constexpr int BATCH2D = 64;  // meshes per launch (the parameter block stays below 8 KB)
+constexpr int BATCH2D = 64;  // meshes per launch (the parameter block stays below 10 KB)
 struct Apply2dBatch {
   Apply2dDesc d[BATCH2D];
   int count;
 };
 
-template <class P>
-__global__ void __launch_bounds__(THREADS2D) k_interior2d_batch(const __grid_constant__ Apply2dBatch b) {
+template <class P, int MODE>
+__global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d_batch(const __grid_constant__ Apply2dBatch b) {
   using T = typename P::T;
-  __shared__ T ring_all[THREADS2D / 32][RING][32][2];
+  constexpr int THR = Thr2<MODE>::value;
+  constexpr bool SWEEP = MODE == MODE_JACOBI || MODE == MODE_RESIDUAL;
+  __shared__ T ring_all[THR / 32][RING][32][2];
+  __shared__ T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
   int lo = 0, hi = b.count - 1;  // the last mesh whose range starts at or before this block
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -404,10 +410,9 @@ __global__ void __launch_bounds__(THREADS2D) k_interior2d_batch(const __grid_con
       hi = mid - 1;
   }
   const Apply2dDesc& d = b.d[lo];
-  const ModeArgs md{nullptr, nullptr, 0.0};
-  apply2d_block<P, MODE_APPLY>((int)blockIdx.x - d.block_begin, static_cast<const T*>(d.x), static_cast<T*>(d.y),
-                               d.tiles, d.n_tiles > 0 ? d.n_tiles : 1, d.n_warps, d.S, d.n, d.st, d.items,
-                               d.n_items, d.prims, d.incs, d.n_if_blocks, md, ring_all, ring_all);
+  apply2d_block<P, MODE>((int)blockIdx.x - d.block_begin, static_cast<const T*>(d.x), static_cast<T*>(d.y), d.tiles,
+                         d.n_tiles > 0 ? d.n_tiles : 1, d.n_warps, d.S, d.n, d.st, d.items, d.n_items, d.prims,
+                         d.incs, d.n_if_blocks, d.md, ring_all, ringb_all);
 }
 
 // Element-type index of a policy (1 float-float, 2 fp32, 3 native fp64).
@@ -455,9 +460,10 @@ cudaError_t launch(const Mesh& m, const LevelDev& L, const void* x, void* y, cud
   return launch_on<P, MODE>(m, L, tiles, n_tiles, x, y, s, md);
 }
 
-template <class P>
+template <class P, int MODE = MODE_APPLY>
 cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const void* const* xs, void* const* ys,
-                           int count, cudaStream_t s) {
+                           int count, cudaStream_t s, const ModeArgs* mds = nullptr) {
+  constexpr int THR = Thr2<MODE>::value;
   Apply2dBatch b;
   for (int i0 = 0; i0 < count; i0 += BATCH2D) {
     b.count = 0;
@@ -469,8 +475,8 @@ cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const v
       int n_tiles = 0;
       tiles_of<P>(L, &tiles, &n_tiles);
       const int64_t n_warps = (int64_t)n_tiles * m.n_cells;
-      const int64_t int_blocks = (n_warps * 32 + THREADS2D - 1) / THREADS2D;
-      const int if_blocks = (L.n_items + THREADS2D / 128 - 1) / (THREADS2D / 128);
+      const int64_t int_blocks = (n_warps * 32 + THR - 1) / THR;
+      const int if_blocks = (L.n_items + THR / 128 - 1) / (THR / 128);
       if (int_blocks + if_blocks == 0) continue;
       if ((int64_t)blocks + int_blocks + if_blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
       Apply2dDesc& d = b.d[b.count++];
@@ -481,6 +487,7 @@ cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const v
       d.prims = m.d_prims;
       d.incs = m.d_incs;
       d.st = StencilPtr{L.st64, L.st32, L.st_hi, L.st_lo};
+      d.md = mds ? mds[i] : ModeArgs{nullptr, nullptr, 0.0};
       d.n_warps = n_warps;
       d.S = L.slots_per_macro;
       d.n_tiles = n_tiles;
@@ -491,7 +498,7 @@ cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const v
       blocks += int(int_blocks + if_blocks);
     }
     if (b.count == 0) continue;
-    k_interior2d_batch<P><<<blocks, THREADS2D, 0, s>>>(b);
+    k_interior2d_batch<P, MODE><<<blocks, THR, 0, s>>>(b);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -540,6 +547,16 @@ cudaError_t launch_sweep2d(int dtype, bool jacobi, const Mesh& m, const LevelDev
       return jacobi ? launch<ArF32, MODE_JACOBI>(m, L, u, out, s, md) : launch<ArF32, MODE_RESIDUAL>(m, L, u, out, s, md);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_sweep2d_group(bool jacobi, const Mesh* const* ms, const int* levels, const void* const* u,
+                                 const void* const* b, const void* const* dinv, const double* omega,
+                                 void* const* out, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  std::vector<ModeArgs> md(count);
+  for (int i = 0; i < count; ++i) md[i] = ModeArgs{b[i], dinv[i], omega[i]};
+  return jacobi ? launch_batch_t<ArF32, MODE_JACOBI>(ms, levels, u, out, count, s, md.data())
+                : launch_batch_t<ArF32, MODE_RESIDUAL>(ms, levels, u, out, count, s, md.data());
 }
 
 cudaError_t launch_apply2d_batch(int dtype, const Mesh* const* meshes, const int* levels, const void* const* xs,

@@ -14,10 +14,12 @@
 // the coarse micro-edges), dividing every fine value by the number of macros
 // that hold a copy of it; the interface step then sums the partials of the
 // copies of every coarse interface point and zeroes the Dirichlet rows.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "arith.cuh"
+#include "group.cuh"
 #include "hyteg_internal.h"
 
 namespace hyteg {
@@ -71,20 +73,65 @@ __constant__ int c_off3[NW3][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0}
 __constant__ int c_dir2[3][2] = {{1, 0}, {0, 1}, {1, -1}};
 __constant__ int c_dir3[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, -1, 0}, {1, 0, -1}, {0, 1, -1}, {1, -1, 1}};
 
-// ---- elementwise kernels ------------------------------------------------------
+// ---- kernel bodies ----------------------------------------------------------------
+// Every kernel the solve loop and the V-cycle launch is a body run by
+// k_group (group.cuh): the work of block `block` of the `nb` blocks of one
+// mesh's part of a launch, so that one launch serves one mesh or a group of
+// meshes with the same arithmetic.  Grid-stride loops stride over the mesh's
+// own blocks.
 
-template <class T>
-__global__ void k_jacobi(T* __restrict__ u, const T* __restrict__ b, const T* __restrict__ y,
-                         const T* __restrict__ dinv, T omega, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    u[i] = u[i] + omega * dinv[i] * (b[i] - y[i]);
-}
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)block * THREADS + threadIdx.x; i < (n); i += (int64_t)nb * THREADS)
 
+// u = u + omega dinv (b - y)
 template <class T>
-__global__ void k_residual(T* __restrict__ r, const T* __restrict__ b, const T* __restrict__ y, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    r[i] = b[i] - y[i];
-}
+struct Jacobi {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    T* u;
+    const T *b, *y, *dinv;
+    T omega;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    GRID_STRIDE(i, p.n) p.u[i] = p.u[i] + p.omega * p.dinv[i] * (p.b[i] - p.y[i]);
+  }
+};
+
+// r = b - y
+template <class T>
+struct Residual {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    T* r;
+    const T *b, *y;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    GRID_STRIDE(i, p.n) p.r[i] = p.b[i] - p.y[i];
+  }
+};
+
+// dst = src; p = 0
+template <class T>
+struct Copy {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    T* dst;
+    const T* src;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) { GRID_STRIDE(i, p.n) p.dst[i] = p.src[i]; }
+};
+template <class T>
+struct Zero {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    T* p;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) { GRID_STRIDE(i, p.n) p.p[i] = T(0); }
+};
 
 __global__ void k_add_f64(double* __restrict__ u, const double* __restrict__ e, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -99,29 +146,43 @@ __global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ e, i
 // (u, ulo) <- (fl(u + ulo), the rest): u becomes the float64 rounding of the
 // two-part value (Fast2Sum, exact while |ulo| <= |u|, which the corrections
 // keep: ulo collects rounding errors of u).
-__global__ void k_normalize_two_part(double* __restrict__ u, double* __restrict__ ulo, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double a = u[i], b = ulo[i];
-    const double sum = __dadd_rn(a, b);
-    u[i] = sum;
-    ulo[i] = __dsub_rn(b, __dsub_rn(sum, a));
+struct Normalize {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    double *u, *ulo;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    GRID_STRIDE(i, p.n) {
+      const double a = p.u[i], b = p.ulo[i];
+      const double sum = __dadd_rn(a, b);
+      p.u[i] = sum;
+      p.ulo[i] = __dsub_rn(b, __dsub_rn(sum, a));
+    }
   }
-}
+};
 
 // (u + ulo) += e for an iterate of two float64 parts: u takes the rounded
 // sum, and its rounding error (Knuth's TwoSum, exact) goes into ulo.
 template <class T>
-__global__ void k_add_two_part(double* __restrict__ u, double* __restrict__ ulo, const T* __restrict__ e,
-                               int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double a = u[i], d = (double)e[i];
-    const double sum = __dadd_rn(a, d);
-    const double bv = __dsub_rn(sum, a);
-    const double err = __dadd_rn(__dsub_rn(a, __dsub_rn(sum, bv)), __dsub_rn(d, bv));
-    u[i] = sum;
-    ulo[i] = __dadd_rn(ulo[i], err);
+struct AddTwoPart {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    double *u, *ulo;
+    const T* e;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    GRID_STRIDE(i, p.n) {
+      const double a = p.u[i], d = (double)p.e[i];
+      const double sum = __dadd_rn(a, d);
+      const double bv = __dsub_rn(sum, a);
+      const double err = __dadd_rn(__dsub_rn(a, __dsub_rn(sum, bv)), __dsub_rn(d, bv));
+      p.u[i] = sum;
+      p.ulo[i] = __dadd_rn(p.ulo[i], err);
+    }
   }
-}
+};
 
 // ---- accurate residual ------------------------------------------------------
 // Macro-local part of (A u) at every slot in difference form,
@@ -135,46 +196,57 @@ __global__ void k_add_two_part(double* __restrict__ u, double* __restrict__ ulo,
 // With `ulo` (an iterate u + ulo of two float64 parts) the differences of the
 // low parts join those of the high parts: sum w_k ((u_k - u_c) + (lo_k - lo_c)).
 template <int DIM>
-__global__ void k_partial_diff(const double* __restrict__ u, const double* __restrict__ ulo, double* __restrict__ y,
-                               const unsigned* __restrict__ lpts, const double* __restrict__ st, int n, int64_t S,
-                               int64_t total) {
-  constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
-  constexpr int NW = DIM == 2 ? NW2 : NW3;
-  constexpr int CEN = DIM == 2 ? C2 : C3;
-  const SlotDiv divS(S, total);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = divS(i);
-    int q[3];
-    unpack<DIM>(lpts[i - cell * S], q);
-    const int cls = pclass<DIM>(n, q);
-    const double* __restrict__ w = st + (cell * NCLS + cls) * NW;
-    const double* __restrict__ um = u + cell * S;
-    const double* __restrict__ lm = ulo ? ulo + cell * S : nullptr;
-    const double uc = um[i - cell * S];
-    const double lc = lm ? lm[i - cell * S] : 0.0;
-    double acc = 0.0;
+struct PartialDiff {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    const double *u, *ulo;
+    double* y;
+    const unsigned* lpts;
+    const double* st;
+    int n;
+    int64_t S, total;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    constexpr int NCLS = DIM == 2 ? NCLS2 : NCLS3;
+    constexpr int NW = DIM == 2 ? NW2 : NW3;
+    constexpr int CEN = DIM == 2 ? C2 : C3;
+    const int n = p.n;
+    const int64_t S = p.S;
+    const SlotDiv divS(S, p.total);
+    GRID_STRIDE(i, p.total) {
+      const int64_t cell = divS(i);
+      int q[3];
+      unpack<DIM>(p.lpts[i - cell * S], q);
+      const int cls = pclass<DIM>(n, q);
+      const double* __restrict__ w = p.st + (cell * NCLS + cls) * NW;
+      const double* __restrict__ um = p.u + cell * S;
+      const double* __restrict__ lm = p.ulo ? p.ulo + cell * S : nullptr;
+      const double uc = um[i - cell * S];
+      const double lc = lm ? lm[i - cell * S] : 0.0;
+      double acc = 0.0;
 #pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      if (k == CEN) continue;
-      int j[3];
-      if (DIM == 2) {
-        j[0] = q[0] + c_off2[k][0];
-        j[1] = q[1] + c_off2[k][1];
-        j[2] = 0;
-      } else {
-        j[0] = q[0] + c_off3[k][0];
-        j[1] = q[1] + c_off3[k][1];
-        j[2] = q[2] + c_off3[k][2];
+      for (int k = 0; k < NW; ++k) {
+        if (k == CEN) continue;
+        int j[3];
+        if (DIM == 2) {
+          j[0] = q[0] + c_off2[k][0];
+          j[1] = q[1] + c_off2[k][1];
+          j[2] = 0;
+        } else {
+          j[0] = q[0] + c_off3[k][0];
+          j[1] = q[1] + c_off3[k][1];
+          j[2] = q[2] + c_off3[k][2];
+        }
+        if (!inside<DIM>(n, j)) continue;
+        const int64_t sj = slotq<DIM>(n, j);
+        double d = __dsub_rn(um[sj], uc);
+        if (lm) d = __dadd_rn(d, __dsub_rn(lm[sj], lc));
+        acc = __fma_rn(__ldg(w + k), d, acc);
       }
-      if (!inside<DIM>(n, j)) continue;
-      const int64_t sj = slotq<DIM>(n, j);
-      double d = __dsub_rn(um[sj], uc);
-      if (lm) d = __dadd_rn(d, __dsub_rn(lm[sj], lc));
-      acc = __fma_rn(__ldg(w + k), d, acc);
+      p.y[i] = acc;
     }
-    y[i] = acc;
   }
-}
+};
 
 // ---- transfers --------------------------------------------------------------
 
@@ -219,66 +291,78 @@ __device__ __forceinline__ T restrict_partial(const T* __restrict__ rf, const T*
 // also performs the coarse level's first weighted-Jacobi sweep from u_c = 0,
 // u_c = omega D^-1 b_c, at every slot.
 template <class T, int DIM>
-__global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ bc,
-                                                        T* __restrict__ uc, const T* __restrict__ dinv, T omega,
-                                                        const unsigned* __restrict__ lpts_c,
-                                                        const T* __restrict__ multinv, const int4* __restrict__ items,
-                                                        const Prim* __restrict__ prims, const Inc* __restrict__ incs,
-                                                        int nc, int64_t Sc, int64_t Sf, int64_t total,
-                                                        int n_if_blocks) {
-  if ((int)blockIdx.x < n_if_blocks) {
-    const int4 it = items[blockIdx.x];
-    const int a = it.z + threadIdx.x;
-    if (a >= it.w) return;
-    const Prim p = prims[it.x];
-    const int b = it.y;
-    int wv[3] = {0, 0, 0};
-    if (p.type == 0) {
-      wv[0] = nc;
-    } else if (p.type == 1) {
-      wv[0] = nc - a;
-      wv[1] = a;
-    } else {
-      wv[0] = nc - a - b;
-      wv[1] = a;
-      wv[2] = b;
-    }
-    auto local = [&](const Inc& inc, int q[3]) {
-      q[0] = q[1] = q[2] = 0;
-      for (int j = 0; j <= p.type; ++j)
-        if (inc.corner[j] >= 1) q[inc.corner[j] - 1] += wv[j];
-    };
-    T acc = T(0);
-    if (!p.boundary) {
-      for (int i = 0; i < p.inc_count; ++i) {
-        const Inc inc = incs[p.inc_begin + i];
+struct Restrict {
+  static constexpr int kThreads = 128;
+  struct Prm {
+    const T* rf;
+    T *bc, *uc;
+    const T* dinv;
+    T omega;
+    const unsigned* lpts_c;
+    const T* multinv;
+    const int4* items;
+    const Prim* prims;
+    const Inc* incs;
+    int nc;
+    int64_t Sc, Sf, total;
+    int n_if_blocks;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    const int nc = p.nc;
+    if (block < p.n_if_blocks) {
+      const int4 it = p.items[block];
+      const int a = it.z + threadIdx.x;
+      if (a >= it.w) return;
+      const Prim pr = p.prims[it.x];
+      const int b = it.y;
+      int wv[3] = {0, 0, 0};
+      if (pr.type == 0) {
+        wv[0] = nc;
+      } else if (pr.type == 1) {
+        wv[0] = nc - a;
+        wv[1] = a;
+      } else {
+        wv[0] = nc - a - b;
+        wv[1] = a;
+        wv[2] = b;
+      }
+      auto local = [&](const Inc& inc, int q[3]) {
+        q[0] = q[1] = q[2] = 0;
+        for (int j = 0; j <= pr.type; ++j)
+          if (inc.corner[j] >= 1) q[inc.corner[j] - 1] += wv[j];
+      };
+      T acc = T(0);
+      if (!pr.boundary) {
+        for (int i = 0; i < pr.inc_count; ++i) {
+          const Inc inc = p.incs[pr.inc_begin + i];
+          int q[3];
+          local(inc, q);
+          acc += restrict_partial<T, DIM>(p.rf, p.multinv, inc.cell, q, nc, p.Sf);
+        }
+      }
+      for (int i = 0; i < pr.inc_count; ++i) {
+        const Inc inc = p.incs[pr.inc_begin + i];
         int q[3];
         local(inc, q);
-        acc += restrict_partial<T, DIM>(rf, multinv, inc.cell, q, nc, Sf);
+        const int64_t sl = (int64_t)inc.cell * p.Sc + slotq<DIM>(nc, q);
+        p.bc[sl] = acc;
+        if (p.uc) p.uc[sl] = p.omega * p.dinv[sl] * acc;
       }
+      return;
     }
-    for (int i = 0; i < p.inc_count; ++i) {
-      const Inc inc = incs[p.inc_begin + i];
+    const SlotDiv divSc(p.Sc, p.total);
+    const int64_t stride = (int64_t)(nb - p.n_if_blocks) * 128;
+    for (int64_t i = (int64_t)(block - p.n_if_blocks) * 128 + threadIdx.x; i < p.total; i += stride) {
+      const int64_t cell = divSc(i);
       int q[3];
-      local(inc, q);
-      const int64_t sl = (int64_t)inc.cell * Sc + slotq<DIM>(nc, q);
-      bc[sl] = acc;
-      if (uc) uc[sl] = omega * dinv[sl] * acc;
+      unpack<DIM>(p.lpts_c[i - cell * p.Sc], q);
+      if (pclass<DIM>(nc, q) != 0) continue;  // macro-boundary point: an interface item's
+      const T acc = restrict_partial<T, DIM>(p.rf, p.multinv, cell, q, nc, p.Sf);
+      p.bc[i] = acc;
+      if (p.uc) p.uc[i] = p.omega * p.dinv[i] * acc;
     }
-    return;
   }
-  const SlotDiv divSc(Sc, total);
-  const int64_t stride = (int64_t)(gridDim.x - n_if_blocks) * blockDim.x;
-  for (int64_t i = (int64_t)(blockIdx.x - n_if_blocks) * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int64_t cell = divSc(i);
-    int q[3];
-    unpack<DIM>(lpts_c[i - cell * Sc], q);
-    if (pclass<DIM>(nc, q) != 0) continue;  // macro-boundary point: an interface item's
-    const T acc = restrict_partial<T, DIM>(rf, multinv, cell, q, nc, Sf);
-    bc[i] = acc;
-    if (uc) uc[i] = omega * dinv[i] * acc;
-  }
-}
+};
 
 // ---- set-up: inverse diagonals and owner flags ----------------------------------
 // Every slot first takes the centre weight of its macro's class stencil (the
@@ -351,79 +435,112 @@ __global__ void k_diag_invert(double* __restrict__ d64, float* __restrict__ d32,
 // u_f += P e_c at every fine slot: coincident points copy, micro-edge
 // midpoints take the mean of the two coarse end points.
 template <class T, int DIM>
-__global__ void k_prolong_add(T* __restrict__ uf, const T* __restrict__ ec, const unsigned* __restrict__ lpts_f,
-                              int nc, int64_t Sc, int64_t Sf, int64_t total) {
-  const SlotDiv divSf(Sf, total);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cell = divSf(i);
-    int q[3];
-    unpack<DIM>(lpts_f[i - cell * Sf], q);
-    const T* __restrict__ e = ec + cell * Sc;
-    const int px = q[0] & 1, py = q[1] & 1, pz = q[2] & 1;
-    T v;
-    if (!(px | py | pz)) {
-      const int c[3] = {q[0] >> 1, q[1] >> 1, q[2] >> 1};
-      v = e[slotq<DIM>(nc, c)];
-    } else {
-      int d[3] = {px, py, pz};
-      if (DIM == 2) {
-        if (px && py) d[1] = -1;  // the diagonal (1,-1)
+struct Prolong {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    T* uf;
+    const T* ec;
+    const unsigned* lpts_f;
+    int nc;
+    int64_t Sc, Sf, total;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    const int nc = p.nc;
+    const SlotDiv divSf(p.Sf, p.total);
+    GRID_STRIDE(i, p.total) {
+      const int64_t cell = divSf(i);
+      int q[3];
+      unpack<DIM>(p.lpts_f[i - cell * p.Sf], q);
+      const T* __restrict__ e = p.ec + cell * p.Sc;
+      const int px = q[0] & 1, py = q[1] & 1, pz = q[2] & 1;
+      T v;
+      if (!(px | py | pz)) {
+        const int c[3] = {q[0] >> 1, q[1] >> 1, q[2] >> 1};
+        v = e[slotq<DIM>(nc, c)];
       } else {
-        if (px && py && !pz) d[1] = -1;        // (1,-1,0)
-        else if (px && pz && !py) d[2] = -1;   // (1,0,-1)
-        else if (py && pz && !px) d[2] = -1;   // (0,1,-1)
-        else if (px && py && pz) d[1] = -1;    // (1,-1,1)
+        int d[3] = {px, py, pz};
+        if (DIM == 2) {
+          if (px && py) d[1] = -1;  // the diagonal (1,-1)
+        } else {
+          if (px && py && !pz) d[1] = -1;        // (1,-1,0)
+          else if (px && pz && !py) d[2] = -1;   // (1,0,-1)
+          else if (py && pz && !px) d[2] = -1;   // (0,1,-1)
+          else if (px && py && pz) d[1] = -1;    // (1,-1,1)
+        }
+        const int c1[3] = {(q[0] - d[0]) >> 1, (q[1] - d[1]) >> 1, (q[2] - d[2]) >> 1};
+        const int c2[3] = {(q[0] + d[0]) >> 1, (q[1] + d[1]) >> 1, (q[2] + d[2]) >> 1};
+        v = T(0.5) * (e[slotq<DIM>(nc, c1)] + e[slotq<DIM>(nc, c2)]);
       }
-      const int c1[3] = {(q[0] - d[0]) >> 1, (q[1] - d[1]) >> 1, (q[2] - d[2]) >> 1};
-      const int c2[3] = {(q[0] + d[0]) >> 1, (q[1] + d[1]) >> 1, (q[2] + d[2]) >> 1};
-      v = T(0.5) * (e[slotq<DIM>(nc, c1)] + e[slotq<DIM>(nc, c2)]);
+      p.uf[i] = p.uf[i] + v;
     }
-    uf[i] = uf[i] + v;
   }
-}
+};
 
 // Level 0: e = A0^{-1} r on the coarse vertices, written to every copy.
 template <class T>
-__global__ void k_coarse_solve(T* __restrict__ e, const T* __restrict__ r, const T* __restrict__ a0inv,
-                               const int* __restrict__ v_of_slot, const int* __restrict__ slot_of_v, int V,
-                               int64_t nslots) {
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots; s += (int64_t)gridDim.x * blockDim.x) {
-    const T* __restrict__ row = a0inv + (int64_t)v_of_slot[s] * V;
-    T acc = T(0);
-    for (int j = 0; j < V; ++j) acc += row[j] * r[slot_of_v[j]];
-    e[s] = acc;
+struct Coarse {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    T* e;
+    const T *r, *a0inv;
+    const int *v_of_slot, *slot_of_v;
+    int V;
+    int64_t nslots;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    GRID_STRIDE(s, p.nslots) {
+      const T* __restrict__ row = p.a0inv + (int64_t)p.v_of_slot[s] * p.V;
+      T acc = T(0);
+      for (int j = 0; j < p.V; ++j) acc += row[j] * p.r[p.slot_of_v[j]];
+      p.e[s] = acc;
+    }
   }
+};
+
+__device__ __forceinline__ double block_sum(double acc) {
+  __shared__ double sm[THREADS];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sm[0];
 }
 
-// Deterministic two-stage sum of owner[i] * a[i] * b[i] (float64).
+// Deterministic two-stage sum of owner[i] * a[i] * b[i] (float64): RED_BLOCKS
+// partial sums, then one block adds them.
 template <class T>
-__global__ void k_dot_partial(const T* __restrict__ a, const T* __restrict__ b, const unsigned char* __restrict__ owner,
-                              int64_t n, double* __restrict__ partial) {
-  __shared__ double sm[THREADS];
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (owner[i]) acc += (double)a[i] * (double)b[i];
-  sm[threadIdx.x] = acc;
-  __syncthreads();
-  for (int s = THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
-    __syncthreads();
+struct DotPartial {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    const T *a, *b;
+    const unsigned char* owner;
+    int64_t n;
+    double* partial;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    double acc = 0.0;
+    GRID_STRIDE(i, p.n) if (p.owner[i]) acc += (double)p.a[i] * (double)p.b[i];
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) p.partial[block] = t;
   }
-  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
-}
+};
 
-__global__ void k_dot_final(const double* __restrict__ partial, int nb, double* __restrict__ out) {
-  __shared__ double sm[THREADS];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nb; i += THREADS) acc += partial[i];
-  sm[threadIdx.x] = acc;
-  __syncthreads();
-  for (int s = THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
-    __syncthreads();
+struct DotFinal {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    const double* partial;
+    int n_partial;
+    double* out;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int, int) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < p.n_partial; i += THREADS) acc += p.partial[i];
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) *p.out = t;
   }
-  if (threadIdx.x == 0) *out = sm[0];
-}
+};
 
 // r = b - y at every slot, stored as TO (the correction cycle's right-hand
 // side), and per-block partial sums of r^2 over one copy of every
@@ -431,26 +548,30 @@ __global__ void k_dot_final(const double* __restrict__ partial, int nb, double* 
 // With u_out non-null it also performs the correction cycle's first sweep
 // from a zero guess: u_out = omega D^-1 (TO)r.
 template <class TO>
-__global__ void k_residual_norm(TO* __restrict__ out, TO* __restrict__ u_out, const TO* __restrict__ dinv, TO omega,
-                                const double* __restrict__ b, const double* __restrict__ y,
-                                const unsigned char* __restrict__ owner, int64_t n, double* __restrict__ partial) {
-  __shared__ double sm[THREADS];
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double r = b[i] - y[i];
-    const TO rt = (TO)r;
-    out[i] = rt;
-    if (u_out) u_out[i] = omega * dinv[i] * rt;
-    if (owner[i]) acc += r * r;
+struct ResidualNorm {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    TO *out, *u_out;
+    const TO* dinv;
+    TO omega;
+    const double *b, *y;
+    const unsigned char* owner;
+    int64_t n;
+    double* partial;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    double acc = 0.0;
+    GRID_STRIDE(i, p.n) {
+      const double r = p.b[i] - p.y[i];
+      const TO rt = (TO)r;
+      p.out[i] = rt;
+      if (p.u_out) p.u_out[i] = p.omega * p.dinv[i] * rt;
+      if (p.owner[i]) acc += r * r;
+    }
+    const double t = block_sum(acc);
+    if (threadIdx.x == 0) p.partial[block] = t;
   }
-  sm[threadIdx.x] = acc;
-  __syncthreads();
-  for (int s = THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
-}
+};
 
 int grid_for(int64_t n) {
   const int64_t g = (n + THREADS - 1) / THREADS;
@@ -488,146 +609,335 @@ struct Vecs<double> {
     if (e_ != cudaSuccess) return e_;      \
   } while (0)
 
+// ---- launches over a group of meshes --------------------------------------------
+// The V-cycle and the solve loop run over a group of meshes (a mesh alone is a
+// group of one): every step is one launch for all of them (group.cuh), each
+// mesh with its own vectors, tables and block count.  The meshes of a group
+// have the same dimension and smoother sweep counts.
+
+template <class Body>
+struct Batch {
+  std::vector<typename Body::Prm> p;
+  std::vector<int> blocks;
+  void add(const typename Body::Prm& q, int nb) {
+    p.push_back(q);
+    blocks.push_back(nb);
+  }
+  cudaError_t launch(cudaStream_t s) const {
+    return p.empty() ? cudaSuccess : launch_group<Body>(p.data(), blocks.data(), int(p.size()), s);
+  }
+};
+
+int64_t n_slots(const Mesh& m, int l) { return m.levels[l].slots_per_macro * m.n_cells; }
+
 // b_c = P^T r_f on level lf - 1; with u_c non-null also u_c = omega D^-1 b_c
 // (the coarse level's first sweep from a zero guess).
+template <class T, int DIM>
+cudaError_t restrict_d(Mesh* const* ms, int cnt, int lf, const T* const* rf, T* const* bc, T* const* uc,
+                       cudaStream_t s) {
+  Batch<Restrict<T, DIM>> B;
+  for (int i = 0; i < cnt; ++i) {
+    const Mesh& m = *ms[i];
+    const Solver& sv = *m.solver;
+    const LevelDev& Lc = m.levels[lf - 1];
+    const LevelDev& Lf = m.levels[lf];
+    const int64_t total = Lc.slots_per_macro * m.n_cells;
+    const MgLevel& gc = sv.lv[lf - 1];
+    const int64_t want = (total + 127) / 128;
+    const int int_blocks = int(want < 152 * 32 ? (want > 0 ? want : 1) : 152 * 32);
+    B.add({rf[i], bc[i], uc ? uc[i] : nullptr, Vecs<T>::dinv(gc), T(sv.omega), gc.lpts, Vecs<T>::multinv(gc),
+           Lc.items, m.d_prims, m.d_incs, Lc.n, Lc.slots_per_macro, Lf.slots_per_macro, total, Lc.n_items},
+          Lc.n_items + int_blocks);
+  }
+  return B.launch(s);
+}
 template <class T>
-cudaError_t restrict_t(const Mesh& m, int lf, const T* rf, T* bc, cudaStream_t s, T* uc = nullptr) {
-  const Solver& sv = *m.solver;
-  const LevelDev& Lc = m.levels[lf - 1];
-  const LevelDev& Lf = m.levels[lf];
-  const int64_t total = Lc.slots_per_macro * m.n_cells;
-  const MgLevel& gc = sv.lv[lf - 1];
-  const int if_blocks = Lc.n_items;
-  const int64_t want = (total + 127) / 128;
-  const int int_blocks = int(want < 152 * 32 ? (want > 0 ? want : 1) : 152 * 32);
-  const T omega = T(sv.omega);
-  if (m.dim == 2)
-    k_restrict_fused<T, 2><<<if_blocks + int_blocks, 128, 0, s>>>(rf, bc, uc, Vecs<T>::dinv(gc), omega, gc.lpts,
-                                                                   Vecs<T>::multinv(gc), Lc.items, m.d_prims,
-                                                                   m.d_incs, Lc.n, Lc.slots_per_macro,
-                                                                   Lf.slots_per_macro, total, if_blocks);
-  else
-    k_restrict_fused<T, 3><<<if_blocks + int_blocks, 128, 0, s>>>(rf, bc, uc, Vecs<T>::dinv(gc), omega, gc.lpts,
-                                                                   Vecs<T>::multinv(gc), Lc.items, m.d_prims,
-                                                                   m.d_incs, Lc.n, Lc.slots_per_macro,
-                                                                   Lf.slots_per_macro, total, if_blocks);
-  return cudaGetLastError();
+cudaError_t restrict_g(Mesh* const* ms, int cnt, int lf, const T* const* rf, T* const* bc, T* const* uc,
+                       cudaStream_t s) {
+  return ms[0]->dim == 2 ? restrict_d<T, 2>(ms, cnt, lf, rf, bc, uc, s) : restrict_d<T, 3>(ms, cnt, lf, rf, bc, uc, s);
+}
+
+// u_f += P e_c
+template <class T, int DIM>
+cudaError_t prolong_d(Mesh* const* ms, int cnt, int lf, const T* const* ec, T* const* uf, cudaStream_t s) {
+  Batch<Prolong<T, DIM>> B;
+  for (int i = 0; i < cnt; ++i) {
+    const Mesh& m = *ms[i];
+    const LevelDev& Lc = m.levels[lf - 1];
+    const LevelDev& Lf = m.levels[lf];
+    const int64_t total = Lf.slots_per_macro * m.n_cells;
+    B.add({uf[i], ec[i], m.solver->lv[lf].lpts, Lc.n, Lc.slots_per_macro, Lf.slots_per_macro, total},
+          grid_for(total));
+  }
+  return B.launch(s);
+}
+template <class T>
+cudaError_t prolong_g(Mesh* const* ms, int cnt, int lf, const T* const* ec, T* const* uf, cudaStream_t s) {
+  return ms[0]->dim == 2 ? prolong_d<T, 2>(ms, cnt, lf, ec, uf, s) : prolong_d<T, 3>(ms, cnt, lf, ec, uf, s);
 }
 
 template <class T>
-cudaError_t prolong_add_t(const Mesh& m, int lf, const T* ec, T* uf, cudaStream_t s) {
-  const Solver& sv = *m.solver;
-  const LevelDev& Lc = m.levels[lf - 1];
-  const LevelDev& Lf = m.levels[lf];
-  const int64_t total = Lf.slots_per_macro * m.n_cells;
-  if (m.dim == 2)
-    k_prolong_add<T, 2><<<grid_for(total), THREADS, 0, s>>>(uf, ec, sv.lv[lf].lpts, Lc.n, Lc.slots_per_macro,
-                                                             Lf.slots_per_macro, total);
-  else
-    k_prolong_add<T, 3><<<grid_for(total), THREADS, 0, s>>>(uf, ec, sv.lv[lf].lpts, Lc.n, Lc.slots_per_macro,
-                                                             Lf.slots_per_macro, total);
-  return cudaGetLastError();
+cudaError_t jacobi_g(Mesh* const* ms, int cnt, int l, T* const* u, const T* const* b, const T* const* y,
+                     cudaStream_t s) {
+  Batch<Jacobi<T>> B;
+  for (int i = 0; i < cnt; ++i) {
+    const int64_t ns = n_slots(*ms[i], l);
+    B.add({u[i], b[i], y[i], Vecs<T>::dinv(ms[i]->solver->lv[l]), T(ms[i]->solver->omega), ns}, grid_for(ns));
+  }
+  return B.launch(s);
 }
 
-// One V(nu1, nu2) cycle on level l for A u = b (u updated in place).
 template <class T>
-// first_done: u already holds the first pre-smoothing sweep from a zero guess
-// (u = omega D^-1 b, written by the launch that produced b), so one sweep
-// fewer is run here.
-cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s, bool first_done = false) {
-  Solver& sv = *m.solver;
-  MgLevel& g = sv.lv[l];
-  const int64_t ns = m.levels[l].slots_per_macro * m.n_cells;
-  const char* what;
-  if (l == 0) {
-    k_coarse_solve<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, Vecs<T>::a0inv(sv), sv.v_of_slot0, sv.slot_of_v0,
-                                                       sv.nv0, ns);
-    return cudaGetLastError();
+cudaError_t residual_g(Mesh* const* ms, int cnt, int l, T* const* r, const T* const* b, const T* const* y,
+                       cudaStream_t s) {
+  Batch<Residual<T>> B;
+  for (int i = 0; i < cnt; ++i) {
+    const int64_t ns = n_slots(*ms[i], l);
+    B.add({r[i], b[i], y[i], ns}, grid_for(ns));
   }
-  T* y = Vecs<T>::y(g);
-  T* r = Vecs<T>::r(g);
-  const T omega = T(sv.omega);
-  const LevelDev& L = m.levels[l];
-  // 2D fp32 cycles: every sweep is one fused launch (apply, interface and
-  // Jacobi update together), alternating between u and y; the residual
-  // likewise.  Float64 cycles and 3D apply, then update.
-  constexpr bool fused_ok = sizeof(T) == 4;
-  // `cur` holds the smoothed iterate; it alternates between u and y and is
-  // copied back into u only if the sweep count is odd
-  T* cur = u;
-  auto sweeps2d = [&](int count) -> cudaError_t {
-    for (int it = 0; it < count; ++it) {
-      T* alt = cur == u ? y : u;
-      HY_TRY(launch_sweep2d(Vecs<T>::dtype, true, m, L, cur, b, Vecs<T>::dinv(g), sv.omega, alt, s));
-      cur = alt;
-    }
-    return cudaSuccess;
-  };
-  const int pre = sv.nu1 - (first_done ? 1 : 0);
-  if (m.dim == 2 && fused_ok) {
-    HY_TRY(sweeps2d(pre));
-    HY_TRY(launch_sweep2d(Vecs<T>::dtype, false, m, L, cur, b, Vecs<T>::dinv(g), sv.omega, r, s));
-  } else {
-    for (int it = 0; it < pre; ++it) {
-      HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
-      k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
-      HY_TRY(cudaGetLastError());
-    }
-    HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
-    k_residual<T><<<grid_for(ns), THREADS, 0, s>>>(r, b, y, ns);
-    HY_TRY(cudaGetLastError());
+  return B.launch(s);
+}
+
+template <class T>
+cudaError_t copy_g(Mesh* const* ms, int cnt, int l, T* const* dst, const T* const* src, cudaStream_t s) {
+  Batch<Copy<T>> B;
+  for (int i = 0; i < cnt; ++i) {
+    const int64_t ns = n_slots(*ms[i], l);
+    B.add({dst[i], src[i], ns}, grid_for(ns));
   }
-  MgLevel& gc = sv.lv[l - 1];
-  T* bc = Vecs<T>::b(gc);
-  T* uc = Vecs<T>::u(gc);
-  // the restriction also performs the coarse level's first sweep from zero;
-  // level 0 is solved directly and overwrites all of uc
-  const bool first = sv.nu1 >= 1 && l - 1 > 0;
-  HY_TRY(restrict_t<T>(m, l, r, bc, s, first ? uc : nullptr));
-  if (!first && l - 1 > 0)
-    HY_TRY(cudaMemsetAsync(uc, 0, sizeof(T) * m.levels[l - 1].slots_per_macro * m.n_cells, s));
-  HY_TRY(vcycle_t<T>(m, l - 1, bc, uc, s, first));
-  HY_TRY(prolong_add_t<T>(m, l, uc, cur, s));
-  if (m.dim == 2 && fused_ok) {
-    HY_TRY(sweeps2d(sv.nu2));
-    if (cur != u) HY_TRY(cudaMemcpyAsync(u, cur, sizeof(T) * ns, cudaMemcpyDeviceToDevice, s));
-  } else {
-    for (int it = 0; it < sv.nu2; ++it) {
-      HY_TRY(launch_apply(m, l, Vecs<T>::dtype, u, y, s, nullptr, &what));
-      k_jacobi<T><<<grid_for(ns), THREADS, 0, s>>>(u, b, y, Vecs<T>::dinv(g), omega, ns);
-      HY_TRY(cudaGetLastError());
+  return B.launch(s);
+}
+
+template <class T>
+cudaError_t zero_g(Mesh* const* ms, int cnt, int l, T* const* p, cudaStream_t s) {
+  Batch<Zero<T>> B;
+  for (int i = 0; i < cnt; ++i) {
+    const int64_t ns = n_slots(*ms[i], l);
+    B.add({p[i], ns}, grid_for(ns));
+  }
+  return B.launch(s);
+}
+
+// Level 0: e = A0^{-1} r
+template <class T>
+cudaError_t coarse_g(Mesh* const* ms, int cnt, T* const* e, const T* const* r, cudaStream_t s) {
+  Batch<Coarse<T>> B;
+  for (int i = 0; i < cnt; ++i) {
+    const Solver& sv = *ms[i]->solver;
+    const int64_t ns = n_slots(*ms[i], 0);
+    B.add({e[i], r[i], Vecs<T>::a0inv(sv), sv.v_of_slot0, sv.slot_of_v0, sv.nv0, ns}, grid_for(ns));
+  }
+  return B.launch(s);
+}
+
+// y = A x of every member (element type dtype as hyteg_apply's).  Alone: the
+// mesh's own apply; in a group the members of each element type share the
+// launches (the float-float apply runs native fp64 on levels whose weights
+// lie outside its range).
+cudaError_t apply_g(Mesh* const* ms, int cnt, int l, int dtype, const void* const* x, void* const* y,
+                    cudaStream_t s) {
+  if (cnt == 1) {
+    const char* what = "";
+    return launch_apply(*ms[0], l, dtype, x[0], y[0], s, nullptr, &what);
+  }
+  for (int dt = 1; dt <= 3; ++dt) {
+    std::vector<const Mesh*> mm;
+    std::vector<int> lv;
+    std::vector<const void*> xx;
+    std::vector<void*> yy;
+    for (int i = 0; i < cnt; ++i) {
+      const int eff = (dtype == 1 && !ms[i]->levels[l].ff_ok) ? 3 : dtype;
+      if (eff != dt) continue;
+      mm.push_back(ms[i]);
+      lv.push_back(l);
+      xx.push_back(x[i]);
+      yy.push_back(y[i]);
+    }
+    if (mm.empty()) continue;
+    const int k = int(mm.size());
+    if (ms[0]->dim == 2) {
+      HY_TRY(launch_apply2d_batch(dt, mm.data(), lv.data(), xx.data(), yy.data(), k, s));
+    } else {
+      HY_TRY(launch_slab3d_group(dt, mm.data(), lv.data(), xx.data(), yy.data(), k, s));
+      HY_TRY(launch_interface_reduce_group(dt, mm.data(), lv.data(), xx.data(), yy.data(), k, s));
     }
   }
   return cudaSuccess;
 }
 
-// ||v||_2 over one copy of every non-Dirichlet DoF, to host (synchronises s).
+// y = A (u + ulo) in float64, difference form (ulo nullable); Dirichlet
+// rows: y = u.
+cudaError_t accurate_g(Mesh* const* ms, int cnt, int l, const double* const* u, const double* const* ulo,
+                       double* const* y, cudaStream_t s) {
+  std::vector<const Mesh*> mm(ms, ms + cnt);
+  std::vector<int> lv(cnt, l);
+  std::vector<const void*> uu(u, u + cnt);
+  std::vector<void*> yy(y, y + cnt);
+  if (ms[0]->dim == 2) {
+    Batch<PartialDiff<2>> B;
+    for (int i = 0; i < cnt; ++i) {
+      const LevelDev& L = ms[i]->levels[l];
+      const int64_t ns = n_slots(*ms[i], l);
+      B.add({u[i], ulo ? ulo[i] : nullptr, y[i], ms[i]->solver->lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns},
+            grid_for(ns));
+    }
+    HY_TRY(B.launch(s));
+  } else {
+    Batch<PartialDiff<3>> B;
+    for (int i = 0; i < cnt; ++i) {
+      const LevelDev& L = ms[i]->levels[l];
+      const int64_t ns = n_slots(*ms[i], l);
+      B.add({u[i], ulo ? ulo[i] : nullptr, y[i], ms[i]->solver->lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns},
+            grid_for(ns));
+    }
+    HY_TRY(B.launch(s));
+  }
+  // sum the copies; Dirichlet rows: y = u
+  return launch_interface_reduce_group(3, mm.data(), lv.data(), uu.data(), yy.data(), cnt, s);
+}
+
+// 2D fp32 fused sweeps (apply, interface and Jacobi update or residual in one
+// launch): out = sweep(cur) with the level's b and inverse diagonal
+cudaError_t sweep2d_g(bool jacobi, Mesh* const* ms, int cnt, int l, const float* const* cur, const float* const* b,
+                      float* const* out, cudaStream_t s) {
+  if (cnt == 1) {
+    const Mesh& m = *ms[0];
+    return launch_sweep2d(2, jacobi, m, m.levels[l], cur[0], b[0], m.solver->lv[l].dinv32, m.solver->omega, out[0],
+                          s);
+  }
+  std::vector<const Mesh*> mm(ms, ms + cnt);
+  std::vector<int> lv(cnt, l);
+  std::vector<const void*> uu(cur, cur + cnt), bb(b, b + cnt), dd(cnt);
+  std::vector<void*> oo(out, out + cnt);
+  std::vector<double> om(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    dd[i] = ms[i]->solver->lv[l].dinv32;
+    om[i] = ms[i]->solver->omega;
+  }
+  return launch_sweep2d_group(jacobi, mm.data(), lv.data(), uu.data(), bb.data(), dd.data(), om.data(), oo.data(),
+                              cnt, s);
+}
+
+// One V(nu1, nu2) cycle on level l for A u = b of every member (u updated in
+// place).  first_done: u already holds the first pre-smoothing sweep from a
+// zero guess (u = omega D^-1 b, written by the launch that produced b), so
+// one sweep fewer is run here.
 template <class T>
-cudaError_t norm2(const Mesh& m, int l, const T* v, double* out, cudaStream_t s) {
-  const Solver& sv = *m.solver;
-  const int64_t ns = m.levels[l].slots_per_macro * m.n_cells;
-  k_dot_partial<T><<<RED_BLOCKS, THREADS, 0, s>>>(v, v, sv.lv[l].owner, ns, sv.red);
-  HY_TRY(cudaGetLastError());
-  k_dot_final<<<1, THREADS, 0, s>>>(sv.red, RED_BLOCKS, sv.red + RED_BLOCKS);
-  HY_TRY(cudaGetLastError());
-  double h = 0.0;
-  HY_TRY(cudaMemcpyAsync(&h, sv.red + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s));
+cudaError_t vcycle_g(Mesh* const* ms, int cnt, int l, const T* const* b, T* const* u, cudaStream_t s,
+                     bool first_done) {
+  if (l == 0) return coarse_g<T>(ms, cnt, u, b, s);
+  const Solver& sv0 = *ms[0]->solver;
+  std::vector<T*> y(cnt), r(cnt), cur(u, u + cnt), alt(cnt), bc(cnt), uc(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    MgLevel& g = ms[i]->solver->lv[l];
+    MgLevel& gc = ms[i]->solver->lv[l - 1];
+    y[i] = Vecs<T>::y(g);
+    r[i] = Vecs<T>::r(g);
+    bc[i] = Vecs<T>::b(gc);
+    uc[i] = Vecs<T>::u(gc);
+  }
+  // 2D fp32 cycles: every sweep is one fused launch (apply, interface and
+  // Jacobi update together), alternating between u and y; the residual
+  // likewise.  Float64 cycles and 3D: apply, then update.  `cur` holds the
+  // smoothed iterate; it alternates between u and y and is copied back into
+  // u only if the sweep count is odd.
+  const bool fused = sizeof(T) == 4 && ms[0]->dim == 2;
+  auto sweeps = [&](int count) -> cudaError_t {
+    for (int it = 0; it < count; ++it) {
+      for (int i = 0; i < cnt; ++i) alt[i] = cur[i] == u[i] ? y[i] : u[i];
+      HY_TRY(sweep2d_g(true, ms, cnt, l, reinterpret_cast<const float* const*>(cur.data()),
+                       reinterpret_cast<const float* const*>(b), reinterpret_cast<float* const*>(alt.data()), s));
+      cur.swap(alt);
+    }
+    return cudaSuccess;
+  };
+  const std::vector<const void*> uv(u, u + cnt);
+  const std::vector<void*> yv(y.begin(), y.end());
+  const int pre = sv0.nu1 - (first_done ? 1 : 0);
+  if (fused) {
+    HY_TRY(sweeps(pre));
+    HY_TRY(sweep2d_g(false, ms, cnt, l, reinterpret_cast<const float* const*>(cur.data()),
+                     reinterpret_cast<const float* const*>(b), reinterpret_cast<float* const*>(r.data()), s));
+  } else {
+    for (int it = 0; it < pre; ++it) {
+      HY_TRY(apply_g(ms, cnt, l, Vecs<T>::dtype, uv.data(), yv.data(), s));
+      HY_TRY(jacobi_g<T>(ms, cnt, l, u, b, y.data(), s));
+    }
+    HY_TRY(apply_g(ms, cnt, l, Vecs<T>::dtype, uv.data(), yv.data(), s));
+    HY_TRY(residual_g<T>(ms, cnt, l, r.data(), b, y.data(), s));
+  }
+  // the restriction also performs the coarse level's first sweep from zero;
+  // level 0 is solved directly and overwrites all of uc
+  const bool first = sv0.nu1 >= 1 && l - 1 > 0;
+  HY_TRY(restrict_g<T>(ms, cnt, l, r.data(), bc.data(), first ? uc.data() : nullptr, s));
+  if (!first && l - 1 > 0) HY_TRY(zero_g<T>(ms, cnt, l - 1, uc.data(), s));
+  HY_TRY(vcycle_g<T>(ms, cnt, l - 1, bc.data(), uc.data(), s, first));
+  HY_TRY(prolong_g<T>(ms, cnt, l, uc.data(), cur.data(), s));
+  if (fused) {
+    HY_TRY(sweeps(sv0.nu2));
+    if (cur[0] != u[0]) HY_TRY(copy_g<T>(ms, cnt, l, u, cur.data(), s));
+  } else {
+    for (int it = 0; it < sv0.nu2; ++it) {
+      HY_TRY(apply_g(ms, cnt, l, Vecs<T>::dtype, uv.data(), yv.data(), s));
+      HY_TRY(jacobi_g<T>(ms, cnt, l, u, b, y.data(), s));
+    }
+  }
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t vcycle_t(Mesh& m, int l, const T* b, T* u, cudaStream_t s, bool first_done = false) {
+  Mesh* mp = &m;
+  return vcycle_g<T>(&mp, 1, l, &b, &u, s, first_done);
+}
+
+// ||v||_2 over one copy of every non-Dirichlet DoF of every member, to host
+// (synchronises s once).
+template <class T>
+cudaError_t norms_g(Mesh* const* ms, int cnt, int l, const T* const* v, double* out, cudaStream_t s) {
+  Batch<DotPartial<T>> P;
+  Batch<DotFinal> F;
+  for (int i = 0; i < cnt; ++i) {
+    const Solver& sv = *ms[i]->solver;
+    P.add({v[i], v[i], sv.lv[l].owner, n_slots(*ms[i], l), sv.red}, RED_BLOCKS);
+    F.add({sv.red, RED_BLOCKS, sv.red + RED_BLOCKS}, 1);
+  }
+  HY_TRY(P.launch(s));
+  HY_TRY(F.launch(s));
+  for (int i = 0; i < cnt; ++i)
+    HY_TRY(cudaMemcpyAsync(out + i, ms[i]->solver->red + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s));
   HY_TRY(cudaStreamSynchronize(s));
-  *out = sqrt(h);
+  for (int i = 0; i < cnt; ++i) out[i] = sqrt(out[i]);
   return cudaSuccess;
 }
 
 }  // namespace
 
 cudaError_t mg_restrict(const Mesh& m, int lf, int dtype, const void* rf, void* bc, cudaStream_t s) {
-  return dtype == 2 ? restrict_t<float>(m, lf, (const float*)rf, (float*)bc, s)
-                    : restrict_t<double>(m, lf, (const double*)rf, (double*)bc, s);
+  Mesh* mp = const_cast<Mesh*>(&m);
+  if (dtype == 2) {
+    const float* r = static_cast<const float*>(rf);
+    float* b = static_cast<float*>(bc);
+    return restrict_g<float>(&mp, 1, lf, &r, &b, nullptr, s);
+  }
+  const double* r = static_cast<const double*>(rf);
+  double* b = static_cast<double*>(bc);
+  return restrict_g<double>(&mp, 1, lf, &r, &b, nullptr, s);
 }
 
 cudaError_t mg_prolong_add(const Mesh& m, int lf, int dtype, const void* ec, void* uf, cudaStream_t s) {
-  return dtype == 2 ? prolong_add_t<float>(m, lf, (const float*)ec, (float*)uf, s)
-                    : prolong_add_t<double>(m, lf, (const double*)ec, (double*)uf, s);
+  Mesh* mp = const_cast<Mesh*>(&m);
+  if (dtype == 2) {
+    const float* e = static_cast<const float*>(ec);
+    float* u = static_cast<float*>(uf);
+    return prolong_g<float>(&mp, 1, lf, &e, &u, s);
+  }
+  const double* e = static_cast<const double*>(ec);
+  double* u = static_cast<double*>(uf);
+  return prolong_g<double>(&mp, 1, lf, &e, &u, s);
 }
+
+namespace {
 
 // One V-cycle on level l's own vectors (b, u of the level's workspace).  From
 // the second solve on the same workspace it runs as a CUDA graph, captured
@@ -635,19 +945,24 @@ cudaError_t mg_prolong_add(const Mesh& m, int lf, int dtype, const void* ec, voi
 // one graph launch.  A first solve runs the cycle directly (instantiating a
 // graph costs more than the launches it saves when the workspace serves one
 // solve only), as do streams that cannot be captured (the legacy default
-// stream).
+// stream).  A group of several meshes runs its cycles directly.
 template <class T>
-cudaError_t vcycle_own(Mesh& m, int l, cudaStream_t s, bool first_done) {
-  Solver& sv = *m.solver;
-  MgLevel& g = sv.lv[l];
-  if (sv.solves == 0 || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
-    return vcycle_t<T>(m, l, Vecs<T>::b(g), Vecs<T>::u(g), s, first_done);
+cudaError_t vcycle_own(Mesh* const* ms, int cnt, int l, cudaStream_t s, bool first_done) {
+  std::vector<const T*> b(cnt);
+  std::vector<T*> u(cnt);
+  for (int i = 0; i < cnt; ++i) {
+    b[i] = Vecs<T>::b(ms[i]->solver->lv[l]);
+    u[i] = Vecs<T>::u(ms[i]->solver->lv[l]);
+  }
+  Solver& sv = *ms[0]->solver;
+  if (cnt > 1 || sv.solves == 0 || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
+    return vcycle_g<T>(ms, cnt, l, b.data(), u.data(), s, first_done);
   std::vector<cudaGraphExec_t>& ge = sizeof(T) == 4 ? sv.graph32 : sv.graph64;
   if ((int)ge.size() <= l) ge.resize(l + 1, nullptr);
   if (!ge[l]) {
     cudaGraph_t graph = nullptr;
     HY_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const cudaError_t e = vcycle_t<T>(m, l, Vecs<T>::b(g), Vecs<T>::u(g), s, first_done);
+    const cudaError_t e = vcycle_g<T>(ms, 1, l, b.data(), u.data(), s, first_done);
     const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -663,6 +978,40 @@ cudaError_t vcycle_own(Mesh& m, int l, cudaStream_t s, bool first_done) {
   return cudaGraphLaunch(ge[l], s);
 }
 
+// u += e (float64 iterate) or (u + ulo) += e (two-part iterate)
+template <class T>
+struct AddOne {
+  static constexpr int kThreads = THREADS;
+  struct Prm {
+    double* u;
+    const T* e;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Prm& p, int block, int nb) {
+    GRID_STRIDE(i, p.n) p.u[i] = p.u[i] + (double)p.e[i];
+  }
+};
+
+template <class T>
+cudaError_t update_g(Mesh* const* ms, int cnt, int l, double* const* u, double* const* ulo, cudaStream_t s) {
+  if (ulo) {
+    Batch<AddTwoPart<T>> B;
+    for (int i = 0; i < cnt; ++i) {
+      const int64_t ns = n_slots(*ms[i], l);
+      B.add({u[i], ulo[i], Vecs<T>::u(ms[i]->solver->lv[l]), ns}, grid_for(ns));
+    }
+    return B.launch(s);
+  }
+  Batch<AddOne<T>> B;
+  for (int i = 0; i < cnt; ++i) {
+    const int64_t ns = n_slots(*ms[i], l);
+    B.add({u[i], Vecs<T>::u(ms[i]->solver->lv[l]), ns}, grid_for(ns));
+  }
+  return B.launch(s);
+}
+
+}  // namespace
+
 cudaError_t mg_vcycle(Mesh& m, int l, int dtype, const void* b, void* u, cudaStream_t s) {
   return dtype == 2 ? vcycle_t<float>(m, l, (const float*)b, (float*)u, s)
                     : vcycle_t<double>(m, l, (const double*)b, (double*)u, s);
@@ -671,19 +1020,13 @@ cudaError_t mg_vcycle(Mesh& m, int l, int dtype, const void* b, void* u, cudaStr
 // y = A (u + ulo) in float64, difference form (ulo nullable); Dirichlet
 // rows: y = u.
 cudaError_t accurate_apply(const Mesh& m, int l, const double* u, const double* ulo, double* y, cudaStream_t s) {
-  const Solver& sv = *m.solver;
-  const LevelDev& L = m.levels[l];
-  const int64_t ns = L.slots_per_macro * m.n_cells;
-  if (m.dim == 2)
-    k_partial_diff<2><<<grid_for(ns), THREADS, 0, s>>>(u, ulo, y, sv.lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns);
-  else
-    k_partial_diff<3><<<grid_for(ns), THREADS, 0, s>>>(u, ulo, y, sv.lv[l].lpts, L.st64, L.n, L.slots_per_macro, ns);
-  HY_TRY(cudaGetLastError());
-  return launch_interface_reduce(3, m.dim, m, L, u, y, s);  // sum the copies; Dirichlet rows: y = u
+  Mesh* mp = const_cast<Mesh*>(&m);
+  return accurate_g(&mp, 1, l, &u, ulo ? &ulo : nullptr, &y, s);
 }
 
-cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, double* ulo, double rtol,
-                     int max_iter, cudaStream_t s, int* iters, double* relres) {
+cudaError_t mg_solve_group(Mesh* const* ms, int cnt, int l, int mode, const double* const* b, double* const* u,
+                           double* const* ulo, double rtol, int max_iter, cudaStream_t s, int* iters,
+                           double* relres) {
   // Residual correction: r = b - A u (float64), e = V-cycle(A e = r)
   // from e = 0 in fp32 (HYTEG_SOLVE_MIXED) or float64 (HYTEG_SOLVE_F64),
   // u += e.  The float64 residual bounds the attainable accuracy; the cycles
@@ -692,96 +1035,183 @@ cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, doubl
   // residual takes both parts and every update keeps its rounding error in
   // ulo, which lifts the floor that the float64 rounding of u sets on the
   // relative residual (it grows like h^-2).
-  Solver& sv = *m.solver;
-  MgLevel& g = sv.lv[l];
-  const int64_t ns = m.levels[l].slots_per_macro * m.n_cells;
-  double nb = 0.0;
-  HY_TRY(norm2<double>(m, l, b, &nb, s));
-  if (nb == 0.0) nb = 1.0;
-  double rel = 0.0, prev = 0.0;
-  int it = 0, stalled = 0;
+  //
+  // Every member of the group follows this loop on its own residuals (its
+  // own stopping decisions and iteration count); the members still
+  // iterating share each launch, and one synchronisation per residual pass
+  // reads all their norms.
+  struct State {
+    double nb = 1.0, rel = 0.0, prev = 0.0;
+    int it = 0, stalled = 0;
+    bool fast = true, live = true;
+  };
+  std::vector<State> st(cnt);
+  {
+    std::vector<double> nb(cnt);
+    HY_TRY(norms_g<double>(ms, cnt, l, b, nb.data(), s));
+    for (int i = 0; i < cnt; ++i) st[i].nb = nb[i] == 0.0 ? 1.0 : nb[i];
+  }
   // While the residual is large the float-float apply gives it accurately
   // enough (its error is ~2^-44 of sum_j |a_ij u_j|, orders below a residual
   // of relative size 1e-6) at a third of the cost of the float64 difference
   // form; from there on, and for every stopping decision, the difference form.
   constexpr double kFastUntil = 1e-6;
-  bool fast = true;
   // r = b - A u goes straight into the correction cycle's right-hand side
   // (fp32 for HYTEG_SOLVE_MIXED), its norm from the same pass, and the
   // cycle's first sweep from a zero correction with it
-  const bool first = sv.nu1 >= 1 && l > 0;
-  auto residual = [&](bool ff, double* out) -> cudaError_t {
-    if (ff) {
-      const char* what = "";
-      HY_TRY(launch_apply(m, l, 1, u, g.y64, s, nullptr, &what));
-    } else {
-      HY_TRY(accurate_apply(m, l, u, ulo, g.y64, s));
-    }
-    if (mode == 2)
-      k_residual_norm<float><<<RED_BLOCKS, THREADS, 0, s>>>(g.b32, first ? g.u32 : nullptr, g.dinv32,
-                                                             (float)sv.omega, b, g.y64, g.owner, ns, sv.red);
-    else
-      k_residual_norm<double><<<RED_BLOCKS, THREADS, 0, s>>>(g.b64, first ? g.u64 : nullptr, g.dinv64, sv.omega, b,
-                                                              g.y64, g.owner, ns, sv.red);
-    HY_TRY(cudaGetLastError());
-    k_dot_final<<<1, THREADS, 0, s>>>(sv.red, RED_BLOCKS, sv.red + RED_BLOCKS);
-    HY_TRY(cudaGetLastError());
-    double h = 0.0;
-    HY_TRY(cudaMemcpyAsync(&h, sv.red + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s));
-    HY_TRY(cudaStreamSynchronize(s));
-    *out = sqrt(h) / nb;
-    return cudaSuccess;
-  };
-  for (;; ++it) {
-    HY_TRY(residual(fast, &rel));
-    if (fast && (rel <= (rtol > kFastUntil ? rtol : kFastUntil) || !std::isfinite(rel))) {
-      fast = false;
-      HY_TRY(residual(false, &rel));
-    }
-    if (rel <= rtol || it >= max_iter || !std::isfinite(rel)) break;  // a non-finite residual ends the loop
-    // A cycle reduces the residual by its convergence factor (about 0.4 on
-    // most meshes, up to about 0.8 on strongly distorted 3D ones) until the
-    // representation of u is reached: the float64 rounding of u, or far
-    // lower for the two-part iterate.  Two iterations in a row that each
-    // remove less than a tenth of it mean that floor has been reached.
-    stalled = (it > 0 && rel > 0.9 * prev) ? stalled + 1 : 0;
-    if (stalled >= 2) {
-      if (fast) {  // a stall seen on the float-float residual: decide on the accurate one
-        fast = false;
-        HY_TRY(residual(false, &rel));
-        if (rel <= rtol) break;
-        stalled = 0;
+  const bool first = ms[0]->solver->nu1 >= 1 && l > 0;
+  // the residual of the members `idx`, float-float or difference form as
+  // their `fast` flags say, and their relative norms
+  auto residual = [&](const std::vector<int>& idx) -> cudaError_t {
+    if (idx.empty()) return cudaSuccess;
+    for (int pass = 0; pass < 2; ++pass) {  // float-float members, then difference-form members
+      std::vector<Mesh*> mm;
+      std::vector<const double*> uu, ll;
+      std::vector<double*> yy;
+      for (int i : idx) {
+        if (st[i].fast != (pass == 0)) continue;
+        mm.push_back(ms[i]);
+        uu.push_back(u[i]);
+        ll.push_back(ulo ? ulo[i] : nullptr);
+        yy.push_back(ms[i]->solver->lv[l].y64);
+      }
+      if (mm.empty()) continue;
+      const int k = int(mm.size());
+      if (pass == 0) {
+        std::vector<const void*> xv(uu.begin(), uu.end());
+        std::vector<void*> yv(yy.begin(), yy.end());
+        HY_TRY(apply_g(mm.data(), k, l, 1, xv.data(), yv.data(), s));
       } else {
-        break;
+        HY_TRY(accurate_g(mm.data(), k, l, uu.data(), ulo ? ll.data() : nullptr, yy.data(), s));
       }
     }
-    prev = rel;
+    Batch<DotFinal> F;
     if (mode == 2) {
-      if (!first) HY_TRY(cudaMemsetAsync(g.u32, 0, sizeof(float) * ns, s));
-      HY_TRY(vcycle_own<float>(m, l, s, first));
-      if (ulo)
-        k_add_two_part<float><<<grid_for(ns), THREADS, 0, s>>>(u, ulo, g.u32, ns);
-      else
-        k_add_f32<<<grid_for(ns), THREADS, 0, s>>>(u, g.u32, ns);
-      HY_TRY(cudaGetLastError());
+      Batch<ResidualNorm<float>> R;
+      for (int i : idx) {
+        MgLevel& g = ms[i]->solver->lv[l];
+        R.add({g.b32, first ? g.u32 : nullptr, g.dinv32, (float)ms[i]->solver->omega, b[i], g.y64, g.owner,
+               n_slots(*ms[i], l), ms[i]->solver->red},
+              RED_BLOCKS);
+      }
+      HY_TRY(R.launch(s));
     } else {
-      if (!first) HY_TRY(cudaMemsetAsync(g.u64, 0, sizeof(double) * ns, s));
-      HY_TRY(vcycle_own<double>(m, l, s, first));
-      if (ulo)
-        k_add_two_part<double><<<grid_for(ns), THREADS, 0, s>>>(u, ulo, g.u64, ns);
-      else
-        k_add_f64<<<grid_for(ns), THREADS, 0, s>>>(u, g.u64, ns);
-      HY_TRY(cudaGetLastError());
+      Batch<ResidualNorm<double>> R;
+      for (int i : idx) {
+        MgLevel& g = ms[i]->solver->lv[l];
+        R.add({g.b64, first ? g.u64 : nullptr, g.dinv64, ms[i]->solver->omega, b[i], g.y64, g.owner,
+               n_slots(*ms[i], l), ms[i]->solver->red},
+              RED_BLOCKS);
+      }
+      HY_TRY(R.launch(s));
     }
+    for (int i : idx) F.add({ms[i]->solver->red, RED_BLOCKS, ms[i]->solver->red + RED_BLOCKS}, 1);
+    HY_TRY(F.launch(s));
+    std::vector<double> h(idx.size());
+    for (size_t k = 0; k < idx.size(); ++k)
+      HY_TRY(cudaMemcpyAsync(&h[k], ms[idx[k]]->solver->red + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost,
+                             s));
+    HY_TRY(cudaStreamSynchronize(s));
+    for (size_t k = 0; k < idx.size(); ++k) st[idx[k]].rel = sqrt(h[k]) / st[idx[k]].nb;
+    return cudaSuccess;
+  };
+  for (;;) {
+    std::vector<int> live, redo;
+    for (int i = 0; i < cnt; ++i)
+      if (st[i].live) live.push_back(i);
+    if (live.empty()) break;
+    HY_TRY(residual(live));
+    for (int i : live)
+      if (st[i].fast && (st[i].rel <= (rtol > kFastUntil ? rtol : kFastUntil) || !std::isfinite(st[i].rel))) {
+        st[i].fast = false;
+        redo.push_back(i);
+      }
+    HY_TRY(residual(redo));
+    redo.clear();
+    std::vector<int> go;
+    for (int i : live) {
+      State& q = st[i];
+      if (q.rel <= rtol || q.it >= max_iter || !std::isfinite(q.rel)) {  // a non-finite residual ends the loop
+        q.live = false;
+        continue;
+      }
+      // A cycle reduces the residual by its convergence factor (about 0.4 on
+      // most meshes, up to about 0.8 on strongly distorted 3D ones) until the
+      // representation of u is reached: the float64 rounding of u, or far
+      // lower for the two-part iterate.  Two iterations in a row that each
+      // remove less than a tenth of it mean that floor has been reached.
+      q.stalled = (q.it > 0 && q.rel > 0.9 * q.prev) ? q.stalled + 1 : 0;
+      if (q.stalled >= 2) {
+        if (q.fast) {  // a stall seen on the float-float residual: decide on the accurate one
+          q.fast = false;
+          redo.push_back(i);
+          continue;
+        }
+        q.live = false;
+        continue;
+      }
+      go.push_back(i);
+    }
+    HY_TRY(residual(redo));
+    for (int i : redo) {
+      State& q = st[i];
+      if (q.rel <= rtol) {
+        q.live = false;
+        continue;
+      }
+      q.stalled = 0;
+      go.push_back(i);
+    }
+    if (go.empty()) continue;
+    std::sort(go.begin(), go.end());
+    std::vector<Mesh*> mm;
+    std::vector<double*> uu, ll;
+    for (int i : go) {
+      st[i].prev = st[i].rel;
+      mm.push_back(ms[i]);
+      uu.push_back(u[i]);
+      ll.push_back(ulo ? ulo[i] : nullptr);
+    }
+    const int k = int(mm.size());
+    if (mode == 2) {
+      if (!first) {
+        std::vector<float*> z(k);
+        for (int j = 0; j < k; ++j) z[j] = mm[j]->solver->lv[l].u32;
+        HY_TRY(zero_g<float>(mm.data(), k, l, z.data(), s));
+      }
+      HY_TRY(vcycle_own<float>(mm.data(), k, l, s, first));
+      HY_TRY(update_g<float>(mm.data(), k, l, uu.data(), ulo ? ll.data() : nullptr, s));
+    } else {
+      if (!first) {
+        std::vector<double*> z(k);
+        for (int j = 0; j < k; ++j) z[j] = mm[j]->solver->lv[l].u64;
+        HY_TRY(zero_g<double>(mm.data(), k, l, z.data(), s));
+      }
+      HY_TRY(vcycle_own<double>(mm.data(), k, l, s, first));
+      HY_TRY(update_g<double>(mm.data(), k, l, uu.data(), ulo ? ll.data() : nullptr, s));
+    }
+    for (int i : go) ++st[i].it;
   }
   if (ulo) {  // u: the float64 rounding of the solution, ulo: the rest
-    k_normalize_two_part<<<grid_for(ns), THREADS, 0, s>>>(u, ulo, ns);
-    HY_TRY(cudaGetLastError());
+    Batch<Normalize> B;
+    for (int i = 0; i < cnt; ++i) {
+      const int64_t ns = n_slots(*ms[i], l);
+      B.add({u[i], ulo[i], ns}, grid_for(ns));
+    }
+    HY_TRY(B.launch(s));
   }
-  *iters = it;
-  *relres = rel;
-  ++sv.solves;
+  for (int i = 0; i < cnt; ++i) {
+    iters[i] = st[i].it;
+    relres[i] = st[i].rel;
+    ++ms[i]->solver->solves;
+  }
   return cudaSuccess;
+}
+
+cudaError_t mg_solve(Mesh& m, int l, int mode, const double* b, double* u, double* ulo, double rtol,
+                     int max_iter, cudaStream_t s, int* iters, double* relres) {
+  Mesh* mp = &m;
+  return mg_solve_group(&mp, 1, l, mode, &b, &u, ulo ? &ulo : nullptr, rtol, max_iter, s, iters, relres);
 }
 
 cudaError_t mg_diag_setup(const Mesh& m, int l, MgLevel& g, cudaStream_t s) {

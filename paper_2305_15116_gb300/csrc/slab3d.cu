@@ -28,6 +28,7 @@
 
 #include "arith.cuh"
 #include "fallback.cuh"
+#include "group.cuh"
 #include "hyteg_internal.h"
 
 namespace hyteg {
@@ -139,11 +140,12 @@ __device__ __forceinline__ int tri_row(int q, int K) {
 
 constexpr int NRING = 4;  // slices z-1, z, z+1 being read, z+2 being filled
 
+// The work of one CTA: work item `it` = (macro, z0, z1) of a mesh whose
+// vectors are x and y.
 template <class P>
-__global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(const typename P::T* __restrict__ x,
-                                                         typename P::T* __restrict__ y,
-                                                         const int4* __restrict__ items, int n, int64_t S,
-                                                         int buf_elems, int guard, StencilPtr st) {
+__device__ __forceinline__ void slab3d_item(const typename P::T* __restrict__ x, typename P::T* __restrict__ y,
+                                            const int4 it, int n, int64_t S, int buf_elems, int guard,
+                                            const StencilPtr st) {
   using SS = Stage<P>;
   using SV = typename SS::S;
   using T = typename P::T;
@@ -161,7 +163,6 @@ __global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(cons
   // offset of element 0 of slice z's buffer inside `ring`
   auto roff = [&](int z) -> int { return (z & (NRING - 1)) * stride + guard; };
 
-  const int4 it = items[blockIdx.x];
   const int m = it.x, z0 = it.y, z1 = it.z;
   const T* __restrict__ xm = x + (int64_t)m * S;
   T* __restrict__ ym = y + (int64_t)m * S;
@@ -325,6 +326,46 @@ __global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(cons
   cp_async_wait_all();
 }
 
+template <class P>
+__global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(const typename P::T* __restrict__ x,
+                                                         typename P::T* __restrict__ y,
+                                                         const int4* __restrict__ items, int n, int64_t S,
+                                                         int buf_elems, int guard, StencilPtr st) {
+  slab3d_item<P>(x, y, items[blockIdx.x], n, S, buf_elems, guard, st);
+}
+
+// Several meshes in one launch: each owns a consecutive range of the blocks
+// (one per work item, as in its own launch) and a block finds its mesh by
+// binary search over the ranges.  The meshes share n (the shared-memory
+// layout).
+struct SlabDesc {
+  const void* x;
+  void* y;
+  const int4* items;
+  int64_t S;
+  StencilPtr st;
+  int block_begin;
+};
+struct SlabGroup {
+  SlabDesc d[kGroupMax];
+  int count, n, buf_elems, guard;
+};
+
+template <class P>
+__global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d_group(const __grid_constant__ SlabGroup g) {
+  int lo = 0, hi = g.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.d[mid].block_begin <= (int)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const SlabDesc& d = g.d[lo];
+  slab3d_item<P>(static_cast<const typename P::T*>(d.x), static_cast<typename P::T*>(d.y),
+                 d.items[(int)blockIdx.x - d.block_begin], g.n, d.S, g.buf_elems, g.guard, d.st);
+}
+
 // The shared-memory limit is a property of the kernel shared by every thread
 // and stream of the process: raise it once, to what the largest slab level
 // (n = 64) needs, so that concurrent launches for different levels never see
@@ -340,6 +381,8 @@ cudaError_t ensure_attr() {
     const size_t wb = ((size_t)NCLS3 * NW3 * sizeof(typename WStore<P>::S) + 15) / 16 * 16;
     const size_t rb = ((size_t)NRING * (bmax + 2 * (nmax + 3)) * sizeof(SV) + 15) / 16 * 16;
     attr = cudaFuncSetAttribute(k_slab3d<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wb + rb));
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(k_slab3d_group<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wb + rb));
   });
   return attr;
 }
@@ -361,6 +404,48 @@ cudaError_t launch_items(const LevelDev& L, const int4* items, int n_items, cons
   k_slab3d<P><<<n_items, SLAB_THREADS, bytes, s>>>((const typename P::T*)x, (typename P::T*)y, items, n,
                                                   L.slots_per_macro, buf, guard, st);
   return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_group_t(const Mesh* const* ms, const int* levels, const void* const* xs, void* const* ys,
+                           int count, int dt, cudaStream_t s) {
+  using SV = typename Stage<P>::S;
+  const int n = ms[0]->levels[levels[0]].n;
+  if (n > 64) return cudaErrorInvalidValue;
+  const int buf = (n + 1) * (n + 2) / 2;
+  const int guard = n + 3;
+  const size_t w_bytes = ((size_t)NCLS3 * NW3 * sizeof(typename WStore<P>::S) + 15) / 16 * 16;
+  const size_t ring_bytes = ((size_t)NRING * (buf + 2 * guard) * sizeof(SV) + 15) / 16 * 16;
+  const cudaError_t attr = ensure_attr<P>();
+  if (attr != cudaSuccess) return attr;
+  SlabGroup g;
+  g.n = n;
+  g.buf_elems = buf;
+  g.guard = guard;
+  for (int i0 = 0; i0 < count;) {
+    g.count = 0;
+    int blocks = 0;
+    int i = i0;
+    for (; i < count && g.count < kGroupMax; ++i) {
+      const LevelDev& L = ms[i]->levels[levels[i]];
+      if (L.n != n || L.n_slabs == 0) return cudaErrorInvalidValue;
+      const bool tuned = L.slabs_dt[dt] != nullptr;
+      const int n_items = tuned ? L.n_slabs_dt[dt] : L.n_slabs;
+      SlabDesc& d = g.d[g.count++];
+      d.x = xs[i];
+      d.y = ys[i];
+      d.items = tuned ? L.slabs_dt[dt] : L.slabs;
+      d.S = L.slots_per_macro;
+      d.st = StencilPtr{L.st64, L.st32, L.st_hi, L.st_lo};
+      d.block_begin = blocks;
+      blocks += n_items;
+    }
+    i0 = i;
+    k_slab3d_group<P><<<blocks, SLAB_THREADS, w_bytes + ring_bytes, s>>>(g);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // the level's work list for element type dt (the autotuned one when present)
@@ -386,6 +471,17 @@ cudaError_t launch_slab3d_items(int dtype, const LevelDev& L, const int4* items,
     case 1: return launch_items<ArF64FF>(L, items, n_items, x, y, s);
     case 2: return launch_items<ArF32>(L, items, n_items, x, y, s);
     case 3: return launch_items<ArF64Native>(L, items, n_items, x, y, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_slab3d_group(int dtype, const Mesh* const* ms, const int* levels, const void* const* xs,
+                                void* const* ys, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  switch (dtype) {
+    case 1: return launch_group_t<ArF64FF>(ms, levels, xs, ys, count, 1, s);
+    case 2: return launch_group_t<ArF32>(ms, levels, xs, ys, count, 2, s);
+    case 3: return launch_group_t<ArF64Native>(ms, levels, xs, ys, count, 3, s);
     default: return cudaErrorInvalidValue;
   }
 }

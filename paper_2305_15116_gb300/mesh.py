@@ -290,3 +290,31 @@ def apply_batch(meshes, levels, xs, ys, ieee: bool = False, stream=None):
             "hyteg_apply_batch")
     return ys
 
+
+
+def solve_two_part_group(meshes, level: int, bs, us, u_los, mode: int = SOLVE_MIXED, rtol: float = 1e-10,
+                         max_iter: int = 100, stream=None):
+    """Solve A_i (u_i + u_lo_i) = b_i for several meshes at one level in
+    lockstep (hyteg_solve_two_part_group): every solve step is one launch for
+    all problems still iterating.  bs, us, u_los: float64 CUDA tensors in the
+    slot layout of each mesh.  Returns [(iterations, relative residual)]."""
+    n = len(meshes)
+    if not (len(bs) == len(us) == len(u_los) == n):
+        raise ValueError("meshes, bs, us and u_los must have the same length")
+    if n == 0:
+        return []
+    for M, b, u, lo in zip(meshes, bs, us, u_los):
+        ns, _ = M.num_slots(level)
+        for v in (b, u, lo):
+            if not v.is_cuda or v.dtype.itemsize != 8 or not v.is_contiguous() or v.numel() != ns:
+                raise ValueError(f"vectors must be contiguous float64 CUDA tensors of {ns} elements")
+    hs = (ctypes.c_void_p * n)(*[M._h.value if isinstance(M._h, ctypes.c_void_p) else M._h for M in meshes])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    up = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+    lp = (ctypes.c_void_p * n)(*[u.data_ptr() for u in u_los])
+    it = (ctypes.c_int * n)()
+    rel = (ctypes.c_double * n)()
+    C.check(C.lib.hyteg_solve_two_part_group(hs, n, level, mode, bp, up, lp, rtol, max_iter,
+                                             ctypes.c_void_p(_stream_ptr(stream)), it, rel),
+            "hyteg_solve_two_part_group")
+    return [(it[i], rel[i]) for i in range(n)]
