@@ -489,7 +489,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
     pending = collections.deque(reqs)
     retry = collections.deque()
     outstanding = {}
-    lat, run, queue_s, iters, rels, ngs, setup, missed = [], [], [], [], [], [], [], []
+    lat, run, queue_s, iters, rels, ngs, setup, missed, groups = [], [], [], [], [], [], [], [], []
     hits = failed = eagain = 0
     errors = collections.Counter()
     t0 = time.perf_counter()
@@ -533,6 +533,7 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
             queue_s.append(r.queue_s)
             iters.append(r.iters)
             rels.append(r.relres)
+            groups.append(r.group)
             if r.relres > rtol:
                 missed.append((q.dim, list(q.shape), q.level, r.iters, r.relres))
             ngs.append(r.n_global)
@@ -549,7 +550,8 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
                      f"levels 3..6; lumped-mass RHS with 0.1 N(0,1) Philox noise per request seed); rtol {rtol}, "
                      + ("fp32 V(3,3) cycles in float64 refinement" if mode == H.SOLVE_MIXED else
                         "float64 V(3,3) cycles") + "; every solution copied to host memory; "
-                     f"{workers} worker streams, {cap_bytes >> 30} GiB device arena"),
+                     f"{workers} worker streams, each solving up to 8 queued requests of one class (dimension, "
+                     f"level) as one group; {cap_bytes >> 30} GiB device arena"),
         "offered_rate_per_s": rate,
         "solves_per_s": len(lat) / span, "gdofs_solved_per_s": float(np.sum(ngs)) / span / 1e9,
         "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
@@ -562,6 +564,9 @@ def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=Non
         "reached_rtol": bool(rels and max(rels) <= rtol),
         "reached_rtol_share": float(np.mean(np.asarray(rels) <= rtol)) if rels else None,
         "not_reached_rtol": [dict(zip(("dim", "shape", "level", "iters", "relres"), m)) for m in missed[:8]],
+        "group_size_mean": float(np.mean(groups)) if groups else None,
+        "grouped_share": float(np.mean(np.asarray(groups) > 1)) if groups else None,
+        "group_solves": st["group_solves"],
     }
 
 

@@ -400,7 +400,12 @@ int hyteg_to_global(const hyteg_mesh* mesh, int level, const double* v, double* 
  * solver above for many independent problems at once.
  *  - Worker threads, each with its own CUDA stream, take requests in arrival
  *    order as soon as they are free (continuous batching: a new request starts
- *    while others are mid-solve, and their kernels share the GPU).
+ *    while others are mid-solve, and their kernels share the GPU).  A worker
+ *    takes the oldest queued request together with up to 7 more queued
+ *    requests of the same class (dimension, level, mode, rtol and max_iter;
+ *    3D up to level 6) and solves them as one group
+ *    (hyteg_solve_two_part_group): one launch per solve step for all of
+ *    them.
  *  - Device memory comes from one arena of mem_cap bytes reserved at
  *    creation; a request is admitted only while the estimated device bytes of
  *    the requests in flight plus its own stay within the cap (else
@@ -409,7 +414,8 @@ int hyteg_to_global(const hyteg_mesh* mesh, int level, const double* v, double* 
  *    level; idle cached meshes are dropped, least recently used first, when a
  *    new one needs the room.
  *  - Every request's result is independent of the others in flight: the same
- *    request gives bitwise the same solution alone or in a batch. */
+ *    request gives bitwise the same solution alone, in a batch or in a
+ *    group. */
 typedef struct hyteg_server hyteg_server;  /* opaque, owned by the library */
 
 typedef struct hyteg_request {
@@ -447,6 +453,7 @@ typedef struct hyteg_result {
   double run_s;     /* seconds from the start to the end of the work */
   int64_t n_global; /* DoFs of the request's problem */
   double setup_s;   /* part of run_s spent building the refined mesh (0 on a cache hit) */
+  int group;        /* requests solved together with this one in one group solve (1: alone) */
 } hyteg_result;
 
 /* Creates a server on `device` with a device arena of mem_cap bytes and
@@ -477,6 +484,8 @@ typedef struct hyteg_server_stats {
   int64_t cached_meshes, cache_hits, evictions;
   size_t reserved_bytes;  /* estimated bytes of the requests in flight */
   size_t arena_used;      /* bytes of the arena in use (requests and cache) */
+  int64_t group_solves;   /* group solves of two or more requests */
+  int64_t grouped;        /* requests solved in such groups */
 } hyteg_server_stats;
 
 int hyteg_server_stats_get(hyteg_server* server, hyteg_server_stats* out);

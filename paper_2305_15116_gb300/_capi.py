@@ -114,14 +114,16 @@ class Result(ctypes.Structure):
     """struct hyteg_result"""
     _fields_ = [("status", ctypes.c_int), ("error", ctypes.c_int), ("iters", ctypes.c_int),
                 ("cache_hit", ctypes.c_int), ("relres", ctypes.c_double), ("queue_s", ctypes.c_double),
-                ("run_s", ctypes.c_double), ("n_global", ctypes.c_int64), ("setup_s", ctypes.c_double)]
+                ("run_s", ctypes.c_double), ("n_global", ctypes.c_int64), ("setup_s", ctypes.c_double),
+                ("group", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
     """struct hyteg_server_stats"""
     _fields_ = [("submitted", ctypes.c_int64), ("done", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("in_flight", ctypes.c_int64), ("cached_meshes", ctypes.c_int64), ("cache_hits", ctypes.c_int64),
-                ("evictions", ctypes.c_int64), ("reserved_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t)]
+                ("evictions", ctypes.c_int64), ("reserved_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
+                ("group_solves", ctypes.c_int64), ("grouped", ctypes.c_int64)]
 
 
 lib.hyteg_server_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]

@@ -2,7 +2,10 @@
 //
 // Worker threads with one CUDA stream each take requests in arrival order as
 // soon as they are free, so a new request starts while others are mid-solve
-// (continuous batching; their kernels share the GPU).  All device memory of
+// (continuous batching; their kernels share the GPU).  A worker takes the
+// oldest queued request together with queued requests of the same class
+// (dimension, level, mode, rtol, max_iter) and solves them as one group: one
+// launch per solve step for all of them (hyteg_solve_two_part_group).  All device memory of
 // the requests and of the mesh cache comes from one arena reserved at
 // creation (devmem.cpp): admission keeps the estimated bytes of the requests
 // in flight within the cap, refined meshes stay cached for later requests on
@@ -95,6 +98,17 @@ std::string make_key(const Req& r) {
   return k;
 }
 
+// Requests solved together: at most kMaxGroup of one class.  3D levels above
+// 6 (the row kernel) have no group launch and are solved alone.
+constexpr int kMaxGroup = 8;
+bool same_class(const Req& a, const Req& b) {
+  return a.dim == b.dim && a.level == b.level && a.mode == b.mode && a.rtol == b.rtol && a.max_iter == b.max_iter;
+}
+bool groupable(const Req& r) { return r.dim == 2 || r.level <= 6; }
+
+// acquire() of a group member after the first: no room without waiting
+constexpr int kWouldWait = 1000;
+
 }  // namespace
 
 struct hyteg_server {
@@ -115,15 +129,25 @@ struct hyteg_server {
 
   std::list<Entry*> idle;  // idle cached entries, most recently used first
   std::vector<std::unique_ptr<Entry>> entries;
-  int64_t submitted = 0, done = 0, failed = 0, hits = 0, evictions = 0;
+  int64_t submitted = 0, done = 0, failed = 0, hits = 0, evictions = 0, group_solves = 0, grouped = 0;
 
   void worker(int w);
-  int run(Req& r, cudaStream_t s, bool* hit, hyteg_result* res, std::string* msg);
-  Entry* acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::string* msg);
+  void run_group(std::vector<Req*>& grp, cudaStream_t s);
+  Entry* acquire(Req& r, cudaStream_t s, bool may_wait, bool* hit, int* err, std::string* msg);
   void release(Entry* e);
+  void drop(Entry* e);  // destroys an entry whose last use failed
+  void finish(Req* r, int rc, const hyteg_result& res, const std::string& msg);
+  void requeue(Req* r);
   bool evict_one();  // caller holds mu
+  bool others_hold_memory() const;  // caller holds mu
   void destroy_entry(Entry* e);
 };
+
+bool hyteg_server::others_hold_memory() const {
+  for (const auto& e : entries)
+    if (e->busy) return true;
+  return false;
+}
 
 void hyteg_server::destroy_entry(Entry* e) {
   if (e->mesh) {
@@ -154,7 +178,7 @@ bool hyteg_server::evict_one() {
   return true;
 }
 
-Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::string* msg) {
+Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool may_wait, bool* hit, int* err, std::string* msg) {
   {
     std::lock_guard<std::mutex> lk(mu);
     for (auto it = idle.begin(); it != idle.end(); ++it)
@@ -181,8 +205,12 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
         if (region || !evict_one()) break;
       }
       if (!region) {
-        // only another request in flight can hand memory back: with none, fail now
-        const bool others = submitted - done - failed > 1;
+        if (!may_wait) {
+          *err = kWouldWait;
+          return nullptr;
+        }
+        // only a request holding memory can hand it back: with none, fail now
+        const bool others = others_hold_memory();
         if (!others || Clock::now() > deadline ||
             cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
           *err = HYTEG_ENOMEM;
@@ -242,7 +270,11 @@ Entry* hyteg_server::acquire(Req& r, cudaStream_t s, bool* hit, int* err, std::s
     // the mesh outgrew its region and the arena: drop an idle mesh and retry
     std::unique_lock<std::mutex> lk(mu);
     if (evict_one()) continue;
-    const bool others = submitted - done - failed > 1;
+    if (!may_wait) {
+      *err = kWouldWait;
+      return nullptr;
+    }
+    const bool others = others_hold_memory();
     if (!others || Clock::now() > deadline || cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
       *err = HYTEG_ENOMEM;
       *msg = "device arena exhausted: " + why;
@@ -261,103 +293,194 @@ void hyteg_server::release(Entry* e) {
   cv_done.notify_all();
 }
 
-int hyteg_server::run(Req& r, cudaStream_t s, bool* hit, hyteg_result* res, std::string* msg) {
-  int err = HYTEG_OK;
-  const auto t0 = Clock::now();
-  Entry* e = acquire(r, s, hit, &err, msg);
-  res->setup_s = seconds_since(t0, Clock::now());
-  if (!e) return err;
-  hyteg::Mesh& m = e->mesh->m;
-  m.mem.stream = s;
-  const int64_t ns = slots_of(r.dim, r.level, m.n_cells);
-  res->n_global = e->n_global;
+void hyteg_server::drop(Entry* e) {
+  std::lock_guard<std::mutex> lk(mu);
+  destroy_entry(e);
+  for (auto it = entries.begin(); it != entries.end(); ++it)
+    if (it->get() == e) {
+      entries.erase(it);
+      break;
+    }
+  cv_done.notify_all();
+}
+
+void hyteg_server::finish(Req* r, int rc, const hyteg_result& res, const std::string& msg) {
+  std::lock_guard<std::mutex> lk(mu);
+  r->res.iters = res.iters;
+  r->res.relres = res.relres;
+  r->res.n_global = res.n_global;
+  r->res.setup_s = res.setup_s;
+  r->res.group = res.group;
+  r->msg = msg;
+  r->res.run_s = seconds_since(r->t_start, Clock::now());
+  r->res.cache_hit = res.cache_hit;
+  r->res.error = rc;
+  r->res.status = rc == HYTEG_OK ? HYTEG_REQ_DONE : HYTEG_REQ_FAILED;
+  reserved -= r->est;
+  if (rc == HYTEG_OK) {
+    ++done;
+    hits += res.cache_hit ? 1 : 0;
+    grouped += res.group > 1 ? 1 : 0;
+  } else {
+    ++failed;
+  }
+  cv_done.notify_all();
+}
+
+void hyteg_server::requeue(Req* r) {
+  std::lock_guard<std::mutex> lk(mu);
+  r->res.status = HYTEG_REQ_QUEUED;
+  queue.push_front(r);
+  cv_work.notify_one();
+}
+
+// One group of requests of one class on stream s: the meshes (cached or
+// built; a member after the first that finds no room without waiting goes
+// back to the queue), the right-hand sides, one solve for all (alone: the
+// single solve with its captured V-cycles), the results to host memory.
+void hyteg_server::run_group(std::vector<Req*>& grp, cudaStream_t s) {
+  struct Member {
+    Req* r;
+    Entry* e;
+    hyteg_result res;
+    int rc;
+    std::string msg;
+  };
+  std::vector<Member> ms;
+  for (size_t k = 0; k < grp.size(); ++k) {
+    Req* r = grp[k];
+    bool hit = false;
+    int err = HYTEG_OK;
+    std::string msg;
+    const auto t0 = Clock::now();
+    Entry* e = acquire(*r, s, k == 0, &hit, &err, &msg);
+    hyteg_result res{};
+    res.setup_s = seconds_since(t0, Clock::now());
+    res.cache_hit = hit ? 1 : 0;
+    res.group = 1;
+    if (!e) {
+      if (err == kWouldWait)
+        requeue(r);
+      else
+        finish(r, err, res, msg);
+      continue;
+    }
+    e->mesh->m.mem.stream = s;
+    res.n_global = e->n_global;
+    ms.push_back({r, e, res, HYTEG_OK, std::string()});
+  }
+  if (ms.empty()) return;
+  const int cnt = int(ms.size());
   int rc = HYTEG_OK;
-  cudaError_t ce = hyteg::poisson_rhs(m, r.level, r.seed, r.noise, e->b, s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(e->u, 0, size_t(ns) * 8, s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(e->ulo, 0, size_t(ns) * 8, s);
-  if (ce != cudaSuccess) {
-    rc = HYTEG_ECUDA;
-    *msg = std::string("right-hand side: ") + cudaGetErrorString(ce);
+  std::string msg;
+  for (Member& q : ms) {
+    const Req& r = *q.r;
+    hyteg::Mesh& m = q.e->mesh->m;
+    const int64_t ns = slots_of(r.dim, r.level, m.n_cells);
+    cudaError_t ce = hyteg::poisson_rhs(m, r.level, r.seed, r.noise, q.e->b, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(q.e->u, 0, size_t(ns) * 8, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(q.e->ulo, 0, size_t(ns) * 8, s);
+    if (ce != cudaSuccess) {
+      rc = HYTEG_ECUDA;
+      msg = std::string("right-hand side: ") + cudaGetErrorString(ce);
+      break;
+    }
   }
   if (rc == HYTEG_OK) {
     // the iterate of two float64 parts reaches rtol below the floor of a
     // float64 solution's rounding (which grows like h^-2)
-    rc = hyteg_solve_two_part(e->mesh, r.level, r.mode, e->b, e->u, e->ulo, r.rtol, r.max_iter, s, &res->iters,
-                              &res->relres);
-    if (rc != HYTEG_OK) *msg = hyteg_last_error();
+    const Req& r0 = *ms[0].r;
+    if (cnt == 1) {
+      Member& q = ms[0];
+      rc = hyteg_solve_two_part(q.e->mesh, r0.level, r0.mode, q.e->b, q.e->u, q.e->ulo, r0.rtol, r0.max_iter, s,
+                                &q.res.iters, &q.res.relres);
+    } else {
+      std::vector<hyteg_mesh*> hm(cnt);
+      std::vector<const double*> hb(cnt);
+      std::vector<double*> hu(cnt), hl(cnt);
+      std::vector<int> it(cnt);
+      std::vector<double> rel(cnt);
+      for (int i = 0; i < cnt; ++i) {
+        hm[i] = ms[i].e->mesh;
+        hb[i] = ms[i].e->b;
+        hu[i] = ms[i].e->u;
+        hl[i] = ms[i].e->ulo;
+      }
+      rc = hyteg_solve_two_part_group(hm.data(), cnt, r0.level, r0.mode, hb.data(), hu.data(), hl.data(), r0.rtol,
+                                      r0.max_iter, s, it.data(), rel.data());
+      for (int i = 0; i < cnt; ++i) {
+        ms[i].res.iters = it[i];
+        ms[i].res.relres = rel[i];
+        ms[i].res.group = cnt;
+      }
+    }
+    if (rc != HYTEG_OK) msg = hyteg_last_error();
   }
-  for (int k = 0; k < 3 && rc == HYTEG_OK; ++k) {
-    double* host = k == 0 ? r.u_out : k == 1 ? r.b_out : r.u_lo_out;
-    if (!host) continue;
-    ce = hyteg::to_global(m, r.level, k == 0 ? e->u : k == 1 ? e->b : e->ulo, e->glob, s);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpyAsync(host, e->glob, size_t(e->n_global) * 8, cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    if (ce != cudaSuccess) {
-      rc = HYTEG_ECUDA;
-      *msg = std::string("result copy: ") + cudaGetErrorString(ce);
+  for (Member& q : ms) {
+    q.rc = rc;
+    q.msg = msg;
+    const Req& r = *q.r;
+    hyteg::Mesh& m = q.e->mesh->m;
+    for (int k = 0; k < 3 && q.rc == HYTEG_OK; ++k) {
+      double* host = k == 0 ? r.u_out : k == 1 ? r.b_out : r.u_lo_out;
+      if (!host) continue;
+      cudaError_t ce = hyteg::to_global(m, r.level, k == 0 ? q.e->u : k == 1 ? q.e->b : q.e->ulo, q.e->glob, s);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(host, q.e->glob, size_t(q.e->n_global) * 8, cudaMemcpyDeviceToHost, s);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      if (ce != cudaSuccess) {
+        q.rc = HYTEG_ECUDA;
+        q.msg = std::string("result copy: ") + cudaGetErrorString(ce);
+      }
     }
   }
-  ce = cudaStreamSynchronize(s);
-  if (ce != cudaSuccess && rc == HYTEG_OK) {
-    rc = HYTEG_ECUDA;
-    *msg = cudaGetErrorString(ce);
-  }
-  if (rc == HYTEG_ECUDA) {
-    // leave a mesh whose last use failed out of the cache
+  const cudaError_t ce = cudaStreamSynchronize(s);
+  if (cnt > 1 && rc == HYTEG_OK) {
     std::lock_guard<std::mutex> lk(mu);
-    destroy_entry(e);
-    for (auto it = entries.begin(); it != entries.end(); ++it)
-      if (it->get() == e) {
-        entries.erase(it);
-        break;
-      }
-    cv_done.notify_all();
-  } else {
-    release(e);
+    ++group_solves;
   }
-  return rc;
+  for (Member& q : ms) {
+    if (ce != cudaSuccess && q.rc == HYTEG_OK) {
+      q.rc = HYTEG_ECUDA;
+      q.msg = cudaGetErrorString(ce);
+    }
+    if (q.rc == HYTEG_ECUDA)
+      drop(q.e);  // leave a mesh whose last use failed out of the cache
+    else
+      release(q.e);
+    finish(q.r, q.rc, q.res, q.msg);
+  }
 }
 
 void hyteg_server::worker(int w) {
   cudaSetDevice(device);
   cudaStream_t s = streams[w];
   for (;;) {
-    Req* r = nullptr;
+    std::vector<Req*> grp;
     {
       std::unique_lock<std::mutex> lk(mu);
       cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
       if (queue.empty()) return;  // stopping
-      r = queue.front();
+      grp.push_back(queue.front());
       queue.pop_front();
-      r->res.status = HYTEG_REQ_RUNNING;
-      r->t_start = Clock::now();
-      r->res.queue_s = seconds_since(r->t_submit, r->t_start);
-    }
-    bool hit = false;
-    hyteg_result res{};
-    std::string msg;
-    const int rc = run(*r, s, &hit, &res, &msg);
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      r->res.iters = res.iters;
-      r->res.relres = res.relres;
-      r->res.n_global = res.n_global;
-      r->res.setup_s = res.setup_s;
-      r->msg = msg;
-      r->res.run_s = seconds_since(r->t_start, Clock::now());
-      r->res.cache_hit = hit ? 1 : 0;
-      r->res.error = rc;
-      r->res.status = rc == HYTEG_OK ? HYTEG_REQ_DONE : HYTEG_REQ_FAILED;
-      reserved -= r->est;
-      if (rc == HYTEG_OK) {
-        ++done;
-        hits += hit ? 1 : 0;
-      } else {
-        ++failed;
+      // the queued requests of the same class join it, oldest first
+      if (groupable(*grp[0]))
+        for (auto it = queue.begin(); it != queue.end() && int(grp.size()) < kMaxGroup;) {
+          if (same_class(**it, *grp[0])) {
+            grp.push_back(*it);
+            it = queue.erase(it);
+          } else {
+            ++it;
+          }
+        }
+      const auto now = Clock::now();
+      for (Req* r : grp) {
+        r->res.status = HYTEG_REQ_RUNNING;
+        r->t_start = now;
+        r->res.queue_s = seconds_since(r->t_submit, now);
       }
-      cv_done.notify_all();
     }
+    run_group(grp, s);
   }
 }
 
@@ -499,6 +622,8 @@ int hyteg_server_stats_get(hyteg_server* sv, hyteg_server_stats* out) {
   out->evictions = sv->evictions;
   out->reserved_bytes = sv->reserved;
   out->arena_used = hyteg::arena_used(sv->arena);
+  out->group_solves = sv->group_solves;
+  out->grouped = sv->grouped;
   return HYTEG_OK;
 }
 

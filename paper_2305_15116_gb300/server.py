@@ -22,6 +22,7 @@ class Result:
     n_global: int
     setup_s: float = 0.0
     message: str = ""
+    group: int = 1  # requests solved together in one group solve
 
     @property
     def finished(self) -> bool:
@@ -31,7 +32,7 @@ class Result:
 def _result(r: C.Result) -> Result:
     msg = C.lib.hyteg_last_error().decode(errors="replace") if r.status == REQ_FAILED else ""
     return Result(r.status, r.error, r.iters, bool(r.cache_hit), r.relres, r.queue_s, r.run_s, r.n_global,
-                  r.setup_s, msg)
+                  r.setup_s, msg, r.group)
 
 
 class Server:

@@ -212,3 +212,53 @@ def test_server_allocation_failure_is_reported(cuda):
         assert r2.status == H.REQ_DONE and r2.relres <= 1e-9
         s = sv.stats()
         assert s["failed"] == 1 and s["done"] == 1
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_server_groups_requests_of_one_class(cuda, dim):
+    """One worker busy with a long request while five requests of one class
+    queue up: the worker then solves them as one group (one launch per solve
+    step for all), and every solution is bitwise that of the request solved
+    alone."""
+    H = _lib()
+    if dim == 2:
+        blocker = (rect_mesh(4, 4, 0.15, 9), 9, 30)
+        same = [(rect_mesh(2, 2, 0.15, k), 6, 31 + k) for k in range(3)] + \
+               [(rect_mesh(3, 2, 0.15, 5), 6, 35), (rect_mesh(2, 2, 0.15, 0), 6, 36)]
+    else:
+        blocker = (box_kuhn_mesh(2, 2, 2, 0.1, 9), 6, 30)
+        same = [(box_kuhn_mesh(1, 1, 1, 0.1, k), 4, 31 + k) for k in range(3)] + \
+               [(box_kuhn_mesh(2, 1, 1, 0.1, 5), 4, 35), (box_kuhn_mesh(1, 1, 1, 0.1, 0), 4, 36)]
+
+    def n_of(coarse, L):
+        return oracle.RefinedMesh(coarse.coords, coarse.cells, L).n_global
+
+    alone = []
+    with _server(workers=1) as sv:
+        for coarse, L, seed in same:
+            u = np.full(n_of(coarse, L), np.nan)
+            lo = np.full_like(u, np.nan)
+            t = sv.submit(coarse.coords, coarse.cells, L, seed, 0.1, rtol=1e-10, u_out=u, u_lo_out=lo)
+            r = sv.wait(t, 300)
+            assert r.status == H.REQ_DONE and r.group == 1
+            alone.append((u, lo, r.iters, r.relres))
+            sv.release(t)
+    with _server(workers=1) as sv:
+        c, L, seed = blocker
+        tb = sv.submit(c.coords, c.cells, L, seed, 0.1, rtol=1e-10)
+        outs = []
+        for coarse, L, seed in same:
+            u = np.full(n_of(coarse, L), np.nan)
+            lo = np.full_like(u, np.nan)
+            outs.append((sv.submit(coarse.coords, coarse.cells, L, seed, 0.1, rtol=1e-10, u_out=u, u_lo_out=lo), u, lo))
+        assert sv.wait(tb, 300).status == H.REQ_DONE
+        groups = []
+        for (t, u, lo), (ua, loa, it, rel) in zip(outs, alone):
+            r = sv.wait(t, 300)
+            assert r.status == H.REQ_DONE
+            groups.append(r.group)
+            assert r.iters == it and r.relres == rel and rel <= 1e-10
+            assert np.array_equal(u, ua) and np.array_equal(lo, loa)
+        st = sv.stats()
+    # the five queued behind the blocker: one group of five
+    assert max(groups) >= 2 and st["group_solves"] >= 1 and st["grouped"] >= 2, (groups, st)
