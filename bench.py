@@ -421,11 +421,13 @@ def solve_workload(device, stream, reps=3, rtol=1e-10):
             M.vcycle(L, b32, u32, stream=stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_vcycles")
         e0.record(stream)
         for _ in range(20):
             M.vcycle(L, b32, u32, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1) / 20
     vb = vcycle_bytes(M, L, 4)
     peak, peak_kind = measured_peaks()
