@@ -184,7 +184,7 @@ cudaError_t tiles2d_autotune(Mesh& m, LevelDev& L) {
       }
       float best_ms = 0.0f;
       for (int c : kCand) {
-        const std::vector<int4> tl = tile_list_2d(L.n, c);
+        const std::vector<int4> tl = tile_list_2d(L.n, c, kTileWidth2);
         int4* d_tiles = nullptr;
         if ((err = dev_alloc(m, (void**)&d_tiles, tl.size() * sizeof(int4))) != cudaSuccess) break;
         err = dev_upload(m, d_tiles, tl.data(), tl.size() * sizeof(int4));
@@ -213,7 +213,7 @@ cudaError_t tiles2d_autotune(Mesh& m, LevelDev& L) {
       std::lock_guard<std::mutex> lk(mu);
       cache[key] = best;
     }
-    const std::vector<int4> tl = tile_list_2d(L.n, best);
+    const std::vector<int4> tl = tile_list_2d(L.n, best, kTileWidth2);
     if ((err = dev_alloc(m, (void**)&L.tiles_dt[dt], tl.size() * sizeof(int4))) != cudaSuccess) break;
     if ((err = dev_upload(m, L.tiles_dt[dt], tl.data(), tl.size() * sizeof(int4))) != cudaSuccess) break;
     L.n_tiles_dt[dt] = int(tl.size());

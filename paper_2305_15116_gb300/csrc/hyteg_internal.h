@@ -246,7 +246,11 @@ cudaError_t slab3d_autotune(Mesh& m, LevelDev& L);
 // The 2D macro-interior tiles of one macro (same list for every macro):
 // strips of 62 columns from x = 1, rows cut into chunks of `rows`, ordered
 // row chunk by row chunk.
-std::vector<int4> tile_list_2d(int n, int rows);
+// 2D macro-interior tiles: strips of `width` written columns from x = 1
+// (kTileWidth2: 32 lanes x two columns, the outermost two halo), rows chunked
+// by `rows` from y = 1
+constexpr int kTileWidth2 = 62;
+std::vector<int4> tile_list_2d(int n, int rows, int width);
 cudaError_t tiles2d_autotune(Mesh& m, LevelDev& L);
 // the 2D apply over an explicit tile list (the autotuner's candidates)
 cudaError_t launch_apply2d_tiles(int dtype, const Mesh& m, const LevelDev& L, const int4* tiles, int n_tiles,

@@ -107,16 +107,41 @@ struct ReduceFlat {
       if (k >= p.n_rest) return;
       const int item = p.list[k];
       const int4 it = p.items[item];
-      const int a = it.z + (int)(threadIdx.x & 127);
-      if (a >= it.w) return;
+      const int t = (int)(threadIdx.x & 127);
       const Prim pr = p.prims[it.x];
       if (!pr.boundary && pr.inc_count == 1) return;
+      if (pr.type == 0 && !pr.boundary && pr.inc_count <= 32) {
+        // a coarse vertex inside the domain: lane i of the item's first warp
+        // takes copy i, and every lane adds the copies in ascending order
+        // (the order of the loop below) through shuffles
+        if (t >= 32) return;
+        const int64_t* sl = p.slots + p.item_base[item];
+        const bool mine = t < pr.inc_count;
+        const int64_t s = mine ? __ldg(sl + t) : 0;
+        const T v = mine ? p.y[s] : T(0);
+        T acc = T(0);
+        for (int i = 0; i < pr.inc_count; ++i) acc += __shfl_sync(0xFFFFFFFFu, v, i);
+        if (mine) p.y[s] = acc;
+        return;
+      }
+      const int a = it.z + t;
+      if (a >= it.w) return;
       const int64_t* sl = p.slots + p.item_base[item] + (int64_t)(a - it.z) * pr.inc_count;
       T acc = T(0);
       if (pr.boundary) {
         acc = __ldg(p.x + __ldg(sl));
       } else {
-        for (int i = 0; i < pr.inc_count; ++i) acc += p.y[__ldg(sl + i)];
+        // the copies' loads four at a time, added in ascending order
+        int i = 0;
+        for (; i + 4 <= pr.inc_count; i += 4) {
+          const int64_t s0 = __ldg(sl + i), s1 = __ldg(sl + i + 1), s2 = __ldg(sl + i + 2), s3 = __ldg(sl + i + 3);
+          const T v0 = p.y[s0], v1 = p.y[s1], v2 = p.y[s2], v3 = p.y[s3];
+          acc += v0;
+          acc += v1;
+          acc += v2;
+          acc += v3;
+        }
+        for (; i < pr.inc_count; ++i) acc += p.y[__ldg(sl + i)];
       }
       for (int i = 0; i < pr.inc_count; ++i) p.y[__ldg(sl + i)] = acc;
       return;
@@ -151,11 +176,29 @@ struct ReduceItems {
   };
   static __device__ __forceinline__ void run(const Prm& p, int block, int) {
     const int4 it = p.items[block];
-    const int a = it.z + threadIdx.x;
-    if (a >= it.w) return;
     const Prim pr = p.prims[it.x];
     if (!pr.boundary && pr.inc_count == 1) return;
     const int n = p.n;
+    if (pr.type == 0 && !pr.boundary && pr.inc_count <= 32) {
+      // a coarse vertex inside the domain: lane i of the first warp takes
+      // copy i, added in ascending copy order through shuffles
+      if (threadIdx.x >= 32) return;
+      const bool mine = (int)threadIdx.x < pr.inc_count;
+      int64_t s = 0;
+      if (mine) {
+        const Inc inc = p.incs[pr.inc_begin + threadIdx.x];
+        int q[3] = {0, 0, 0};
+        if (inc.corner[0] >= 1) q[inc.corner[0] - 1] += n;
+        s = (int64_t)inc.cell * p.S + (DIM == 2 ? tri_slot(n, q[0], q[1]) : tet_slot(n, q[0], q[1], q[2]));
+      }
+      const T v = mine ? p.y[s] : T(0);
+      T acc = T(0);
+      for (int i = 0; i < pr.inc_count; ++i) acc += __shfl_sync(0xFFFFFFFFu, v, i);
+      if (mine) p.y[s] = acc;
+      return;
+    }
+    const int a = it.z + threadIdx.x;
+    if (a >= it.w) return;
     const int b = it.y;
     int wv[3] = {0, 0, 0};
     if (pr.type == 0) {

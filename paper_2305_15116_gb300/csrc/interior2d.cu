@@ -125,11 +125,28 @@ __device__ __forceinline__ float if_w(const StencilPtr& st, int64_t i, float) { 
 __device__ __forceinline__ double if_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float if_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// The partial row of one copy of an interface point: the class stencil of
+// the point (local coordinates q) in the copy's macro.
+template <class T>
+__device__ __forceinline__ T if_partial(const T* __restrict__ x, const Inc& inc, const int q[2], int n, int64_t S,
+                                        const StencilPtr& st) {
+  const int cls = (q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[0] + q[1] == n ? 4 : 0);
+  const int64_t base = (int64_t)inc.cell * S;
+  const int64_t wb = ((int64_t)inc.cell * NCLS2 + cls) * NW2;
+  T part = T(0);
+#pragma unroll
+  for (int k = 0; k < NW2; ++k) {
+    const int dx = c_if_off[k][0], dy = c_if_off[k][1];
+    if (((cls & 1) && dx < 0) || ((cls & 2) && dy < 0) || ((cls & 4) && dx + dy > 0)) continue;
+    part = if_fma(if_w(st, wb + k, T(0)), __ldg(x + base + if_slot(n, q[0] + dx, q[1] + dy)), part);
+  }
+  return part;
+}
+
 template <int MODE, class T>
-__device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __restrict__ y, const int4& it, int a,
-                                              const Prim* __restrict__ prims, const Inc* __restrict__ incs, int n,
-                                              int64_t S, const StencilPtr& st, const ModeArgs& md) {
-  const Prim p = prims[it.x];
+__device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __restrict__ y, const Prim& p, int a,
+                                              const Inc* __restrict__ incs, int n, int64_t S, const StencilPtr& st,
+                                              const ModeArgs& md) {
   const int wv0 = p.type == 0 ? n : n - a, wv1 = p.type == 0 ? 0 : a;  // weights on the canonical vertices
   auto local = [&](const Inc& inc, int q[2]) {
     q[0] = q[1] = 0;
@@ -142,17 +159,7 @@ __device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __rest
       const Inc inc = incs[p.inc_begin + i];
       int q[2];
       local(inc, q);
-      const int cls = (q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[0] + q[1] == n ? 4 : 0);
-      const int64_t base = (int64_t)inc.cell * S;
-      const int64_t wb = ((int64_t)inc.cell * NCLS2 + cls) * NW2;
-      T part = T(0);
-#pragma unroll
-      for (int k = 0; k < NW2; ++k) {
-        const int dx = c_if_off[k][0], dy = c_if_off[k][1];
-        if (((cls & 1) && dx < 0) || ((cls & 2) && dy < 0) || ((cls & 4) && dx + dy > 0)) continue;
-        part = if_fma(if_w(st, wb + k, T(0)), __ldg(x + base + if_slot(n, q[0] + dx, q[1] + dy)), part);
-      }
-      y[base + if_slot(n, q[0], q[1])] = part;
+      y[(int64_t)inc.cell * S + if_slot(n, q[0], q[1])] = if_partial(x, inc, q, n, S, st);
     }
     return;
   }
@@ -165,17 +172,7 @@ __device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __rest
       const Inc inc = incs[p.inc_begin + i];
       int q[2];
       local(inc, q);
-      const int cls = (q[0] == 0 ? 1 : 0) | (q[1] == 0 ? 2 : 0) | (q[0] + q[1] == n ? 4 : 0);
-      const int64_t base = (int64_t)inc.cell * S;
-      const int64_t wb = ((int64_t)inc.cell * NCLS2 + cls) * NW2;
-      T part = T(0);
-#pragma unroll
-      for (int k = 0; k < NW2; ++k) {
-        const int dx = c_if_off[k][0], dy = c_if_off[k][1];
-        if (((cls & 1) && dx < 0) || ((cls & 2) && dy < 0) || ((cls & 4) && dx + dy > 0)) continue;
-        part = if_fma(if_w(st, wb + k, T(0)), __ldg(x + base + if_slot(n, q[0] + dx, q[1] + dy)), part);
-      }
-      acc += part;
+      acc += if_partial(x, inc, q, n, S, st);
     }
   }
   if (MODE == MODE_JACOBI || MODE == MODE_RESIDUAL) {  // copies hold equal u, b and dinv: use the first
@@ -189,6 +186,37 @@ __device__ __forceinline__ void iface2d_point(const T* __restrict__ x, T* __rest
     local(inc, q);
     y[(int64_t)inc.cell * S + if_slot(n, q[0], q[1])] = acc;
   }
+}
+
+// A coarse vertex inside the domain (at most 32 incident macros): its copies'
+// partial rows are independent, so lane i of one warp takes copy i — walked
+// one after another by one thread, the copies' dependent loads were the
+// latency floor of the launch on small levels — and every lane adds the
+// partials in ascending copy order through shuffles, the order of the serial
+// loop, so the result is the same.
+template <int MODE, class T>
+__device__ __forceinline__ void iface2d_vertex(const T* __restrict__ x, T* __restrict__ y, const Prim& p, int lane,
+                                               const Inc* __restrict__ incs, int n, int64_t S, const StencilPtr& st,
+                                               const ModeArgs& md) {
+  const bool mine = lane < p.inc_count;
+  int q[2] = {0, 0};
+  int64_t slot = 0;
+  T part = T(0);
+  if (mine) {
+    const Inc inc = incs[p.inc_begin + lane];
+    if (inc.corner[0] >= 1) q[inc.corner[0] - 1] += n;
+    slot = (int64_t)inc.cell * S + if_slot(n, q[0], q[1]);
+    part = if_partial(x, inc, q, n, S, st);
+  }
+  if (MODE == MODE_PARTIAL) {
+    if (mine) y[slot] = part;
+    return;
+  }
+  T acc = T(0);
+  for (int i = 0; i < p.inc_count; ++i) acc += __shfl_sync(0xFFFFFFFFu, part, i);
+  if (MODE == MODE_JACOBI || MODE == MODE_RESIDUAL)  // copies hold equal u, b and dinv: use the first
+    acc = mode_out<MODE>(acc, x, md, __shfl_sync(0xFFFFFFFFu, slot, 0));
+  if (mine) y[slot] = acc;
 }
 
 // Rows in flight per warp: each lane stages its two columns of the next RING
@@ -229,8 +257,14 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
     const int item = (THR / 128) * block + (int)(threadIdx.x >> 7);
     if (item >= n_items) return;
     const int4 it = items[item];
-    const int a = it.z + (int)(threadIdx.x & 127);
-    if (a < it.w) iface2d_point<MODE, T>(x, y, it, a, prims, incs, n, S, st, md);
+    const int t = (int)(threadIdx.x & 127);
+    const Prim p = prims[it.x];
+    if (p.type == 0 && !p.boundary && p.inc_count <= 32) {
+      if (t < 32) iface2d_vertex<MODE, T>(x, y, p, t, incs, n, S, st, md);  // the item's first warp
+      return;
+    }
+    const int a = it.z + t;
+    if (a < it.w) iface2d_point<MODE, T>(x, y, p, a, incs, n, S, st, md);
     return;
   }
   const int64_t warp = ((int64_t)(block - n_if_blocks) * blockDim.x + threadIdx.x) >> 5;

@@ -335,10 +335,9 @@ void free_level(const Mesh& m, LevelDev& L) {
   L = LevelDev{};
 }
 
-std::vector<int4> tile_list_2d(int n, int rows) {
-  constexpr int TW2 = 62;
+std::vector<int4> tile_list_2d(int n, int rows, int width) {
   std::vector<int4> tl;
-  for (int x0 = 1; x0 <= n - 2; x0 += TW2) {
+  for (int x0 = 1; x0 <= n - 2; x0 += width) {
     const int ymax = n - 1 - x0;
     for (int y0 = 1; y0 <= ymax; y0 += rows) tl.push_back(make_int4(x0, y0, std::min(y0 + rows, ymax + 1), 0));
   }
@@ -473,7 +472,6 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
   // float64 kernels, 16 for fp32 (measured at level 11, 32 macros: float-
   // float flat within 1 % from 16 to 64 rows, fp32 0.117 ms at 64 rows, 0.109
   // at 16 — more, shorter walks balance its 40 resident warps per SM better).
-  constexpr int TW2 = 62;
   int sms = 0;
   if (d == 2 &&
       (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m.device >= 0 ? m.device : 0) != cudaSuccess ||
@@ -481,19 +479,19 @@ std::string build_level(Mesh& m, int level, LevelDev& L) {
     cudaGetLastError();
     sms = 152;
   }
-  auto strips = [&](int th_max) {
+  auto strips = [&](int th_max, int width) {
     std::vector<int4> tl;
     if (d != 2) return tl;
     auto n_warps = [&](int th) {
       int64_t w = 0;
-      for (int x0 = 1; x0 <= n - 2; x0 += TW2) w += (n - 1 - x0 + th - 1) / th;
+      for (int x0 = 1; x0 <= n - 2; x0 += width) w += (n - 1 - x0 + th - 1) / th;
       return w * m.n_cells;
     };
     int th = th_max;
     while (th > 8 && n_warps(th) < 16 * int64_t(sms)) th /= 2;
-    return tile_list_2d(n, th);
+    return tile_list_2d(n, th, width);
   };
-  std::vector<int4> tiles = strips(64), tiles32 = strips(16);
+  std::vector<int4> tiles = strips(64, kTileWidth2), tiles32 = strips(16, kTileWidth2);
   L.n_tiles32 = int(tiles32.size());
   L.n_tiles = int(tiles.size());
 

@@ -311,9 +311,33 @@ struct Restrict {
     const int nc = p.nc;
     if (block < p.n_if_blocks) {
       const int4 it = p.items[block];
+      const Prim pr = p.prims[it.x];
+      if (pr.type == 0 && !pr.boundary && pr.inc_count <= 32) {
+        // a coarse vertex inside the domain: lane i of the first warp takes
+        // copy i, and every lane adds the partials in ascending copy order
+        // (the order of the loop below) through shuffles
+        if (threadIdx.x >= 32) return;
+        const int lane = threadIdx.x;
+        const bool mine = lane < pr.inc_count;
+        int64_t sl = 0;
+        T part = T(0);
+        if (mine) {
+          const Inc inc = p.incs[pr.inc_begin + lane];
+          int q[3] = {0, 0, 0};
+          if (inc.corner[0] >= 1) q[inc.corner[0] - 1] += nc;
+          sl = (int64_t)inc.cell * p.Sc + slotq<DIM>(nc, q);
+          part = restrict_partial<T, DIM>(p.rf, p.multinv, inc.cell, q, nc, p.Sf);
+        }
+        T acc = T(0);
+        for (int i = 0; i < pr.inc_count; ++i) acc += __shfl_sync(0xFFFFFFFFu, part, i);
+        if (mine) {
+          p.bc[sl] = acc;
+          if (p.uc) p.uc[sl] = p.omega * p.dinv[sl] * acc;
+        }
+        return;
+      }
       const int a = it.z + threadIdx.x;
       if (a >= it.w) return;
-      const Prim pr = p.prims[it.x];
       const int b = it.y;
       int wv[3] = {0, 0, 0};
       if (pr.type == 0) {

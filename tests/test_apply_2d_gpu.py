@@ -147,12 +147,12 @@ def test_full_size_sampled(cuda, kind):
     check_close(yg[slots], yref, absrow, kind, "L11 sampled")
 
 
-def _tiles_2d(n, th):
+def _tiles_2d(n, th, width=62):
     """The macro-interior tiles of a level as the library cuts them: strips of
-    62 written columns from x = 1, rows chunked by th from y = 1 (64 for the
-    float64 kernels and 16 for fp32 at the benchmark's level)."""
+    `width` written columns from x = 1 (32 lanes x two columns, the outermost
+    two halo), rows chunked by th from y = 1."""
     out = []
-    for x0 in range(1, n - 1, 62):
+    for x0 in range(1, n - 1, width):
         ymax = n - 1 - x0
         for y0 in range(1, ymax + 1, th):
             out.append((x0, y0, min(y0 + th, ymax + 1)))
@@ -180,10 +180,11 @@ def test_full_size_every_tile_stratified(cuda, kind):
     rows = M.autotune_choice(L, {"f64": H.F64, "f32": H.F32, "f64_ieee": H.F64_IEEE}[kind])
     assert rows in (8, 16, 32, 64)  # the level was autotuned
     pts = set()
-    for i, (x0, y0, y1) in enumerate(_tiles_2d(n, rows)):
+    width = 62
+    for i, (x0, y0, y1) in enumerate(_tiles_2d(n, rows, width)):
         m = i % coarse.n_cells
         for yy in (y0, y1 - 1):
-            for xx in (x0, min(x0 + 61, n - 1 - yy)):
+            for xx in (x0, x0 + 1, min(x0 + width - 1, n - 1 - yy), min(x0 + width - 2, n - 1 - yy)):
                 pts.add(m * S + yy * (n + 2) - yy * (yy + 1) // 2 + xx)
     slots = np.array(sorted(pts))
     rm = oracle.RefinedMesh(coarse.coords, coarse.cells, L)
