@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(128) k_build_iface_slots(int64_t* __restrict__
 template <class T>
 struct ReduceFlat {
   static constexpr int kThreads = 256;
+  static constexpr bool kLateWait = true;  // the items' tables first
   struct Prm {
     const T* x;
     T* y;
@@ -110,6 +111,7 @@ struct ReduceFlat {
       const int t = (int)(threadIdx.x & 127);
       const Prim pr = p.prims[it.x];
       if (!pr.boundary && pr.inc_count == 1) return;
+      pdl_wait();
       if (pr.type == 0 && !pr.boundary && pr.inc_count <= 32) {
         // a coarse vertex inside the domain: lane i of the item's first warp
         // takes copy i, and every lane adds the copies in ascending order
@@ -149,6 +151,7 @@ struct ReduceFlat {
     const int64_t i = (int64_t)(block - p.rest_blocks) * 256 + threadIdx.x;
     if (i >= p.n_pairs) return;
     const longlong2 pr = p.pairs[i];
+    pdl_wait();
     if (pr.y == -2) {
       p.y[pr.x] = __ldg(p.x + pr.x);
     } else {
@@ -165,6 +168,7 @@ struct ReduceFlat {
 template <class T, int DIM>
 struct ReduceItems {
   static constexpr int kThreads = 128;
+  static constexpr bool kLateWait = true;  // the items' tables first
   struct Prm {
     const T* x;
     T* y;
@@ -179,6 +183,7 @@ struct ReduceItems {
     const Prim pr = p.prims[it.x];
     if (!pr.boundary && pr.inc_count == 1) return;
     const int n = p.n;
+    pdl_wait();
     if (pr.type == 0 && !pr.boundary && pr.inc_count <= 32) {
       // a coarse vertex inside the domain: lane i of the first warp takes
       // copy i, added in ascending copy order through shuffles

@@ -24,6 +24,7 @@
 
 #include "arith.cuh"
 #include "fallback.cuh"
+#include "group.cuh"
 #include "hyteg_internal.h"
 
 namespace hyteg {
@@ -259,6 +260,7 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
     const int4 it = items[item];
     const int t = (int)(threadIdx.x & 127);
     const Prim p = prims[it.x];
+    pdl_wait();  // the vectors after the previous kernel in the stream (group.cuh)
     if (p.type == 0 && !p.boundary && p.inc_count <= 32) {
       if (t < 32) iface2d_vertex<MODE, T>(x, y, p, t, incs, n, S, st, md);  // the item's first warp
       return;
@@ -286,6 +288,7 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
   const int64_t wb = m * (int64_t)(NCLS2 * NW2);  // class 0: the full interior stencil
   const typename P::W wSE = P::weight(st, wb + 1), wC = P::weight(st, wb + 3), wE = P::weight(st, wb + 4),
                       wN = P::weight(st, wb + 6);
+  pdl_wait();  // the vectors after the previous kernel in the stream (group.cuh)
 
   // rows t.y - 1 .. t.z are read, rows t.y .. t.z - 1 written
   const int steps = t.z - t.y + 2;
@@ -399,6 +402,7 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename
   constexpr bool SWEEP = MODE == MODE_JACOBI || MODE == MODE_RESIDUAL;
   __shared__ T ring_all[THR / 32][RING][32][2];
   __shared__ T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
+  pdl_trigger();
   apply2d_block<P, MODE>((int)blockIdx.x, x, y, tiles, n_tiles, n_warps, S, n, st, items, n_items, prims, incs,
                          n_if_blocks, md, ring_all, ringb_all);
 }
@@ -435,6 +439,7 @@ __global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d_batch(const __
   constexpr bool SWEEP = MODE == MODE_JACOBI || MODE == MODE_RESIDUAL;
   __shared__ T ring_all[THR / 32][RING][32][2];
   __shared__ T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
+  pdl_trigger();
   int lo = 0, hi = b.count - 1;  // the last mesh whose range starts at or before this block
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -480,10 +485,10 @@ cudaError_t launch_on(const Mesh& m, const LevelDev& L, const int4* tiles, int n
   const int if_blocks = (L.n_items + per - 1) / per;
   if (int_blocks + if_blocks == 0) return cudaSuccess;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
-  k_interior2d<P, MODE><<<(unsigned)(int_blocks + if_blocks), threads, 0, s>>>(
-      (const typename P::T*)x, (typename P::T*)y, tiles, n_tiles > 0 ? n_tiles : 1, n_warps,
-      L.slots_per_macro, L.n, st, L.items, L.n_items, m.d_prims, m.d_incs, if_blocks, md);
-  return cudaGetLastError();
+  return launch_pdl(k_interior2d<P, MODE>, dim3((unsigned)(int_blocks + if_blocks)), dim3(threads), 0, s,
+                    (const typename P::T*)x, (typename P::T*)y, tiles, n_tiles > 0 ? n_tiles : 1, n_warps,
+                    L.slots_per_macro, L.n, st, (const int4*)L.items, L.n_items, (const Prim*)m.d_prims,
+                    (const Inc*)m.d_incs, if_blocks, md);
 }
 
 template <class P, int MODE>
@@ -532,8 +537,7 @@ cudaError_t launch_batch_t(const Mesh* const* meshes, const int* levels, const v
       blocks += int(int_blocks + if_blocks);
     }
     if (b.count == 0) continue;
-    k_interior2d_batch<P, MODE><<<blocks, THR, 0, s>>>(b);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_pdl(k_interior2d_batch<P, MODE>, dim3(blocks), dim3(THR), 0, s, b);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -293,6 +293,7 @@ __device__ __forceinline__ T restrict_partial(const T* __restrict__ rf, const T*
 template <class T, int DIM>
 struct Restrict {
   static constexpr int kThreads = 128;
+  static constexpr bool kLateWait = true;  // the interface items' tables first
   struct Prm {
     const T* rf;
     T *bc, *uc;
@@ -312,6 +313,7 @@ struct Restrict {
     if (block < p.n_if_blocks) {
       const int4 it = p.items[block];
       const Prim pr = p.prims[it.x];
+      pdl_wait();
       if (pr.type == 0 && !pr.boundary && pr.inc_count <= 32) {
         // a coarse vertex inside the domain: lane i of the first warp takes
         // copy i, and every lane adds the partials in ascending copy order
@@ -374,6 +376,7 @@ struct Restrict {
       }
       return;
     }
+    pdl_wait();
     const SlotDiv divSc(p.Sc, p.total);
     const int64_t stride = (int64_t)(nb - p.n_if_blocks) * 128;
     for (int64_t i = (int64_t)(block - p.n_if_blocks) * 128 + threadIdx.x; i < p.total; i += stride) {

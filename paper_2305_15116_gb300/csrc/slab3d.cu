@@ -172,6 +172,7 @@ __device__ __forceinline__ void slab3d_item(const typename P::T* __restrict__ x,
   // zero the ring (guards and stale tails must hold finite values), class weights
   for (int i = tid; i < NRING * stride; i += SLAB_THREADS) ring[i] = SS::zero();
   for (int i = tid; i < NCLS3 * NW3; i += SLAB_THREADS) wcls[i] = WS::load(st, (int64_t)m * (NCLS3 * NW3) + i);
+  pdl_wait();  // x and y after the previous kernel in the stream (group.cuh)
   __syncthreads();
   // slices z0-1 .. z0+1 directly
   for (int z = max(z0 - 1, 0); z <= min(z0 + 1, n); ++z) {
@@ -331,6 +332,7 @@ __global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d(cons
                                                          typename P::T* __restrict__ y,
                                                          const int4* __restrict__ items, int n, int64_t S,
                                                          int buf_elems, int guard, StencilPtr st) {
+  pdl_trigger();
   slab3d_item<P>(x, y, items[blockIdx.x], n, S, buf_elems, guard, st);
 }
 
@@ -353,6 +355,7 @@ struct SlabGroup {
 
 template <class P>
 __global__ void __launch_bounds__(SLAB_THREADS, SlabOcc<P>::value) k_slab3d_group(const __grid_constant__ SlabGroup g) {
+  pdl_trigger();
   int lo = 0, hi = g.count - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -401,9 +404,8 @@ cudaError_t launch_items(const LevelDev& L, const int4* items, int n_items, cons
   if (attr != cudaSuccess) return attr;
   if (n > 64) return cudaErrorInvalidValue;
   StencilPtr st{L.st64, L.st32, L.st_hi, L.st_lo};
-  k_slab3d<P><<<n_items, SLAB_THREADS, bytes, s>>>((const typename P::T*)x, (typename P::T*)y, items, n,
-                                                  L.slots_per_macro, buf, guard, st);
-  return cudaGetLastError();
+  return launch_pdl(k_slab3d<P>, dim3(n_items), dim3(SLAB_THREADS), bytes, s, (const typename P::T*)x,
+                    (typename P::T*)y, items, n, L.slots_per_macro, buf, guard, st);
 }
 
 template <class P>
@@ -441,8 +443,7 @@ cudaError_t launch_group_t(const Mesh* const* ms, const int* levels, const void*
       blocks += n_items;
     }
     i0 = i;
-    k_slab3d_group<P><<<blocks, SLAB_THREADS, w_bytes + ring_bytes, s>>>(g);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_pdl(k_slab3d_group<P>, dim3(blocks), dim3(SLAB_THREADS), w_bytes + ring_bytes, s, g);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
