@@ -20,6 +20,7 @@
 // pair come from the adjacent lanes by warp shuffles, so every value is read
 // from memory once per tile plus two halo rows.  62 of the 64 columns are
 // written; the outermost two only supply the horizontal halo.
+#include <type_traits>
 #include <vector>
 
 #include "arith.cuh"
@@ -223,8 +224,7 @@ __device__ __forceinline__ void iface2d_vertex(const T* __restrict__ x, T* __res
 // Rows in flight per warp: each lane stages its two columns of the next RING
 // rows in shared memory with cp.async, so a warp keeps RING rows outstanding
 // without holding them in registers.
-constexpr int RING = 8;  // a power of two
-static_assert((RING & (RING - 1)) == 0, "RING must be a power of two");
+constexpr int RING = 6;  // rows in flight; the walk is unrolled by six (two rotations of three rows)
 constexpr int THREADS2D = 256;
 
 // One launch does the whole apply: blocks 0 .. n_if_blocks-1 take the
@@ -290,47 +290,61 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
                       wN = P::weight(st, wb + 6);
   pdl_wait();  // the vectors after the previous kernel in the stream (group.cuh)
 
-  // rows t.y - 1 .. t.z are read, rows t.y .. t.z - 1 written
+  // Step k reads row r_k = t.y - 1 + k (k = 0 .. steps-1) and writes row
+  // r_{k-1} (k >= 2).  Row r holds n + 1 - r points, so column c lies inside
+  // row r_k exactly for k < n + 2 - t.y - c: one compare of the step index per
+  // column.  A point (c, r) is interior when c < len(r) - 1 = len(r + 1), so
+  // the row written at step k holds column c as an interior point exactly when
+  // the row read at step k holds column c: the write predicate is the read
+  // predicate of the same step.
   const int steps = t.z - t.y + 2;
-  Cursor is;  // next row to stage
-  is.init(n, t.y - 1);
-  auto stage = [&](int slot) {
-    if (ca < is.len) {
-      cp_async(&ring[slot][lane][0], xm + is.off + ca, sizeof(T));
-      if (SWEEP) cp_async(&ringb[slot][lane][0], bm + is.off + ca, sizeof(T));
+  const int ka = n + 2 - t.y - ca, kb = ka - 1;  // steps whose row holds column ca / cb
+  const bool wa = lane >= 1, wbb = lane <= 30;   // lane 0's A and lane 31's B are halo
+  int off_s = (t.y - 1) * (n + 2) - ((t.y - 1) * t.y) / 2;  // the row being staged
+  int len_s = n + 2 - t.y;
+  const T* __restrict__ xa = xm + ca;
+  const T* __restrict__ ba = SWEEP ? bm + ca : nullptr;
+  auto stage = [&](int slot, int k) {  // row r_k into ring slot `slot`
+    if (k < ka) {
+      cp_async(&ring[slot][lane][0], xa + off_s, sizeof(T));
+      if (SWEEP) cp_async(&ringb[slot][lane][0], ba + off_s, sizeof(T));
     }
-    if (cb < is.len) {
-      cp_async(&ring[slot][lane][1], xm + is.off + cb, sizeof(T));
-      if (SWEEP) cp_async(&ringb[slot][lane][1], bm + is.off + cb, sizeof(T));
+    if (k < kb) {
+      cp_async(&ring[slot][lane][1], xa + off_s + 1, sizeof(T));
+      if (SWEEP) cp_async(&ringb[slot][lane][1], ba + off_s + 1, sizeof(T));
     }
-    is.next();
+    off_s += len_s;
+    len_s -= 1;
   };
 #pragma unroll
   for (int k = 0; k < RING; ++k) {
-    if (k < steps) stage(k);
+    if (k < steps) stage(k, k);
     cp_async_commit();
   }
-  Cursor cr;  // row being consumed
-  cr.init(n, t.y - 1);
-  auto take = [&](int k) -> Row<P> {
+  // Columns beyond a row's end hold stale values, which reach only results
+  // that are not written; the float-float kernel zeroes them, since its row
+  // marks see every lane's arithmetic.
+  auto take = [&](int k, auto slot_c) -> Row<P> {
+    constexpr int slot = decltype(slot_c)::value;
     cp_async_wait<RING - 1>();
-    const T va = ring[k & (RING - 1)][lane][0], vb = ring[k & (RING - 1)][lane][1];
-    Row<P> r = make_row<P>(ca < cr.len ? P::conv(va) : P::zero(), cb < cr.len ? P::conv(vb) : P::zero());
+    const T va = ring[slot][lane][0], vb = ring[slot][lane][1];
+    Row<P> r = P::kPoison ? make_row<P>(k < ka ? P::conv(va) : P::zero(), k < kb ? P::conv(vb) : P::zero())
+                          : make_row<P>(P::conv(va), P::conv(vb));
     if (SWEEP) {  // read before the slot is staged again
-      r.b[0] = ringb[k & (RING - 1)][lane][0];
-      r.b[1] = ringb[k & (RING - 1)][lane][1];
+      r.b[0] = ringb[slot][lane][0];
+      r.b[1] = ringb[slot][lane][1];
     }
     // the slot of step k is free again: stage step k + RING
-    if (k + RING < steps) stage(k & (RING - 1));
+    if (k + RING < steps) stage(slot, k + RING);
     cp_async_commit();
-    cr.next();
     return r;
   };
-  Cursor out = cr;  // the row being written (set after the first take)
-  const bool wa = lane >= 1, wbb = lane <= 30;  // lane 0's A and lane 31's B are halo
+  int off_o = t.y * (n + 2) - (t.y * (t.y + 1)) / 2;  // the row being written
+  int len_o = n + 1 - t.y;
+  T* __restrict__ ya = ym + ca;
   typename P::Mark mk = P::mark0();
-  // output row from (below, centre, above)
-  auto step = [&](const Row<P>& lo, const Row<P>& ce, const Row<P>& hi) {
+  // output row r_{k-1} from (below, centre, above) = rows r_{k-2}, r_{k-1}, r_k
+  auto step = [&](const Row<P>& lo, const Row<P>& ce, const Row<P>& hi, int k) {
     // the interior stencil is symmetric (w(d) = w(-d), made bitwise equal on
     // the host): add opposite neighbours first
     typename P::Acc a;
@@ -340,7 +354,6 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
     P::add_sym(a, wSE, lo.e, hi.w);
     T outa, outb;
     P::finish(a, outa, outb);
-    // point (c, r) is interior when c <= n - 1 - r, i.e. c < len - 1
     P::mark(mk, a);  // float-float: notes a row that read an input outside the range
     if (SWEEP) {  // the centre values of the row are u (fp32 data)
       float ua = 0.0f, ub = 0.0f;
@@ -351,25 +364,40 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
       outa = mode_out_staged<MODE, T>(outa, (T)ua, ce.b[0], dint, md.omega);
       outb = mode_out_staged<MODE, T>(outb, (T)ub, ce.b[1], dint, md.omega);
     }
-    if (wa && ca < out.len - 1) ym[out.off + ca] = outa;
-    if (wbb && cb < out.len - 1) ym[out.off + cb] = outb;
-    out.next();
+    if (wa && k < ka) ya[off_o] = outa;
+    if (wbb && k < kb) ya[off_o + 1] = outb;
+    off_o += len_o;
+    len_o -= 1;
   };
-  // three rows in registers whose roles rotate, unrolled by three so that no
-  // row is ever copied between registers
-  Row<P> r0 = take(0);
-  out = cr;
-  Row<P> r1 = take(1);
+  // three rows in registers whose roles rotate, unrolled by six so that no
+  // row is ever copied between registers and every ring slot is a constant
+  using S0 = std::integral_constant<int, 0>;
+  using S1 = std::integral_constant<int, 1>;
+  using S2 = std::integral_constant<int, 2>;
+  using S3 = std::integral_constant<int, 3>;
+  using S4 = std::integral_constant<int, 4>;
+  using S5 = std::integral_constant<int, 5>;
+  Row<P> r0 = take(0, S0{});
+  Row<P> r1 = take(1, S1{});
   Row<P> r2;
-  for (int k = 2; k < steps; k += 3) {
-    r2 = take(k);
-    step(r0, r1, r2);
+  for (int k = 2; k < steps; k += 6) {
+    r2 = take(k, S2{});
+    step(r0, r1, r2, k);
     if (k + 1 >= steps) break;
-    r0 = take(k + 1);
-    step(r1, r2, r0);
+    r0 = take(k + 1, S3{});
+    step(r1, r2, r0, k + 1);
     if (k + 2 >= steps) break;
-    r1 = take(k + 2);
-    step(r2, r0, r1);
+    r1 = take(k + 2, S4{});
+    step(r2, r0, r1, k + 2);
+    if (k + 3 >= steps) break;
+    r2 = take(k + 3, S5{});
+    step(r0, r1, r2, k + 3);
+    if (k + 4 >= steps) break;
+    r0 = take(k + 4, S0{});
+    step(r1, r2, r0, k + 4);
+    if (k + 5 >= steps) break;
+    r1 = take(k + 5, S1{});
+    step(r2, r0, r1, k + 5);
   }
   cp_async_wait<0>();
   if constexpr (P::kPoison) {
@@ -388,8 +416,15 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
   }
 }
 
+// Blocks per SM the kernel is built for: three for float-float (80
+// registers), the compiler's own choice otherwise.
+template <class P>
+struct MinBlocks2 {
+  static constexpr int value = P::kPoison ? 3 : 0;
+};
+
 template <class P, int MODE>
-__global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d(const typename P::T* __restrict__ x,
+__global__ void __launch_bounds__(Thr2<MODE>::value, MinBlocks2<P>::value) k_interior2d(const typename P::T* __restrict__ x,
                                                           typename P::T* __restrict__ y,
                                                           const int4* __restrict__ tiles, int n_tiles,
                                                           int64_t n_warps, int64_t S, int n, StencilPtr st,
@@ -433,7 +468,7 @@ struct Apply2dBatch {
 };
 
 template <class P, int MODE>
-__global__ void __launch_bounds__(Thr2<MODE>::value) k_interior2d_batch(const __grid_constant__ Apply2dBatch b) {
+__global__ void __launch_bounds__(Thr2<MODE>::value, MinBlocks2<P>::value) k_interior2d_batch(const __grid_constant__ Apply2dBatch b) {
   using T = typename P::T;
   constexpr int THR = Thr2<MODE>::value;
   constexpr bool SWEEP = MODE == MODE_JACOBI || MODE == MODE_RESIDUAL;

@@ -126,3 +126,25 @@ def test_group_arguments(cuda):
     assert H.solve_two_part_group([], 3, [], [], []) == []
     M2.close()
     M3.close()
+
+
+def test_group_larger_than_one_launch(cuda):
+    """18 problems: every solve step needs two launches of at most 16 meshes
+    each (the group launch's parameter block); each result stays bitwise
+    that of its solve alone."""
+    H = _lib()
+    L = 4
+    cs = [rect_mesh(1 + k % 3, 1 + (k // 3) % 2, 0.15, k) for k in range(18)]
+    alone = []
+    for i, c in enumerate(cs):
+        M, b = _problem(c, L, 80 + i)
+        alone.append(_alone(M, L, b, H.SOLVE_MIXED))
+        M.close()
+    gp = [_problem(c, L, 80 + i) for i, c in enumerate(cs)]
+    grouped = _group([M for M, _ in gp], L, [b for _, b in gp], H.SOLVE_MIXED)
+    for a, g in zip(alone, grouped):
+        assert a[1] <= 1e-10
+        assert a[0] == g[0] and a[1] == g[1]
+        assert np.array_equal(a[2], g[2]) and np.array_equal(a[3], g[3])
+    for M, _ in gp:
+        M.close()
