@@ -133,16 +133,6 @@ struct Zero {
   static __device__ __forceinline__ void run(const Prm& p, int block, int nb) { GRID_STRIDE(i, p.n) p.p[i] = T(0); }
 };
 
-__global__ void k_add_f64(double* __restrict__ u, const double* __restrict__ e, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    u[i] = u[i] + e[i];
-}
-
-__global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ e, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    u[i] = u[i] + (double)e[i];
-}
-
 // (u, ulo) <- (fl(u + ulo), the rest): u becomes the float64 rounding of the
 // two-part value (Fast2Sum, exact while |ulo| <= |u|, which the corrections
 // keep: ulo collects rounding errors of u).
