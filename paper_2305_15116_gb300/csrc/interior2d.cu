@@ -224,7 +224,7 @@ __device__ __forceinline__ void iface2d_vertex(const T* __restrict__ x, T* __res
 // Rows in flight per warp: each lane stages its two columns of the next RING
 // rows in shared memory with cp.async, so a warp keeps RING rows outstanding
 // without holding them in registers.
-constexpr int RING = 6;  // rows in flight; the walk is unrolled by six (two rotations of three rows)
+constexpr int RING = 3;  // rows in flight; the walk is unrolled by three
 constexpr int THREADS2D = 256;
 
 // One launch does the whole apply: blocks 0 .. n_if_blocks-1 take the
@@ -369,35 +369,23 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
     off_o += len_o;
     len_o -= 1;
   };
-  // three rows in registers whose roles rotate, unrolled by six so that no
+  // three rows in registers whose roles rotate, unrolled by three so that no
   // row is ever copied between registers and every ring slot is a constant
   using S0 = std::integral_constant<int, 0>;
   using S1 = std::integral_constant<int, 1>;
   using S2 = std::integral_constant<int, 2>;
-  using S3 = std::integral_constant<int, 3>;
-  using S4 = std::integral_constant<int, 4>;
-  using S5 = std::integral_constant<int, 5>;
   Row<P> r0 = take(0, S0{});
   Row<P> r1 = take(1, S1{});
   Row<P> r2;
-  for (int k = 2; k < steps; k += 6) {
+  for (int k = 2; k < steps; k += 3) {
     r2 = take(k, S2{});
     step(r0, r1, r2, k);
     if (k + 1 >= steps) break;
-    r0 = take(k + 1, S3{});
+    r0 = take(k + 1, S0{});
     step(r1, r2, r0, k + 1);
     if (k + 2 >= steps) break;
-    r1 = take(k + 2, S4{});
+    r1 = take(k + 2, S1{});
     step(r2, r0, r1, k + 2);
-    if (k + 3 >= steps) break;
-    r2 = take(k + 3, S5{});
-    step(r0, r1, r2, k + 3);
-    if (k + 4 >= steps) break;
-    r0 = take(k + 4, S0{});
-    step(r1, r2, r0, k + 4);
-    if (k + 5 >= steps) break;
-    r1 = take(k + 5, S1{});
-    step(r2, r0, r1, k + 5);
   }
   cp_async_wait<0>();
   if constexpr (P::kPoison) {
