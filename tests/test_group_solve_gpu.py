@@ -148,3 +148,24 @@ def test_group_larger_than_one_launch(cuda):
         assert np.array_equal(a[2], g[2]) and np.array_equal(a[3], g[3])
     for M, _ in gp:
         M.close()
+
+
+def test_group_above_the_slab_levels_runs_one_after_another(cuda):
+    """3D level 7 (the row kernel, no group launch): the group call solves
+    its problems one after another, each exactly as alone."""
+    H = _lib()
+    L = 7
+    cs = [box_kuhn_mesh(1, 1, 1, 0.1, 5), box_kuhn_mesh(1, 1, 1, 0.1, 6)]
+    alone = []
+    for i, c in enumerate(cs):
+        M, b = _problem(c, L, 90 + i)
+        alone.append(_alone(M, L, b, H.SOLVE_MIXED, rtol=1e-9))
+        M.close()
+    gp = [_problem(c, L, 90 + i) for i, c in enumerate(cs)]
+    grouped = _group([M for M, _ in gp], L, [b for _, b in gp], H.SOLVE_MIXED, rtol=1e-9)
+    for a, g in zip(alone, grouped):
+        assert a[1] <= 1e-9
+        assert a[0] == g[0] and a[1] == g[1]
+        assert np.array_equal(a[2], g[2]) and np.array_equal(a[3], g[3])
+    for M, _ in gp:
+        M.close()

@@ -44,12 +44,16 @@ def _partitioned(coarse, L, world, xs, kind):
 
 
 @pytest.mark.parametrize("kind", ["f64", "f64_ieee", "f32"])
-@pytest.mark.parametrize("dim,world", [(2, 2), (2, 3), (3, 2), (3, 4)])
-def test_partitioned_apply_bitwise_on_gpu(cuda, dim, world, kind):
+@pytest.mark.parametrize("dim,world,L", [(2, 2, 6), (2, 3, 6), (3, 2, 4), (3, 4, 4), (3, 2, 7)])
+def test_partitioned_apply_bitwise_on_gpu(cuda, dim, world, L, kind):
+    """2D and 3D (level 4: the slab kernel; level 7: the row kernel), two to
+    four ranks."""
     import torch
     H = _lib()
-    coarse = unit_square_mesh(4, 0.15, 0) if dim == 2 else unit_cube_kuhn_mesh(2, 0.1, 0)
-    L = 6 if dim == 2 else 4
+    if dim == 2:
+        coarse = unit_square_mesh(4, 0.15, 0)
+    else:
+        coarse = unit_cube_kuhn_mesh(2, 0.1, 0) if L < 7 else unit_cube_kuhn_mesh(1, 0.1, 0)
     M = H.Mesh(coarse.coords, coarse.cells).refine(L)
     ns, ng = M.num_slots(L)
     xs = random_vector(ng, 9)[M.dof_map(L)]
