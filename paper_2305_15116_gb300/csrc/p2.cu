@@ -14,6 +14,8 @@
 //
 // Layout per macro: vertex array (row y at y(n+2) - y(y+1)/2), then the X, Y
 // and XY edge arrays, edge (x, y) at y n - y(y-1)/2 + x.
+#include <type_traits>
+
 #include "arith.cuh"
 #include "fallback.cuh"
 #include "hyteg_internal.h"
@@ -196,11 +198,12 @@ __device__ __forceinline__ void p2_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void p2_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// rows in flight per warp (a power of two): 8 for fp32, 4 for 8-byte data
-// (the static shared-memory limit)
+// rows in flight per warp: three, one per register row, so that the walk
+// unrolled by three finds every ring slot at a constant (8 rows for fp32 and
+// 4 for 8-byte data with a computed slot ran 6 % / 1 % slower)
 template <class T>
 struct P2Ring {
-  static constexpr int value = sizeof(T) == 4 ? 8 : 4;
+  static constexpr int value = 3;
 };
 constexpr int P2THREADS = 256;
 
@@ -272,9 +275,9 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
   Cur cr;  // row being consumed
   cr.init(n, t.y - 1);
   int rc = t.y - 1;
-  auto take = [&](int k) -> P2Row<P> {
+  auto take = [&](int k, auto slot_c) -> P2Row<P> {
     p2_wait<P2RING - 1>();
-    const int slot = k & (P2RING - 1);
+    constexpr int slot = decltype(slot_c)::value;
     const bool okv = rc >= 0 && c >= 0 && c < cr.lv, oke = rc >= 0 && c >= 0 && c < cr.le;
     const V v = okv ? P::conv(ring[slot][0][lane]) : P::zero();
     const V ex = oke ? P::conv(ring[slot][1][lane]) : P::zero();
@@ -354,17 +357,20 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
     ++yo;
     co.next();
   };
-  P2Row<P> r0 = take(0);
-  P2Row<P> r1 = take(1);
+  using S0 = std::integral_constant<int, 0>;
+  using S1 = std::integral_constant<int, 1>;
+  using S2 = std::integral_constant<int, 2>;
+  P2Row<P> r0 = take(0, S0{});
+  P2Row<P> r1 = take(1, S1{});
   P2Row<P> r2;
   for (int k = 2; k < steps; k += 3) {
-    r2 = take(k);
+    r2 = take(k, S2{});
     step(r0, r1, r2);
     if (k + 1 >= steps) break;
-    r0 = take(k + 1);
+    r0 = take(k + 1, S0{});
     step(r1, r2, r0);
     if (k + 2 >= steps) break;
-    r1 = take(k + 2);
+    r1 = take(k + 2, S1{});
     step(r2, r0, r1);
   }
   p2_wait<0>();
