@@ -450,6 +450,62 @@ def solve_workload(device, stream, reps=3, rtol=1e-10):
     return out
 
 
+def group_workload(device, stream, count=8, level=7, reps=3, rtol=1e-10):
+    """`count` Poisson problems on different 2D meshes (8 to 12 jittered
+    macro-triangles) at one level, solved one after another with
+    hyteg_solve_two_part against all at once with hyteg_solve_two_part_group
+    (one launch per solve step for all problems still iterating); the
+    results agree bit for bit."""
+    import torch
+    import paper_2305_15116_gb300 as H
+    from inputs import rect_mesh
+    meshes, bs = [], []
+    for k in range(count):
+        c = rect_mesh(2, 2 + k % 2, 0.15, k)
+        M = H.Mesh(c.coords, c.cells).refine(level).solver_setup(level)
+        b = torch.empty(M.num_slots(level)[0], dtype=torch.float64, device=device)
+        M.poisson_rhs(level, 100 + k, 0.1, b, stream=stream)
+        meshes.append(M)
+        bs.append(b)
+    us = [torch.zeros_like(b) for b in bs]
+    ls = [torch.zeros_like(b) for b in bs]
+
+    def alone():
+        out = []
+        for M, b, u, lo in zip(meshes, bs, us, ls):
+            u.zero_()
+            lo.zero_()
+            out.append(M.solve_two_part(level, b, u, lo, rtol=rtol, max_iter=100, stream=stream))
+        return out
+
+    def grouped():
+        for u, lo in zip(us, ls):
+            u.zero_()
+            lo.zero_()
+        return H.solve_two_part_group(meshes, level, bs, us, ls, rtol=rtol, max_iter=100, stream=stream)
+
+    out = {"workload": f"{count} Poisson problems, 2D, 8 or 12 jittered macro-triangles each, level {level}, "
+                       f"rtol {rtol}, fp32 V(3,3) cycles in two-part float64 refinement"}
+    res = {}
+    for label, fn in (("one_after_another", alone), ("group", grouped)):
+        fn()  # warm-up (the single solves' second run replays their cycles as CUDA graphs)
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+        res[label] = ([u.clone() for u in us], r)
+        out[label] = {"ms": 1e3 * min(times), "iterations": [it for it, _ in r],
+                      "relres_max": max(rel for _, rel in r)}
+    out["speedup"] = out["one_after_another"]["ms"] / out["group"]["ms"]
+    out["bitwise_equal"] = all(torch.equal(a, b) for a, b in zip(res["one_after_another"][0], res["group"][0]))
+    for M in meshes:
+        M.close()
+    return out
+
+
 # ---------------------------------------------------------------- solve server
 def serve_workload(n_requests, workers, cap_bytes=40 << 30, rtol=1e-10, mode=None, rate=2000.0):
     """The solve server under the synthetic request stream of inputs.serving:
@@ -809,6 +865,7 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_variants:
         line["solve"] = solve_workload(device, stream)
+        line["group_solve"] = group_workload(device, stream)
         torch.cuda.empty_cache()
 
     if rank == 0 and world == 1 and not args.no_variants and args.serve_requests > 0:
