@@ -835,16 +835,35 @@ cudaError_t sweep2d_g(bool jacobi, Mesh* const* ms, int cnt, int l, const float*
                               cnt, s);
 }
 
+// Whether a level's sweeps are fused 2D fp32 launches (apply, interface and
+// Jacobi update together, alternating between the level's u and y) rather
+// than an apply followed by an in-place update.
+template <class T>
+bool fused_sweeps(const Mesh& m) {
+  return sizeof(T) == 4 && m.dim == 2;
+}
+
+// The vector that receives a level's first sweep from a zero guess when the
+// launch producing its right-hand side performs it: on fused levels the
+// spare y, so that the even number of sweeps of V(3,3) (the first, two more
+// pre-sweeps, three post-sweeps) ends in u without a copy; else u.
+template <class T>
+T* first_sweep_vector(Mesh& m, int l) {
+  MgLevel& g = m.solver->lv[l];
+  return fused_sweeps<T>(m) ? Vecs<T>::y(g) : Vecs<T>::u(g);
+}
+
 // One V(nu1, nu2) cycle on level l for A u = b of every member (u updated in
-// place).  first_done: u already holds the first pre-smoothing sweep from a
-// zero guess (u = omega D^-1 b, written by the launch that produced b), so
-// one sweep fewer is run here.
+// place).  first_done: the first pre-smoothing sweep from a zero guess
+// (omega D^-1 b) has been written by the launch that produced b, into
+// first_sweep_vector, so one sweep fewer is run here.
 template <class T>
 cudaError_t vcycle_g(Mesh* const* ms, int cnt, int l, const T* const* b, T* const* u, cudaStream_t s,
                      bool first_done) {
   if (l == 0) return coarse_g<T>(ms, cnt, u, b, s);
   const Solver& sv0 = *ms[0]->solver;
-  std::vector<T*> y(cnt), r(cnt), cur(u, u + cnt), alt(cnt), bc(cnt), uc(cnt);
+  const bool fused = fused_sweeps<T>(*ms[0]);
+  std::vector<T*> y(cnt), r(cnt), cur(u, u + cnt), alt(cnt), bc(cnt), uc(cnt), fc(cnt);
   for (int i = 0; i < cnt; ++i) {
     MgLevel& g = ms[i]->solver->lv[l];
     MgLevel& gc = ms[i]->solver->lv[l - 1];
@@ -852,13 +871,14 @@ cudaError_t vcycle_g(Mesh* const* ms, int cnt, int l, const T* const* b, T* cons
     r[i] = Vecs<T>::r(g);
     bc[i] = Vecs<T>::b(gc);
     uc[i] = Vecs<T>::u(gc);
+    fc[i] = first_sweep_vector<T>(*ms[i], l - 1);
+    if (fused && first_done) cur[i] = y[i];  // where the first sweep landed
   }
   // 2D fp32 cycles: every sweep is one fused launch (apply, interface and
   // Jacobi update together), alternating between u and y; the residual
   // likewise.  Float64 cycles and 3D: apply, then update.  `cur` holds the
   // smoothed iterate; it alternates between u and y and is copied back into
   // u only if the sweep count is odd.
-  const bool fused = sizeof(T) == 4 && ms[0]->dim == 2;
   auto sweeps = [&](int count) -> cudaError_t {
     for (int it = 0; it < count; ++it) {
       for (int i = 0; i < cnt; ++i) alt[i] = cur[i] == u[i] ? y[i] : u[i];
@@ -886,7 +906,7 @@ cudaError_t vcycle_g(Mesh* const* ms, int cnt, int l, const T* const* b, T* cons
   // the restriction also performs the coarse level's first sweep from zero;
   // level 0 is solved directly and overwrites all of uc
   const bool first = sv0.nu1 >= 1 && l - 1 > 0;
-  HY_TRY(restrict_g<T>(ms, cnt, l, r.data(), bc.data(), first ? uc.data() : nullptr, s));
+  HY_TRY(restrict_g<T>(ms, cnt, l, r.data(), bc.data(), first ? fc.data() : nullptr, s));
   if (!first && l - 1 > 0) HY_TRY(zero_g<T>(ms, cnt, l - 1, uc.data(), s));
   HY_TRY(vcycle_g<T>(ms, cnt, l - 1, bc.data(), uc.data(), s, first));
   HY_TRY(prolong_g<T>(ms, cnt, l, uc.data(), cur.data(), s));
@@ -1107,8 +1127,8 @@ cudaError_t mg_solve_group(Mesh* const* ms, int cnt, int l, int mode, const doub
       Batch<ResidualNorm<float>> R;
       for (int i : idx) {
         MgLevel& g = ms[i]->solver->lv[l];
-        R.add({g.b32, first ? g.u32 : nullptr, g.dinv32, (float)ms[i]->solver->omega, b[i], g.y64, g.owner,
-               n_slots(*ms[i], l), ms[i]->solver->red},
+        R.add({g.b32, first ? first_sweep_vector<float>(*ms[i], l) : nullptr, g.dinv32,
+               (float)ms[i]->solver->omega, b[i], g.y64, g.owner, n_slots(*ms[i], l), ms[i]->solver->red},
               RED_BLOCKS);
       }
       HY_TRY(R.launch(s));
@@ -1116,8 +1136,8 @@ cudaError_t mg_solve_group(Mesh* const* ms, int cnt, int l, int mode, const doub
       Batch<ResidualNorm<double>> R;
       for (int i : idx) {
         MgLevel& g = ms[i]->solver->lv[l];
-        R.add({g.b64, first ? g.u64 : nullptr, g.dinv64, ms[i]->solver->omega, b[i], g.y64, g.owner,
-               n_slots(*ms[i], l), ms[i]->solver->red},
+        R.add({g.b64, first ? first_sweep_vector<double>(*ms[i], l) : nullptr, g.dinv64, ms[i]->solver->omega,
+               b[i], g.y64, g.owner, n_slots(*ms[i], l), ms[i]->solver->red},
               RED_BLOCKS);
       }
       HY_TRY(R.launch(s));
