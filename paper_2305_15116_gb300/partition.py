@@ -78,6 +78,10 @@ class PartitionPlan:
         cells = np.ascontiguousarray(cells, dtype=np.int64)
         if world > 63:
             raise ValueError("at most 63 ranks")
+        if not 0 <= rank < world:
+            raise ValueError("rank must lie in 0 .. world - 1")
+        if world > cells.shape[0]:
+            raise ValueError("more ranks than coarse cells: every rank needs a macro")
         self.level, self.rank, self.world = level, rank, world
         self.blocks = cell_blocks(cells.shape[0], world)
         c0, c1 = self.blocks[rank]

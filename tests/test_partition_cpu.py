@@ -164,3 +164,15 @@ def test_rank_mesh_has_the_whole_meshs_slot_layout(case, world):
         # between the two numberings
         pairs = np.unique(np.stack([lid, blk]), axis=1).shape[1]
         assert pairs == np.unique(lid).size == np.unique(blk).size
+
+
+def test_plan_arguments():
+    """A rank outside the world, or more ranks than coarse cells (every rank
+    owns at least one macro), are refused before any mesh is built."""
+    sys.path.insert(0, ROOT)
+    from paper_2305_15116_gb300.partition import PartitionPlan
+    coarse, L = _coarse("square8_L3")
+    with pytest.raises(ValueError):
+        PartitionPlan(coarse.coords, coarse.cells, L, 3, 3)
+    with pytest.raises(ValueError):
+        PartitionPlan(coarse.coords, coarse.cells, L, 0, coarse.cells.shape[0] + 1)
