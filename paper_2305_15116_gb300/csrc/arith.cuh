@@ -100,30 +100,31 @@ __device__ __forceinline__ FF ff_split(double v) {
   // sign | (e - 896) << 23 | top 23 mantissa bits  (truncation)
   unsigned hb = __funnelshift_l(lo, hi - (896u << 20), 3);
   hb = (hb & 0x7FFFFFFFu) | (hi & 0x80000000u);
-  // next 23 mantissa bits (bits 28..6 of the low word) as an exact integer
-  const float t = __fsub_rn(__uint_as_float(0x4B000000u | ((lo >> 6) & 0x7FFFFFu)), 8388608.0f);
-  // their weight: 2^(exponent of v - 46), with the sign of v (a normal fp32
-  // inside the range; finite for zero, where t = 0)
-  const unsigned sb = (hb & 0xFF800000u) - (46u << 23);
+  // the next 23 mantissa bits (bits 28..6 of the low word) as the mantissa of
+  // a float with the sign of v and the exponent of h minus 23: that float is
+  // 2^(e-23) + l exactly, and subtracting 2^(e-23) leaves l (exact; a normal
+  // fp32 inside the range, and l = 0 for zero)
+  const unsigned eb = (hb & 0xFF800000u) - (23u << 23);
+  const float lb = __uint_as_float(eb | ((lo >> 6) & 0x7FFFFFu));
   const bool in_range = mag - (unsigned(1023 + FF_EMIN) << 20) < (unsigned(FF_EMAX - FF_EMIN) << 20);
   const bool zero = (mag | lo) == 0u;
   FF r;
   r.h = in_range ? __uint_as_float(hb) : (zero ? __uint_as_float(hi & 0x80000000u) : __int_as_float(0x7FC00000));
-  r.l = __fmul_rn(t, __uint_as_float(sb));
+  r.l = __fsub_rn(lb, __uint_as_float(eb));
   return r;
 }
 
 // Exact float32 -> float64 of 2^-40 f with integer instructions (no
 // conversion unit): the row sums carry the weights' 2^40 scaling.  Zero
-// maps to zero; fp32 subnormals (|f| < 2^-126) are dropped.
+// maps to zero; an fp32 subnormal (|f| < 2^-126, standing for less than
+// 2^-166) maps to a float64 subnormal (below 2^-1022), which is as good as
+// dropping it.
 __device__ __forceinline__ double f32s_to_f64_bits(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned a = u & 0x7FFFFFFFu;
-  const unsigned hi =
-      a >= 0x00800000u ? (((a >> 3) + ((896u - unsigned(FF_WSCALE)) << 20)) | (u & 0x80000000u))
-                       : (u & 0x80000000u);
-  const unsigned lo = a >= 0x00800000u ? (u << 29) : 0u;
-  return __hiloint2double((int)hi, (int)lo);
+  const unsigned bias = a >= 0x00800000u ? ((896u - unsigned(FF_WSCALE)) << 20) : 0u;
+  const unsigned hi = ((a >> 3) + bias) | (u & 0x80000000u);
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 // float64 value of 2^-40 (s + e) for the unevaluated sum s + e of a row

@@ -20,6 +20,7 @@
 // pair come from the adjacent lanes by warp shuffles, so every value is read
 // from memory once per tile plus two halo rows.  62 of the 64 columns are
 // written; the outermost two only supply the horizontal halo.
+#include <cstdint>
 #include <type_traits>
 #include <vector>
 
@@ -74,6 +75,14 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem));
 }
+// an 8-byte element of shared memory set to zero by an asynchronous copy that
+// reads no bytes (src, a valid global address, is not accessed)
+__device__ __forceinline__ void cp_async_zero(void* smem, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, 0;" ::"r"(sa), "l"(src));
+}
+// a lane's two fp32 columns as one 8-byte-aligned pair
+__device__ __forceinline__ bool pair_aligned(const float* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -304,7 +313,21 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
   int len_s = n + 2 - t.y;
   const T* __restrict__ xa = xm + ca;
   const T* __restrict__ ba = SWEEP ? bm + ca : nullptr;
+  // fp32 apply: on the rows where a lane's two columns form an aligned pair
+  // (the same for every lane of the warp) one 8-byte copy and one store take
+  // both (the load/store queue bounds this kernel; in the other kernels the
+  // extra code costs more than it saves)
+  constexpr bool kPairs = sizeof(T) == 4 && !SWEEP;
   auto stage = [&](int slot, int k) {  // row r_k into ring slot `slot`
+    if constexpr (kPairs) {
+      const T* src = xa + off_s;
+      if (k < kb && pair_aligned(reinterpret_cast<const float*>(src))) {
+        cp_async(&ring[slot][lane][0], src, 2 * sizeof(T));
+        off_s += len_s;
+        len_s -= 1;
+        return;
+      }
+    }
     if (k < ka) {
       cp_async(&ring[slot][lane][0], xa + off_s, sizeof(T));
       if (SWEEP) cp_async(&ringb[slot][lane][0], ba + off_s, sizeof(T));
@@ -316,20 +339,32 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
     off_s += len_s;
     len_s -= 1;
   };
+  if constexpr (P::kPoison) {
+    // The float-float row marks see every lane's arithmetic, also on columns
+    // beyond a row's end, which the ring leaves holding an earlier row's
+    // value: the ring starts zeroed (zero-filling copies that read nothing,
+    // completed before the first row is staged), so a stale value is zero or
+    // an input already split in an earlier row.
+#pragma unroll
+    for (int k = 0; k < RING; ++k) {
+      cp_async_zero(&ring[k][lane][0], xm);
+      cp_async_zero(&ring[k][lane][1], xm);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+  }
 #pragma unroll
   for (int k = 0; k < RING; ++k) {
     if (k < steps) stage(k, k);
     cp_async_commit();
   }
   // Columns beyond a row's end hold stale values, which reach only results
-  // that are not written; the float-float kernel zeroes them, since its row
-  // marks see every lane's arithmetic.
+  // that are not written.
   auto take = [&](int k, auto slot_c) -> Row<P> {
     constexpr int slot = decltype(slot_c)::value;
     cp_async_wait<RING - 1>();
     const T va = ring[slot][lane][0], vb = ring[slot][lane][1];
-    Row<P> r = P::kPoison ? make_row<P>(k < ka ? P::conv(va) : P::zero(), k < kb ? P::conv(vb) : P::zero())
-                          : make_row<P>(P::conv(va), P::conv(vb));
+    Row<P> r = make_row<P>(P::conv(va), P::conv(vb));
     if (SWEEP) {  // read before the slot is staged again
       r.b[0] = ringb[slot][lane][0];
       r.b[1] = ringb[slot][lane][1];
@@ -364,8 +399,18 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
       outa = mode_out_staged<MODE, T>(outa, (T)ua, ce.b[0], dint, md.omega);
       outb = mode_out_staged<MODE, T>(outb, (T)ub, ce.b[1], dint, md.omega);
     }
-    if (wa && k < ka) ya[off_o] = outa;
-    if (wbb && k < kb) ya[off_o + 1] = outb;
+    if constexpr (kPairs) {
+      T* dst = ya + off_o;
+      if (wa && wbb && k < kb && pair_aligned(reinterpret_cast<const float*>(dst))) {
+        *reinterpret_cast<float2*>(dst) = make_float2((float)outa, (float)outb);
+      } else {
+        if (wa && k < ka) dst[0] = outa;
+        if (wbb && k < kb) dst[1] = outb;
+      }
+    } else {
+      if (wa && k < ka) ya[off_o] = outa;
+      if (wbb && k < kb) ya[off_o + 1] = outb;
+    }
     off_o += len_o;
     len_o -= 1;
   };
@@ -423,8 +468,8 @@ __global__ void __launch_bounds__(Thr2<MODE>::value, MinBlocks2<P>::value) k_int
   using T = typename P::T;
   constexpr int THR = Thr2<MODE>::value;
   constexpr bool SWEEP = MODE == MODE_JACOBI || MODE == MODE_RESIDUAL;
-  __shared__ T ring_all[THR / 32][RING][32][2];
-  __shared__ T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
+  __shared__ __align__(8) T ring_all[THR / 32][RING][32][2];
+  __shared__ __align__(8) T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
   pdl_trigger();
   apply2d_block<P, MODE>((int)blockIdx.x, x, y, tiles, n_tiles, n_warps, S, n, st, items, n_items, prims, incs,
                          n_if_blocks, md, ring_all, ringb_all);
@@ -460,8 +505,8 @@ __global__ void __launch_bounds__(Thr2<MODE>::value, MinBlocks2<P>::value) k_int
   using T = typename P::T;
   constexpr int THR = Thr2<MODE>::value;
   constexpr bool SWEEP = MODE == MODE_JACOBI || MODE == MODE_RESIDUAL;
-  __shared__ T ring_all[THR / 32][RING][32][2];
-  __shared__ T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
+  __shared__ __align__(8) T ring_all[THR / 32][RING][32][2];
+  __shared__ __align__(8) T ringb_all[SWEEP ? THR / 32 : 1][RING][32][2];
   pdl_trigger();
   int lo = 0, hi = b.count - 1;  // the last mesh whose range starts at or before this block
   while (lo < hi) {

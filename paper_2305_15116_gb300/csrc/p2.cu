@@ -194,6 +194,15 @@ __device__ __forceinline__ void p2_cp_async(void* smem, const void* gmem, int by
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem));
 }
+// a shared-memory element of `bytes` (4 or 8) set to zero by an asynchronous
+// copy that reads no bytes (src, a valid global address, is not accessed)
+__device__ __forceinline__ void p2_cp_zero(void* smem, const void* src, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, 0;" ::"r"(sa), "l"(src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, 0;" ::"r"(sa), "l"(src));
+}
 __device__ __forceinline__ void p2_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
 __device__ __forceinline__ void p2_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -267,6 +276,19 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
     ++rs;
     cs.next();
   };
+  if constexpr (P::kPoison) {
+    // Float-float: the ring starts zeroed (copies that read nothing, completed
+    // before the first row is staged) and a value outside a row is not
+    // selected away: it is zero or an input of an earlier row, met only by
+    // zero weights, and one outside the float-float range marks the row,
+    // which is then recomputed in native fp64.
+#pragma unroll
+    for (int k = 0; k < P2RING; ++k)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) p2_cp_zero(&ring[k][j][lane], xm, sizeof(T));
+    p2_commit();
+    p2_wait<0>();
+  }
 #pragma unroll
   for (int k = 0; k < P2RING; ++k) {
     if (k < steps) stage(k);
@@ -278,7 +300,8 @@ __global__ void __launch_bounds__(P2THREADS) k_p2_rows(const typename P::T* __re
   auto take = [&](int k, auto slot_c) -> P2Row<P> {
     p2_wait<P2RING - 1>();
     constexpr int slot = decltype(slot_c)::value;
-    const bool okv = rc >= 0 && c >= 0 && c < cr.lv, oke = rc >= 0 && c >= 0 && c < cr.le;
+    const bool okv = P::kPoison || (rc >= 0 && c >= 0 && c < cr.lv),
+               oke = P::kPoison || (rc >= 0 && c >= 0 && c < cr.le);
     const V v = okv ? P::conv(ring[slot][0][lane]) : P::zero();
     const V ex = oke ? P::conv(ring[slot][1][lane]) : P::zero();
     const V ey = oke ? P::conv(ring[slot][2][lane]) : P::zero();

@@ -83,6 +83,15 @@ __device__ __forceinline__ void r3_cp_async(void* smem, const void* gmem, int by
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem));
 }
+// a shared-memory element of `bytes` (4 or 8) set to zero by an asynchronous
+// copy that reads no bytes (src, a valid global address, is not accessed)
+__device__ __forceinline__ void r3_cp_zero(void* smem, const void* src, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, 0;" ::"r"(sa), "l"(src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, 0;" ::"r"(sa), "l"(src));
+}
 __device__ __forceinline__ void r3_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
 __device__ __forceinline__ void r3_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -154,6 +163,19 @@ __global__ void __launch_bounds__(R3THREADS) k_row3d(const typename P::T* __rest
     su.next();
     sd.next();
   };
+  if constexpr (P::kPoison) {
+    // Float-float: the ring starts zeroed (copies that read nothing, completed
+    // before the first row is staged) and a value outside the macro is not
+    // selected away: it is zero or an input of an earlier row, met only by
+    // zero class weights, and one outside the float-float range marks the
+    // row, which is then recomputed in native fp64.
+#pragma unroll
+    for (int k = 0; k < RING; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) r3_cp_zero(&ring[k][j][lane], xm, sizeof(T));
+    r3_commit();
+    r3_wait<0>();
+  }
 #pragma unroll
   for (int k = 0; k < RING; ++k) {
     if (k < steps) stage(k);
@@ -168,9 +190,9 @@ __global__ void __launch_bounds__(R3THREADS) k_row3d(const typename P::T* __rest
     r3_wait<RING - 1>();
     const int slot = k & (RING - 1);
     const bool ok = rc >= 0 && c >= 0;
-    const V vz = ok && c < cz.len ? P::conv(ring[slot][0][lane]) : P::zero();
-    const V vu = ok && c < cu.len ? P::conv(ring[slot][1][lane]) : P::zero();
-    const V vd = ok && c < cd.len ? P::conv(ring[slot][2][lane]) : P::zero();
+    const V vz = P::kPoison || (ok && c < cz.len) ? P::conv(ring[slot][0][lane]) : P::zero();
+    const V vu = P::kPoison || (ok && c < cu.len) ? P::conv(ring[slot][1][lane]) : P::zero();
+    const V vd = P::kPoison || (ok && c < cd.len) ? P::conv(ring[slot][2][lane]) : P::zero();
     if (k + RING < steps) stage(slot);
     r3_commit();
     ++rc;
