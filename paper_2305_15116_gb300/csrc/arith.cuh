@@ -6,9 +6,11 @@
 // The HYTEG_F64 path therefore keeps float64 vectors in memory but computes in
 // float-float arithmetic: every float64 value v is split with integer
 // instructions only into v = h + l + r, h = v truncated to 24 significant bits,
-// l = the next 23 bits (|r| <= 2^-46 |v|), products keep the exact fp32 FMA
-// product error, the high parts are summed with Knuth's TwoSum, and the result
-// h + l is rebuilt as a float64 with integer instructions and one fp64 add.
+// l = the next 23 bits (|r| <= 2^-46 |v|), the rounded products of the high
+// parts are summed with Knuth's TwoSum, each product's rounding error (from an
+// FMA) and the TwoSum error go to a low-order fp32 sum with the small
+// products, and the result s + e is rebuilt as a float64 with integer
+// instructions and one fp64 add.
 //
 // Range.  The float-float weight tables hold every weight times 2^40 (an
 // exact scaling), so the row sums s + e come out times 2^40 and the final
@@ -293,19 +295,20 @@ struct ArF64FF {
     e = f2_fma(w.h, v.l, e);
     a.e = f2_fma(w.l, v.h, e);
   }
+  // TwoSum(s, p) gives sn = fl(s + p) and s + p - sn = (s - ap) + (p - bp)
+  // exactly (bp = sn - s, ap = sn - bp); the error sum takes s - ap, and
+  // (p - bp) + (wh*vh - p) = wh*vh - bp as one FMA, rounded once (a rounding
+  // of order 2^-24 of a term already below one ulp of the row's sum).
   static __device__ __forceinline__ void add(Acc& a, const W& w, const P2& v) {
+    f2_t e = f2_fma(w.h, v.l, a.e);             // the small products first
     const f2_t pm = neg_products(w, v);         // -p
-    const f2_t pe = f2_fma(w.h, v.h, pm);       // wh*vh - p, exact
-    // TwoSum(s, p): sn + err == s + p exactly
-    const f2_t sn = f2_sub(a.s, pm);
-    const f2_t bp = f2_sub(sn, a.s);
-    const f2_t t2 = f2_sub(a.s, f2_sub(sn, bp));
-    const f2_t err = f2_sub(t2, f2_add(pm, bp));  // t2 + (p - bp)
+    e = f2_fma(w.l, v.h, e);
+    const f2_t sn = f2_sub(a.s, pm);            // s + p, rounded
+    const f2_t nbp = f2_sub(a.s, sn);           // -bp
+    const f2_t t2 = f2_sub(a.s, f2_add(sn, nbp));  // s - ap, exact
     a.s = sn;
-    f2_t e = f2_add(a.e, err);
-    e = f2_add(e, pe);
-    e = f2_fma(w.h, v.l, e);
-    a.e = f2_fma(w.l, v.h, e);
+    e = f2_add(e, f2_fma(w.h, v.h, nbp));       // + (wh*vh - bp)
+    a.e = f2_add(e, t2);
   }
   // acc += w * (u + v) for a symmetric pair of neighbours: the high parts are
   // added exactly with TwoSum, the low parts and the TwoSum error go to the
@@ -355,15 +358,15 @@ struct ArF64FF {
     a.e = __fmaf_rn(w.l1, v.h, e);
     a.s = p;
   }
-  static __device__ __forceinline__ void add1(Acc1& a, const W& w, V v) {
+  static __device__ __forceinline__ void add1(Acc1& a, const W& w, V v) {  // as add
     const float p = __fmul_rn(w.h1, v.h);
-    const float pe = __fmaf_rn(w.h1, v.h, -p);
     const float sn = __fadd_rn(a.s, p);
-    const float bp = __fsub_rn(sn, a.s);
-    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(sn, bp)), __fsub_rn(p, bp));
+    const float nbp = __fsub_rn(a.s, sn);
+    const float t2 = __fsub_rn(a.s, __fadd_rn(sn, nbp));
+    const float q = __fmaf_rn(w.h1, v.h, nbp);
     a.s = sn;
-    float e = __fadd_rn(a.e, err);
-    e = __fadd_rn(e, pe);
+    float e = __fadd_rn(a.e, t2);
+    e = __fadd_rn(e, q);
     e = __fmaf_rn(w.h1, v.l, e);
     a.e = __fmaf_rn(w.l1, v.h, e);
   }
