@@ -809,9 +809,13 @@ def main():
                 continue
             v = setup(name, device, vcode)
             steps = min(args.steps, 100)
-            # vectors that (nearly) fit in L2 are timed with an L2 flush
-            # before every apply; the value is then from the per-apply events
-            small = 2 * v["ns"] * v["elem"] < 4 * L2_BYTES
+            # vectors within three times the L2 are timed with an L2 flush
+            # before every apply (the value is then from the per-apply events);
+            # larger ones back to back like the headline: an apply streams
+            # them in the same order, so nothing survives in L2 from one
+            # apply to the next, while the flush's write leaves the L2 full
+            # of dirty lines whose write-back would land in the timed apply
+            small = 2 * v["ns"] * v["elem"] < 3 * L2_BYTES
             flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device) if small else None
             rv = timed_applies(v, steps, args.warmup, stream, flush=flush)
             del flush

@@ -313,16 +313,19 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
   int len_s = n + 2 - t.y;
   const T* __restrict__ xa = xm + ca;
   const T* __restrict__ ba = SWEEP ? bm + ca : nullptr;
-  // fp32 apply: on the rows where a lane's two columns form an aligned pair
-  // (the same for every lane of the warp) one 8-byte copy and one store take
-  // both (the load/store queue bounds this kernel; in the other kernels the
-  // extra code costs more than it saves)
-  constexpr bool kPairs = sizeof(T) == 4 && !SWEEP;
+  // fp32: on the rows where a lane's two columns form an aligned pair (the
+  // same for every lane of the warp) one 8-byte copy per vector and one
+  // store take both (the load/store queue bounds these kernels; in the
+  // float-float and native kernels the extra code costs more than it saves)
+  constexpr bool kPairs = sizeof(T) == 4;
   auto stage = [&](int slot, int k) {  // row r_k into ring slot `slot`
     if constexpr (kPairs) {
       const T* src = xa + off_s;
-      if (k < kb && pair_aligned(reinterpret_cast<const float*>(src))) {
+      const T* bsrc = SWEEP ? ba + off_s : src;
+      if (k < kb && pair_aligned(reinterpret_cast<const float*>(src)) &&
+          pair_aligned(reinterpret_cast<const float*>(bsrc))) {
         cp_async(&ring[slot][lane][0], src, 2 * sizeof(T));
+        if (SWEEP) cp_async(&ringb[slot][lane][0], bsrc, 2 * sizeof(T));
         off_s += len_s;
         len_s -= 1;
         return;
