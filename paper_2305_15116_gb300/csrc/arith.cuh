@@ -21,8 +21,8 @@
 // zero or has 2^-80 <= |x| < 2^64 and the largest weight of every stencil has
 // 2^-20 <= max |w| <= 2^14 (smaller weights of a stencil are harmless): the
 // scaled products stay below 2^119 and their sums below 2^125, and what
-// gradual underflow rounds or a dropped subnormal s or e loses is below
-// 2^-126 in scaled units, far below one ulp of the row's largest weight times
+// gradual underflow rounds, or the conversion of a subnormal s or e (to a
+// float64 below 2^-1022), loses is below 2^-126 in scaled units, far below one ulp of the row's largest weight times
 // |x|, which is the accuracy the weights themselves carry.  The weights are
 // checked once per level on the host (LevelDev::ff_ok; levels outside the
 // range run the native fp64 kernels).  An input outside the range (also an
