@@ -363,8 +363,12 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
   }
   // Columns beyond a row's end hold stale values, which reach only results
   // that are not written.
-  auto take = [&](int k, auto slot_c) -> Row<P> {
+  // take(k, slot): the row of step k from its ring slot; the slot is then
+  // staged again with the row of step k + RING (always in the main walk
+  // below, where that step exists; when it does in the tail)
+  auto take_g = [&](int k, auto slot_c, auto always_c) -> Row<P> {
     constexpr int slot = decltype(slot_c)::value;
+    constexpr bool always = decltype(always_c)::value;
     cp_async_wait<RING - 1>();
     const T va = ring[slot][lane][0], vb = ring[slot][lane][1];
     Row<P> r = make_row<P>(P::conv(va), P::conv(vb));
@@ -373,10 +377,13 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
       r.b[1] = ringb[slot][lane][1];
     }
     // the slot of step k is free again: stage step k + RING
-    if (k + RING < steps) stage(slot, k + RING);
+    if (always || k + RING < steps) stage(slot, k + RING);
     cp_async_commit();
     return r;
   };
+  using Always = std::integral_constant<bool, true>;
+  using Guarded = std::integral_constant<bool, false>;
+  auto take = [&](int k, auto slot_c) -> Row<P> { return take_g(k, slot_c, Guarded{}); };
   int off_o = t.y * (n + 2) - (t.y * (t.y + 1)) / 2;  // the row being written
   int len_o = n + 1 - t.y;
   T* __restrict__ ya = ym + ca;
@@ -425,7 +432,20 @@ __device__ __forceinline__ void apply2d_block(int block, const typename P::T* __
   Row<P> r0 = take(0, S0{});
   Row<P> r1 = take(1, S1{});
   Row<P> r2;
-  for (int k = 2; k < steps; k += 3) {
+  int k = 2;
+  // main walk: all three steps of a pass exist and stage a later row, so the
+  // pass has no branch inside (the code generator may interleave the split
+  // of one row with the arithmetic of the previous one)
+  for (; k + 2 + RING < steps; k += 3) {
+    r2 = take_g(k, S2{}, Always{});
+    step(r0, r1, r2, k);
+    r0 = take_g(k + 1, S0{}, Always{});
+    step(r1, r2, r0, k + 1);
+    r1 = take_g(k + 2, S1{}, Always{});
+    step(r2, r0, r1, k + 2);
+  }
+  // the last steps (at most RING + 2)
+  for (; k < steps; k += 3) {
     r2 = take(k, S2{});
     step(r0, r1, r2, k);
     if (k + 1 >= steps) break;
