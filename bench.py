@@ -42,7 +42,8 @@ CPU_SAMPLE_LEVEL = 10  # the oracle's sample of the 2D workload (assembly takes 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=2000,
+                   help="timed applies (default 2000: about 0.5 s, so that the clock sampler sees ~10 samples)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-variants", action="store_true", help="skip the fp32 / 3D / native-fp64 lines")
